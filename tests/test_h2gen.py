@@ -1,0 +1,115 @@
+"""Input generator checks: point sets, kernels, cluster tree, block partition and the
+H^2 construction (checked against dense kernel matrices)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import torch
+
+from h2gen import points as P
+from h2gen.kernels import Kernel, laplace2d_cell_average, near_block
+from h2gen.problems import WORKLOADS, family_points_kernel, make_problem
+from h2gen.tree import admissible, build_kdtree, dual_traversal
+from dataclasses import replace
+
+from conftest import problem
+
+
+def test_fibonacci_sphere_on_unit_sphere():
+    x = P.fibonacci_sphere(1000, 1e-3, 0)
+    assert np.allclose(np.linalg.norm(x, axis=1), 1.0)
+    # without jitter the lattice's z coordinates are 1 - (2i+1)/n
+    y = P.fibonacci_sphere(10, 0.0, 0)
+    assert np.allclose(y[:, 2], 1 - (2 * np.arange(10) + 1) / 10)
+
+
+def test_jittered_grid_within_cells():
+    side = 16
+    x = P.jittered_grid_2d(side, 0.25, 3)
+    h = 1.0 / side
+    g = (np.arange(side) + 0.5) * h
+    cx = np.repeat(g, side)
+    cy = np.tile(g, side)
+    assert np.all(np.abs(x[:, 0] - cx) <= 0.25 * h + 1e-15)
+    assert np.all(np.abs(x[:, 1] - cy) <= 0.25 * h + 1e-15)
+
+
+def test_laplace_cell_average_matches_quadrature():
+    h = 0.01
+    f = lambda y, x: -math.log(math.hypot(x, y)) / (2 * math.pi)
+    val, _ = si.dblquad(f, 0, h / 2, 0, h / 2, epsabs=1e-13)
+    assert abs(4 * val / h**2 - laplace2d_cell_average(h)) < 1e-9
+
+
+def test_kernel_values():
+    r = torch.tensor([0.5], dtype=torch.float64)
+    assert float(Kernel("exp", 0.1)(r)) == pytest.approx(math.exp(-5.0))
+    s = math.sqrt(3) * 0.5 / 0.2
+    assert float(Kernel("matern32", 0.2)(r)) == pytest.approx((1 + s) * math.exp(-s))
+    assert float(Kernel("laplace3d")(r)) == pytest.approx(1 / (2 * math.pi))
+
+
+def test_kdtree_structure():
+    x = P.uniform_box(1000, 2, 1)
+    t = build_kdtree(x, 16)
+    assert t.depth == 6
+    assert sorted(t.perm.tolist()) == list(range(1000))
+    for g in range(t.nnodes - (1 << t.depth)):
+        c1, c2 = 2 * g + 1, 2 * g + 2
+        assert t.size[c1] == t.size[g] // 2 and t.size[c2] == t.size[g] - t.size[g] // 2
+        assert t.start[c1] == t.start[g] and t.start[c2] == t.start[g] + t.size[c1]
+    for g in range(t.nnodes):
+        pts = x[t.perm[t.start[g]:t.start[g] + t.size[g]]]
+        assert np.all(pts >= t.lo[g] - 1e-15) and np.all(pts <= t.hi[g] + 1e-15)
+
+
+def test_partition_covers_matrix_once():
+    x = P.uniform_box(512, 2, 2)
+    t = build_kdtree(x, 16)
+    part = dual_traversal(t, 1.0)
+    cover = np.zeros((512, 512), dtype=np.int64)
+    for l in range(t.depth + 1):
+        for s, q in part.adm[l]:
+            cover[t.start[s]:t.start[s] + t.size[s], t.start[q]:t.start[q] + t.size[q]] += 1
+        if l == t.depth:
+            for s, q in part.inad[l]:
+                cover[t.start[s]:t.start[s] + t.size[s], t.start[q]:t.start[q] + t.size[q]] += 1
+    assert np.all(cover == 1)
+    # admissible pairs satisfy Eq. 1.1, inadmissible leaf pairs do not
+    for l in range(t.depth + 1):
+        if len(part.adm[l]):
+            assert admissible(t, part.adm[l][:, 0], part.adm[l][:, 1], 1.0).all()
+    assert not admissible(t, part.inad[t.depth][:, 0], part.inad[t.depth][:, 1], 1.0).any()
+
+
+@pytest.mark.parametrize("name,over,tol", [
+    ("cov2d", dict(n=1024, leaf=32), 1e-6),
+    ("laplace2d", dict(n=1024, leaf=32), 1e-5),
+    ("sphere", dict(n=2048, leaf=64), 1e-3),
+    ("matern3d", dict(n=2048, leaf=32), 1e-3),
+    ("gauss3d", dict(n=2048), 1e-3),
+])
+def test_h2_matches_dense_kernel(name, over, tol):
+    pb = problem(name, **over)
+    A = pb.A
+    w = replace(WORKLOADS[name], **over)
+    pts, kern = family_points_kernel(w)
+    X = torch.as_tensor(pts[A.perm])
+    K = near_block(kern, X, X, same=True)
+    from oracle.dense import expand
+    M = expand(A.numpy())
+    assert np.linalg.norm(M - K.numpy()) / np.linalg.norm(K.numpy()) < tol
+    assert np.allclose(M, M.T, atol=1e-12 * np.abs(M).max())
+    # spectral norm estimate against the dense symmetric eigenvalues
+    ev = np.linalg.eigvalsh(M)
+    assert pb.norm_a == pytest.approx(np.abs(ev).max(), rel=1e-6)
+
+
+def test_bases_orthonormal(cov2d_1k):
+    from oracle.dense import _bases
+    A = cov2d_1k.A.numpy()
+    U = _bases(A)
+    for g in range(A.nnodes):
+        if A.rank[g]:
+            assert np.allclose(U[g].T @ U[g], np.eye(A.rank[g]), atol=1e-12)

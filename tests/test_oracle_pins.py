@@ -1,0 +1,185 @@
+"""Pins of the CPU oracle against facts the paper and linear algebra fix:
+
+* vanishing truncation reproduces dense Gaussian elimination on the expanded H^2
+  matrix (the zero-truncation invariant), for several kernels and leaf sizes;
+* with no admissible block the method is exactly dense LU (same pivots);
+* log|det A| equals the sum over redundant blocks and the top block (the Q~ are
+  orthogonal, the elementary factors unit triangular: Eq. 2.1);
+* at a positive tolerance the backward error scales with eps_lu (Sec. 3, "Solve");
+* the projection identities of Sec. 2.1: Q~ orthogonal, Q~^T V = [0; I; 0], the
+  truncation identity ||V~V~^T F - F|| = ||Vbar Vbar^T Y - Y||;
+* symmetry of the working near-field and fill blocks after each level;
+* colouring validity and brute-force fill pattern / prefix-sum layouts.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from h2gen import rhs
+from oracle import dense, rs
+from oracle import structure as st
+
+from conftest import problem
+
+ZERO_TRUNC = 1e-13
+
+
+def _dense_solution(A, b):
+    M = dense.expand(A)
+    return M, np.linalg.solve(M, b)
+
+
+@pytest.mark.parametrize("name,over", [
+    ("cov2d", dict(n=1024, leaf=32)),
+    ("cov2d", dict(n=512, leaf=16)),
+    ("laplace2d", dict(n=1024, leaf=32)),
+    ("sphere", dict(n=2048, leaf=64)),
+    ("matern3d", dict(n=1024, leaf=32)),
+    ("gauss3d", dict(n=1500, leaf=32)),
+])
+def test_zero_truncation_equals_dense_solve(name, over):
+    pb = problem(name, **over)
+    A = pb.A.numpy()
+    b = rhs(A.n, 3, seed=1)
+    M, xd = _dense_solution(A, b)
+    Z = rs.factorize(A, ZERO_TRUNC, pb.norm_a)
+    x = rs.solve(Z, b)
+    kappa = np.linalg.cond(M)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-15 * kappa * 200
+    nw, _ = dense.backward_error(A, x, b, pb.norm_a)
+    assert nw < 1e-13
+    # slogdet of the factors (Eq. 2.1)
+    assert rs.slogdet(Z) == pytest.approx(np.linalg.slogdet(M)[1], abs=1e-9)
+
+
+def test_no_admissible_block_is_dense_lu():
+    pb = problem("cov2d", n=256, leaf=16, eta=1e-6)
+    A = pb.A.numpy()
+    assert A.top_level() is None
+    Z = rs.factorize(A, 1e-6, pb.norm_a)
+    assert Z.levels == []
+    M = dense.expand(A)
+    lu, piv = sla.lu_factor(M)
+    assert np.array_equal(Z.top_lu[0], lu) and np.array_equal(Z.top_lu[1], piv)
+    b = rhs(A.n, 2)
+    assert np.allclose(rs.solve(Z, b), sla.lu_solve((lu, piv), b), rtol=0, atol=0)
+
+
+def test_backward_error_tracks_tolerance():
+    pb = problem("cov2d", n=1024, leaf=32)
+    A = pb.A.numpy()
+    b = rhs(A.n, 1, seed=2)
+    errs = []
+    for eps in (1e-3, 1e-7, 1e-8, 1e-9):
+        Z = rs.factorize(A, eps, pb.norm_a)
+        nw, _ = dense.backward_error(A, rs.solve(Z, b), b, pb.norm_a)
+        errs.append(nw)
+        assert nw < 10 * eps
+    # once the threshold is below the fill's singular values, lowering it
+    # lowers the error (above that no fill basis vector is kept at all)
+    assert errs[0] >= errs[1] > errs[2] > errs[3]
+
+
+def test_projection_identities():
+    pb = problem("cov2d", n=1024, leaf=32)
+    A = pb.A.numpy()
+    seen = {"aug": 0, "box": 0}
+
+    def hook(ev, **s):
+        if ev == "augment" and s["Frow"] is not None and s["Vt"].shape[1] > s["V"].shape[1]:
+            V, Vt, Fr = s["V"], s["Vt"], s["Frow"]
+            Y = Fr - V @ (V.T @ Fr)
+            Vb = Vt[:, V.shape[1]:]
+            lhs = np.linalg.norm(Vt @ (Vt.T @ Fr) - Fr)
+            rhs_ = np.linalg.norm(Vb @ (Vb.T @ Y) - Y)
+            assert lhs == pytest.approx(rhs_, rel=1e-8, abs=1e-12 * np.linalg.norm(Fr))
+            seen["aug"] += 1
+        if ev == "box":
+            bx, V = s["box"], s["V"]
+            Q = bx.Q
+            assert np.allclose(Q.T @ Q, np.eye(bx.n), atol=1e-13)
+            P = Q.T @ V                            # [0 (r); I (k); 0 (kt-k)]
+            ref = np.zeros_like(P)
+            ref[bx.r:bx.r + bx.k, :] = np.eye(bx.k)
+            assert np.allclose(P, ref, atol=1e-12)
+            seen["box"] += 1
+
+    rs.factorize(A, 1e-10, pb.norm_a, hook=hook)
+    assert seen["aug"] > 10 and seen["box"] > 10
+
+
+def test_working_blocks_stay_symmetric():
+    pb = problem("sphere", n=2048, leaf=64)
+    A = pb.A.numpy()
+    worst = []
+
+    def hook(ev, **s):
+        if ev in ("level_start", "level_end"):
+            D, F = s["D"], s["F"]
+            scale = max(np.abs(B).max() for B in D.values())
+            for (i, j), B in D.items():
+                worst.append(np.abs(B - D[(j, i)].T).max() / scale)
+            for (i, j), B in F.items():
+                worst.append(np.abs(B - F[(j, i)].T).max() / scale)
+
+    rs.factorize(A, 1e-6, pb.norm_a, hook=hook)
+    assert worst and max(worst) < 1e-12
+
+
+def test_colouring_valid_and_bounded():
+    for name, over in [("cov2d", dict(n=2048, leaf=16)), ("matern3d", dict(n=2048, leaf=32))]:
+        A = problem(name, **over).A.numpy()
+        for l in range(1, A.depth + 1):
+            nb = st.neighbours(A, l)
+            col = st.greedy_colouring(nb)
+            for i in range(len(nb)):
+                assert all(col[j] != col[i] for j in nb[i] if j != i)
+            csp = max(len(x) for x in nb)
+            assert max(col) + 1 <= csp
+            # first fit: every box's colour is the smallest not used by a
+            # lower-indexed neighbour
+            for i in range(len(nb)):
+                lower = {col[j] for j in nb[i] if j < i}
+                assert col[i] == min(set(range(len(nb) + 1)) - lower)
+
+
+def test_fill_pattern_brute_force():
+    """The structural fill pattern contains every block that the elimination
+    actually fills, and nothing that could never be filled."""
+    pb = problem("cov2d", n=1024, leaf=32)
+    A = pb.A.numpy()
+    seen = {}
+
+    def hook(ev, **s):
+        if ev == "level_end":
+            seen[s["l"]] = {k for k, B in s["F"].items() if np.abs(B).max() > 0}
+
+    Z = rs.factorize(A, 1e-8, pb.norm_a, hook=hook)
+    for lv in Z.levels:
+        nb = st.neighbours(A, lv.level)
+        lay = lv.layout
+        blocks = {(int(np.searchsorted(lay["row_ptr"], e, side="right") - 1), int(c))
+                  for e, c in enumerate(lay["col"])}
+        near = {(i, j) for i in range(len(nb)) for j in nb[i]}
+        assert near <= blocks
+        assert seen[lv.level] <= blocks - near
+        # offsets are the exclusive prefix sum of n_j * n_k in CSR order
+        order = sorted(blocks)
+        expect = np.concatenate([[0], np.cumsum([lv.sizes[a] * lv.sizes[b] for a, b in order])])
+        assert np.array_equal(lay["offset"], expect)
+
+
+def test_truncation_keeps_strictly_above_threshold():
+    """Sec. 2.1: singular vectors with sigma > eps_fill are kept, the rest dropped."""
+    rng = np.random.default_rng(0)
+    V = np.linalg.qr(rng.standard_normal((20, 3)))[0]
+    P0 = np.linalg.qr(rng.standard_normal((20, 20)))[0]
+    Pperp = P0 - V @ (V.T @ P0)
+    Pperp = np.linalg.qr(Pperp)[0][:, :5]
+    sig = np.array([10.0, 3.0, 1.0, 0.5, 0.1])
+    W = np.linalg.qr(rng.standard_normal((40, 5)))[0]
+    F = Pperp @ np.diag(sig) @ W.T + V @ rng.standard_normal((3, 40))
+    for thr, keep in [(0.09, 5), (0.2, 4), (0.99, 3), (1.01, 2), (20.0, 0)]:
+        Vt = rs._augment(V, F, thr)
+        assert Vt.shape[1] == 3 + keep
+        assert np.allclose(Vt.T @ Vt, np.eye(3 + keep), atol=1e-13)
