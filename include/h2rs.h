@@ -1,0 +1,202 @@
+/*
+ * h2rs — strong recursive skeletonisation (RS-S) factorisation and solve of a
+ * symmetric H^2 matrix on one NVIDIA B300 (sm_103a).
+ *
+ * The method is that of "Linear Complexity H^2 Direct Solver for Fine-Grained
+ * Parallel Architectures" (Boukaram, Keyes, Li, Liu, Turkiyyah): the factorisation
+ * of Alg. 1 / Alg. 2 (Sec. 2.1-2.2, Eq. 2.1) and the solve of Alg. 3 (Sec. 2.3).
+ * Iterative refinement with a float64 H^2 residual is added on top of the paper's
+ * solve so that a reduced-precision factor can reach a float64 backward error.
+ *
+ * Conventions
+ *  - All functions return 0 (H2_OK) on success and a negative H2_ERR_* code on
+ *    failure; h2_last_error() returns a thread-local message for the last failure.
+ *    No C++ exception crosses this interface and no kernel traps.
+ *  - Vectors are in cluster-tree order (the order of h2_matrix_desc.node_start);
+ *    multiple right-hand sides are column-major with a leading dimension.
+ *  - Dense blocks are column-major float64.
+ *  - Nodes of the complete binary cluster tree use heap numbering: level l holds
+ *    the ids 2^l-1 .. 2^(l+1)-2, node g has children 2g+1 and 2g+2.
+ *  - "device" pointers are CUDA device pointers of the current device; the
+ *    library runs every kernel on the stream given in the options / descriptor
+ *    (NULL = the legacy default stream).
+ */
+#ifndef H2RS_H
+#define H2RS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define H2_API __attribute__((visibility("default")))
+#else
+#define H2_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+    H2_OK = 0,
+    H2_ERR_ARG = -1,            /* invalid argument or inconsistent descriptor       */
+    H2_ERR_OOM = -2,            /* device or host allocation failed                   */
+    H2_ERR_SINGULAR = -3,       /* zero or non-finite pivot in a redundant/top block  */
+    H2_ERR_RANK_CAP = -4,       /* augmented rank exceeded the box size (never for k~<=n) */
+    H2_ERR_NONFINITE = -5,      /* non-finite value in an input or a result          */
+    H2_ERR_NO_CONVERGENCE = -6, /* refinement did not reach the tolerance in maxit   */
+    H2_ERR_TIMEOUT = -7,        /* a bounded device wait gave up                      */
+    H2_ERR_CUDA = -8,           /* a CUDA runtime call failed                         */
+    H2_ERR_STATE = -9           /* object used in a wrong state                       */
+};
+
+/* working precision of the factorisation and of the solve that applies it */
+enum {
+    H2_PREC_FP64 = 0,           /* float64 everywhere                                 */
+    H2_PREC_FP32 = 1            /* float32 factor and solve; the top-level dense LU
+                                   and the refinement residual stay float64           */
+};
+
+/* ------------------------------------------------------------------ H^2 matrix */
+/*
+ * Descriptor of a symmetric H^2 matrix A = H + D (Sec. 1.1, Fig. 1-3):
+ *   admissible blocks  A_st = U_s S_st U_t^T  with nested orthonormal bases
+ *   U_p = diag(U_c1, U_c2) [E_c1; E_c2], and dense near-field blocks on the
+ *   inadmissible leaf pairs.  All index arrays are HOST arrays; the four value
+ *   arrays U, E, S, D are host or device arrays (values_on_device).
+ *
+ *   n               matrix size
+ *   depth           d: leaves at level d, root at level 0 (nnodes = 2^(d+1)-1)
+ *   node_start[g]   first tree-order index of node g         (nnodes)
+ *   node_size[g]    number of indices of node g              (nnodes)
+ *   rank[g]         basis rank k_g of node g                 (nnodes)
+ *   U_off[i]        leaf i (node 2^d-1+i): U_i = U[U_off[i] ..], node_size x rank
+ *                   (2^d + 1 entries, last = total)
+ *   E_off[g]        transfer E_g (rank_g x rank_parent), g >= 1; E_off[0] = 0
+ *                   (nnodes + 1 entries)
+ *   adm_ptr[g]      CSR over all nodes of the admissible pairs (s = g, t) of the
+ *   adm_col[e]      same level (nnodes + 1 / nadm entries), symmetric pattern
+ *   S_off[e]        coupling S_st (rank_s x rank_t) of entry e (nadm + 1 entries)
+ *   inad_ptr[g]     CSR over all nodes of the inadmissible pairs of the same
+ *   inad_col[e]     level, including (g, g), symmetric pattern, columns sorted
+ *   D_off[j]        dense block (size_s x size_t) of the j-th inadmissible entry of
+ *                   a LEAF row, in CSR order (nnear + 1 entries)
+ * The library copies everything it needs; the caller keeps ownership of its
+ * arrays, which may be freed after h2_matrix_create returns.
+ */
+typedef struct {
+    int64_t n;
+    int32_t depth;
+    int32_t values_on_device;
+    const int64_t* node_start;
+    const int64_t* node_size;
+    const int64_t* rank;
+    const int64_t* U_off;
+    const double* U;
+    const int64_t* E_off;
+    const double* E;
+    const int64_t* adm_ptr;
+    const int64_t* adm_col;
+    const int64_t* S_off;
+    const double* S;
+    const int64_t* inad_ptr;
+    const int64_t* inad_col;
+    const int64_t* D_off;
+    const double* D;
+    void* stream;               /* cudaStream_t used for the copies */
+} h2_matrix_desc;
+
+typedef struct h2_matrix h2_matrix;   /* opaque: device copy of A + its level plans */
+typedef struct h2_factor h2_factor;   /* opaque: owns all device memory of Z         */
+
+/* Copy A to the device and plan its level structure (near-field graph, greedy
+ * colouring, fill pattern, Schur target lists; Sec. 2.2).  *out is set on success.
+ * Errors: H2_ERR_ARG (inconsistent descriptor), H2_ERR_OOM, H2_ERR_CUDA. */
+H2_API int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out);
+H2_API void h2_matrix_destroy(h2_matrix* A);
+
+/* y = A x in float64 (the H^2 matrix-vector product: upsweep, couplings, downsweep,
+ * near field).  x: n x nrhs (ldx >= n), y: n x nrhs (ldy >= n); both device pointers
+ * when on_device != 0, else host pointers (copied in and out).  Errors: H2_ERR_ARG,
+ * H2_ERR_CUDA. */
+H2_API int h2_matvec(const h2_matrix* A, int32_t nrhs, const double* x, int64_t ldx,
+              double* y, int64_t ldy, int32_t on_device);
+
+/* ------------------------------------------------------------- factorisation */
+typedef struct {
+    double eps_lu;              /* truncation threshold of the fill (Alg. 1)           */
+    double norm_a;              /* ||A||_2 supplied by the caller: eps_fill = eps_lu*norm_a */
+    int32_t precision;          /* H2_PREC_*                                           */
+    int32_t reserved;
+    void* stream;               /* cudaStream_t for every kernel of this factor        */
+} h2_factor_opts;
+
+/* Factorise A (Alg. 1): levels d..t, greedy colours in order, per colour the
+ * batched basis augmentation (QR of the fill row + one-sided Jacobi SVD), orthogonal
+ * completion, projection, partial LU and target-owned Schur update; level close;
+ * float64 dense LU of the top level.  The factor keeps a pointer to A's plans, so A
+ * must outlive it.  Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_SINGULAR (see
+ * h2_factor_stats: error_level / error_box), H2_ERR_NONFINITE, H2_ERR_CUDA. */
+H2_API int h2_factor_create(const h2_matrix* A, const h2_factor_opts* opts, h2_factor** out);
+H2_API void h2_factor_destroy(h2_factor* Z);
+
+/* Solve A x = b with the factor (Alg. 3), in place: b (n x nrhs, ldb >= n) is
+ * overwritten with x.  Device pointer when on_device != 0, else host (copied).
+ * The solve runs in the factor's precision.  Errors: H2_ERR_ARG, H2_ERR_CUDA. */
+H2_API int h2_solve(const h2_factor* Z, int32_t nrhs, double* b, int64_t ldb, int32_t on_device);
+
+/* Iterative refinement in float64: x0 = solve(b); x_{k+1} = x_k + solve(b - A x_k)
+ * until max over columns of ||b - A x|| / (norm_a ||x||) <= tol or maxit
+ * corrections.  b, x: n x nrhs (device when on_device != 0).  *iters receives the
+ * number of corrections, *berr the final backward error.  Returns
+ * H2_ERR_NO_CONVERGENCE (x still written) if tol was not reached. */
+H2_API int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs,
+                    const double* b, int64_t ldb, double* x, int64_t ldx,
+                    double tol, int32_t maxit, int32_t on_device,
+                    int32_t* iters, double* berr);
+
+/* ------------------------------------------------------------------ inspection */
+typedef struct {
+    int32_t nlevels;            /* skeletonised levels (d .. t)                        */
+    int32_t top_level;          /* t, or -1 when no block is admissible                */
+    int64_t top_size;           /* order of the dense top-level matrix                 */
+    int64_t factor_bytes;       /* device bytes held by the factor                     */
+    int64_t peak_bytes;         /* peak device bytes during the factorisation          */
+    int32_t error_level;        /* level / local box of the last singular pivot, or -1 */
+    int32_t error_box;
+    double factor_ms;           /* device time of the last factorisation               */
+    double phase_ms[8];         /* augment, complete+project, lu+trsm, schur, close,
+                                   top, leaf load, other                              */
+    double phase_flops[8];      /* algorithmic flops of the same phases                */
+    double phase_bytes[8];      /* algorithmic bytes of the same phases                */
+} h2_factor_stats;
+
+H2_API int h2_factor_stats_get(const h2_factor* Z, h2_factor_stats* out);
+
+/* Per-level layout of the factorisation, levels numbered 0 = leaves (depth d) up to
+ * nlevels-1 (level t).  h2_layout_counts gives the number of boxes and blocks;
+ * h2_layout_get fills caller arrays (any may be NULL):
+ *   sizes[nbox]   n_i at that level       ranks[nbox]  augmented rank k~_i
+ *   colour[nbox]  greedy colour            row_ptr[nbox+1], col[nblk], kind[nblk]
+ *   offset[nblk+1] prefix sums of n_j*n_k over the merged (near + fill) block list
+ *   kind: 0 near-field block, 1 fill-in block. */
+H2_API int h2_layout_counts(const h2_factor* Z, int32_t level, int64_t* nbox, int64_t* nblk);
+H2_API int h2_layout_get(const h2_factor* Z, int32_t level, int64_t* sizes, int64_t* ranks,
+                  int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind,
+                  int64_t* offset);
+
+/* Host-only query of the level plan (no GPU needed): for the skeletonised level
+ * `level` (0 = leaves), the number of boxes and of merged blocks, the greedy colour
+ * of every box and the merged block CSR with kinds, exactly as h2_factor_create
+ * will use them.  Only the index arrays of the descriptor are read.  Arrays may be
+ * NULL (counts only).  Errors: H2_ERR_ARG. */
+H2_API int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
+                  int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind);
+
+H2_API const char* h2_last_error(void);
+H2_API const char* h2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2RS_H */

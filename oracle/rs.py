@@ -6,9 +6,9 @@ the timed CPU baseline; the CUDA library never imports it and shares no code wit
 
 Factorisation (Alg. 1 and Alg. 2; Sec. 2.1 steps 1-4; level close and Eq. 2.1):
 levels from the leaves (d) up to the top level t; at each level the colours of
-``greedy_colouring`` in order, the boxes of a colour in ascending index.  Processing
-same-coloured boxes one after another equals Alg. 2's "project all, then LU all",
-because no box of the colour touches another's block row or column.  For box i:
+``greedy_colouring`` in order; within a colour, as in Alg. 2, every box is augmented
+from the same fill matrix, then every box is projected, then every box gets its
+partial LU (boxes in ascending index; their Schur updates commute).  For box i:
 
   1. fill row  F_i* of the working fill-in matrix, ``Y = (I - V V^T) F_i*``;
   2. truncSVD option 2 (Sec. 2.1): QR of ``Y^T``, SVD of R; the left singular
@@ -143,23 +143,24 @@ def _complete(Vt):
     return np.hstack([Qh[:, kt:], Vt])
 
 
-def _skeletonise(i, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None):
-    n = sizes[i]
-    k = V[i].shape[1]
+def _augment_box(i, sizes, V, F, frow, eps_fill, hook=None):
+    """Alg. 2, first parallel loop: V~_i = [V_i, truncSVD((I - V V^T) F_i*)]."""
     frow_keys = [(i, j) for j in frow.get(i, [])]
     Frow = np.hstack([F[key] for key in frow_keys]) if frow_keys else None
     Vt = _augment(V[i], Frow, eps_fill)
     if hook is not None:
         hook("augment", i=i, V=V[i], Vt=Vt, Frow=Frow)
-    kt = Vt.shape[1]
-    r = n - kt
-    Q = _complete(Vt)
-    # projection of the block row and column of i (D and F)
+    return Vt
+
+
+def _project_box(i, Q, r, nbrs, D, F, frow, fcol):
+    """Alg. 2: D <- Q^T D Q and F <- Q^T F Q on the block row and column of box i,
+    with the redundant rows/columns of F dropped (the truncation)."""
     for j in nbrs[i]:
         D[(i, j)] = Q.T @ D[(i, j)]
     for j in nbrs[i]:
         D[(j, i)] = D[(j, i)] @ Q
-    for key in frow_keys:
+    for key in [(i, j) for j in frow.get(i, [])]:
         B = Q.T @ F[key]
         B[:r, :] = 0.0
         F[key] = B
@@ -167,7 +168,11 @@ def _skeletonise(i, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None):
         B = F[key] @ Q
         B[:, :r] = 0.0
         F[key] = B
-    # partial LU of the redundant block and Schur update of N(i) x N(i)
+
+
+def _partial_lu(i, n, r, nbrs, sizes, D, F):
+    """Alg. 2 partialLU for box i: LU of D_RR, elementary factors, Schur update of
+    N(i) x N(i) (fill outside the near field goes to F), eliminated rows/cols zeroed."""
     WL, WU = {}, {}
     lu = None
     if r > 0:
@@ -191,7 +196,24 @@ def _skeletonise(i, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None):
         for j in nbrs[i]:
             D[(i, j)][:r, :] = 0.0
             D[(j, i)][:, :r] = 0.0
-    return BoxFactor(n=n, k=k, kt=kt, Q=Q, lu=lu, nb=list(nbrs[i]), WL=WL, WU=WU)
+    return lu, WL, WU
+
+
+def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None):
+    """Alg. 2 for one colour: augment every box from the same fill matrix, then
+    project every box, then the partial LU of every box.  (Boxes of one colour share
+    no near-field block, but two of them can share a fill block, so augmenting one
+    after projecting the other would not be Alg. 2.)"""
+    Vt = {i: _augment_box(i, sizes, V, F, frow, eps_fill, hook) for i in C}
+    Qs = {i: _complete(Vt[i]) for i in C}
+    for i in C:
+        _project_box(i, Qs[i], sizes[i] - Vt[i].shape[1], nbrs, D, F, frow, fcol)
+    out = {}
+    for i in C:
+        n, kt = sizes[i], Vt[i].shape[1]
+        lu, WL, WU = _partial_lu(i, n, n - kt, nbrs, sizes, D, F)
+        out[i] = BoxFactor(n=n, k=V[i].shape[1], kt=kt, Q=Qs[i], lu=lu, nb=list(nbrs[i]), WL=WL, WU=WU)
+    return out
 
 
 # ------------------------------------------------------------------ driver
@@ -224,10 +246,13 @@ def factorize(A, eps_lu: float, norm_a: float, hook=None) -> Factor:
         boxes = [None] * cnt
         if hook is not None:
             hook("level_start", l=l, D=D, F=F, V=V, sizes=sizes)
-        for i in order:
-            boxes[i] = _skeletonise(i, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook)
-            if hook is not None:
-                hook("box", l=l, i=i, box=boxes[i], V=V[i])
+        for c in range(max(colour) + 1):
+            C = [i for i in range(cnt) if colour[i] == c]
+            done = _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook)
+            for i in C:
+                boxes[i] = done[i]
+                if hook is not None:
+                    hook("box", l=l, i=i, box=boxes[i], V=V[i])
         Z.levels.append(LevelFactor(l, list(sizes), colour, order, boxes, layout))
         if hook is not None:
             hook("level_end", l=l, D=D, F=F, boxes=boxes)

@@ -1,0 +1,386 @@
+// C-ABI of the library: object lifetimes, argument checks, error codes.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "factor_impl.h"
+#include "matvec.cuh"
+
+namespace h2rs {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+void DevBuf::alloc(size_t nbytes, cudaStream_t s) {
+    release();
+    stream = s;
+    if (nbytes == 0) nbytes = 1;
+    cudaError_t e = cudaMallocAsync(&ptr, nbytes, s);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        (void)cudaGetLastError();
+        throw Error{H2_ERR_OOM, "device allocation of " + std::to_string(nbytes) +
+                                    " bytes failed: " + cudaGetErrorString(e)};
+    }
+    bytes = nbytes;
+}
+
+void DevBuf::release() {
+    if (ptr) {
+        cudaFreeAsync(ptr, stream);
+        ptr = nullptr;
+        bytes = 0;
+    }
+}
+
+static void keep_pool_memory() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+}
+
+template <class F>
+static int guard(F&& f) {
+    try {
+        f();
+        return H2_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_error(e.what());
+        return H2_ERR_ARG;
+    } catch (...) {
+        set_error("unknown error");
+        return H2_ERR_ARG;
+    }
+}
+
+template <class T>
+static std::vector<T> host_copy(const T* p, int64_t n, const char* what) {
+    H2_REQUIRE(n >= 0, H2_ERR_ARG, std::string("negative length for ") + what);
+    H2_REQUIRE(n == 0 || p != nullptr, H2_ERR_ARG, std::string("null array ") + what);
+    return std::vector<T>(p, p + n);
+}
+
+// index arrays -> host structure, with consistency checks
+static void read_structure(const h2_matrix_desc* d, HostStructure& H) {
+    H2_REQUIRE(d != nullptr, H2_ERR_ARG, "null descriptor");
+    H2_REQUIRE(d->n > 0 && d->depth >= 0 && d->depth < 30, H2_ERR_ARG, "bad n or depth");
+    H.n = d->n;
+    H.d = d->depth;
+    H.nnodes = (int64_t(1) << (H.d + 1)) - 1;
+    const int64_t nn = H.nnodes, nleaf = int64_t(1) << H.d, first_leaf = nleaf - 1;
+    H.node_start = host_copy(d->node_start, nn, "node_start");
+    H.node_size = host_copy(d->node_size, nn, "node_size");
+    H.rank = host_copy(d->rank, nn, "rank");
+    H.U_off = host_copy(d->U_off, nleaf + 1, "U_off");
+    H.E_off = host_copy(d->E_off, nn + 1, "E_off");
+    H.adm_ptr = host_copy(d->adm_ptr, nn + 1, "adm_ptr");
+    H.inad_ptr = host_copy(d->inad_ptr, nn + 1, "inad_ptr");
+    H2_REQUIRE(H.adm_ptr[0] == 0 && H.inad_ptr[0] == 0, H2_ERR_ARG, "CSR must start at 0");
+    H.adm_col = host_copy(d->adm_col, H.adm_ptr[nn], "adm_col");
+    H.S_off = host_copy(d->S_off, H.adm_ptr[nn] + 1, "S_off");
+    H.inad_col = host_copy(d->inad_col, H.inad_ptr[nn], "inad_col");
+    const int64_t nnear = H.inad_ptr[nn] - H.inad_ptr[first_leaf];
+    H.D_off = host_copy(d->D_off, nnear + 1, "D_off");
+    H2_REQUIRE(H.node_size[0] == H.n && H.node_start[0] == 0, H2_ERR_ARG, "root must cover 0..n");
+    for (int64_t g = 0; g < nn - nleaf; ++g) {
+        const int64_t c1 = 2 * g + 1, c2 = 2 * g + 2;
+        H2_REQUIRE(H.node_size[c1] + H.node_size[c2] == H.node_size[g] &&
+                       H.node_start[c1] == H.node_start[g] &&
+                       H.node_start[c2] == H.node_start[g] + H.node_size[c1],
+                   H2_ERR_ARG, "children must partition their parent");
+    }
+    for (int64_t i = 0; i < nleaf; ++i) {
+        const int64_t g = first_leaf + i;
+        H2_REQUIRE(H.rank[g] >= 0 && H.rank[g] <= H.node_size[g], H2_ERR_ARG, "leaf rank > size");
+        H2_REQUIRE(H.U_off[i + 1] - H.U_off[i] == H.node_size[g] * H.rank[g], H2_ERR_ARG, "U_off size");
+    }
+    for (int64_t g = 1; g < nn; ++g)
+        H2_REQUIRE(H.E_off[g + 1] - H.E_off[g] == H.rank[g] * H.rank[(g - 1) / 2], H2_ERR_ARG,
+                   "E_off size");
+    for (int64_t g = 0; g < nn; ++g) {
+        const int l = 63 - __builtin_clzll((unsigned long long)(g + 1));
+        const int64_t lf = (int64_t(1) << l) - 1, ll = (int64_t(1) << (l + 1)) - 1;
+        for (int64_t e = H.adm_ptr[g]; e < H.adm_ptr[g + 1]; ++e) {
+            const int64_t t = H.adm_col[e];
+            H2_REQUIRE(t >= lf && t < ll, H2_ERR_ARG, "admissible pair across levels");
+            H2_REQUIRE(H.S_off[e + 1] - H.S_off[e] == H.rank[g] * H.rank[t], H2_ERR_ARG, "S_off size");
+        }
+        bool self = false;
+        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
+            const int64_t t = H.inad_col[e];
+            H2_REQUIRE(t >= lf && t < ll, H2_ERR_ARG, "inadmissible pair across levels");
+            self |= t == g;
+            if (e > H.inad_ptr[g]) H2_REQUIRE(t > H.inad_col[e - 1], H2_ERR_ARG, "inad_col not sorted");
+            if (g >= first_leaf) {
+                const int64_t j = e - H.inad_ptr[first_leaf];
+                H2_REQUIRE(H.D_off[j + 1] - H.D_off[j] == H.node_size[g] * H.node_size[t], H2_ERR_ARG,
+                           "D_off size");
+            }
+        }
+        H2_REQUIRE(self, H2_ERR_ARG, "every node must be in its own near field");
+    }
+}
+
+template <class T>
+static void upload_values(DevBuf& b, const T* p, int64_t n, bool on_dev, cudaStream_t s) {
+    b.alloc(std::max<int64_t>(1, n) * sizeof(T), s);
+    if (n > 0)
+        H2_CUDA_CHECK(cudaMemcpyAsync(b.ptr, p, n * sizeof(T),
+                                      on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+}  // namespace h2rs
+
+using namespace h2rs;
+
+extern "C" {
+
+const char* h2_last_error(void) { return g_err.c_str(); }
+const char* h2_version(void) { return "h2rs 0.1 (sm_103a)"; }
+
+int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out) {
+    if (!out) { set_error("null output pointer"); return H2_ERR_ARG; }
+    *out = nullptr;
+    h2_matrix* A = nullptr;
+    int rc = guard([&] {
+        keep_pool_memory();
+        A = new h2_matrix();
+        MatrixObj& M = A->m;
+        read_structure(desc, M.H);
+        M.stream = static_cast<cudaStream_t>(desc->stream);
+        cudaStream_t s = M.stream;
+        const HostStructure& H = M.H;
+        const int64_t nn = H.nnodes, nleaf = int64_t(1) << H.d;
+        const bool od = desc->values_on_device != 0;
+        H2_REQUIRE((desc->U || H.U_off[nleaf] == 0) && (desc->E || H.E_off[nn] == 0) &&
+                       (desc->S || H.S_off.back() == 0) && (desc->D || H.D_off.back() == 0),
+                   H2_ERR_ARG, "null value array");
+        upload_values(M.U, desc->U, H.U_off[nleaf], od, s);
+        upload_values(M.E, desc->E, H.E_off[nn], od, s);
+        upload_values(M.S, desc->S, H.S_off.back(), od, s);
+        upload_values(M.D, desc->D, H.D_off.back(), od, s);
+        upload(M.d_node_start, H.node_start, s);
+        upload(M.d_node_size, H.node_size, s);
+        upload(M.d_rank, H.rank, s);
+        upload(M.d_U_off, H.U_off, s);
+        upload(M.d_E_off, H.E_off, s);
+        upload(M.d_S_off, H.S_off, s);
+        upload(M.d_D_off, H.D_off, s);
+        upload(M.d_adm_ptr, H.adm_ptr, s);
+        upload(M.d_adm_col, H.adm_col, s);
+        upload(M.d_inad_ptr, H.inad_ptr, s);
+        upload(M.d_inad_col, H.inad_col, s);
+        M.coef_off.assign(nn + 1, 0);
+        for (int64_t g = 0; g < nn; ++g) M.coef_off[g + 1] = M.coef_off[g] + H.rank[g];
+        upload(M.d_coef_off, M.coef_off, s);
+        build_plan(H, M.plan);
+        H2_CUDA_CHECK(cudaStreamSynchronize(s));
+    });
+    if (rc != H2_OK) { delete A; return rc; }
+    *out = A;
+    return H2_OK;
+}
+
+void h2_matrix_destroy(h2_matrix* A) { delete A; }
+
+int h2_matvec(const h2_matrix* A, int32_t nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
+              int32_t on_device) {
+    return guard([&] {
+        H2_REQUIRE(A && x && y && nrhs > 0, H2_ERR_ARG, "bad matvec arguments");
+        const MatrixObj& M = A->m;
+        const int64_t n = M.H.n;
+        H2_REQUIRE(ldx >= n && ldy >= n, H2_ERR_ARG, "leading dimension < n");
+        cudaStream_t s = M.stream;
+        if (on_device) {
+            matvec_dev(M, nrhs, x, ldx, y, ldy, s);
+        } else {
+            DevBuf dx, dy;
+            dx.alloc(n * nrhs * sizeof(double), s);
+            dy.alloc(n * nrhs * sizeof(double), s);
+            H2_CUDA_CHECK(cudaMemcpy2DAsync(dx.ptr, n * sizeof(double), x, ldx * sizeof(double),
+                                            n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
+            matvec_dev(M, nrhs, dx.as<double>(), n, dy.as<double>(), n, s);
+            H2_CUDA_CHECK(cudaMemcpy2DAsync(y, ldy * sizeof(double), dy.ptr, n * sizeof(double),
+                                            n * sizeof(double), nrhs, cudaMemcpyDeviceToHost, s));
+        }
+        H2_CUDA_CHECK(cudaStreamSynchronize(s));
+    });
+}
+
+int h2_factor_create(const h2_matrix* A, const h2_factor_opts* o, h2_factor** out) {
+    if (!out) { set_error("null output pointer"); return H2_ERR_ARG; }
+    *out = nullptr;
+    h2_factor* Z = nullptr;
+    int rc = guard([&] {
+        H2_REQUIRE(A && o, H2_ERR_ARG, "null matrix or options");
+        H2_REQUIRE(o->eps_lu >= 0 && std::isfinite(o->eps_lu), H2_ERR_ARG, "eps_lu must be >= 0");
+        H2_REQUIRE(o->norm_a > 0 && std::isfinite(o->norm_a), H2_ERR_ARG, "norm_a must be > 0");
+        H2_REQUIRE(o->precision == H2_PREC_FP64 || o->precision == H2_PREC_FP32, H2_ERR_ARG,
+                   "unknown precision");
+        Z = new h2_factor();
+        Z->f = make_factor(&A->m, *o);
+        Z->f->factorize();
+    });
+    if (rc != H2_OK) {
+        delete Z;
+        cudaStreamSynchronize(static_cast<cudaStream_t>(o ? o->stream : nullptr));
+        return rc;
+    }
+    *out = Z;
+    return H2_OK;
+}
+
+void h2_factor_destroy(h2_factor* Z) { delete Z; }
+
+int h2_solve(const h2_factor* Z, int32_t nrhs, double* b, int64_t ldb, int32_t on_device) {
+    return guard([&] {
+        H2_REQUIRE(Z && b && nrhs > 0, H2_ERR_ARG, "bad solve arguments");
+        FactorBase& F = *Z->f;
+        const int64_t n = F.A->H.n;
+        H2_REQUIRE(ldb >= n, H2_ERR_ARG, "ldb < n");
+        cudaStream_t s = F.stream;
+        if (on_device) {
+            F.solve_dev(b, nrhs, ldb);
+        } else {
+            DevBuf db;
+            db.alloc(n * nrhs * sizeof(double), s);
+            H2_CUDA_CHECK(cudaMemcpy2DAsync(db.ptr, n * sizeof(double), b, ldb * sizeof(double),
+                                            n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
+            F.solve_dev(db.as<double>(), nrhs, n);
+            H2_CUDA_CHECK(cudaMemcpy2DAsync(b, ldb * sizeof(double), db.ptr, n * sizeof(double),
+                                            n * sizeof(double), nrhs, cudaMemcpyDeviceToHost, s));
+        }
+        H2_CUDA_CHECK(cudaStreamSynchronize(s));
+    });
+}
+
+int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const double* b, int64_t ldb,
+                    double* x, int64_t ldx, double tol, int32_t maxit, int32_t on_device, int32_t* iters,
+                    double* berr) {
+    int converged = 1;
+    int rc = guard([&] {
+        H2_REQUIRE(Z && A && b && x && nrhs > 0 && maxit >= 0, H2_ERR_ARG, "bad refine arguments");
+        FactorBase& F = *Z->f;
+        H2_REQUIRE(F.A == &A->m, H2_ERR_ARG, "factor belongs to another matrix");
+        const int64_t n = A->m.H.n;
+        H2_REQUIRE(ldb >= n && ldx >= n, H2_ERR_ARG, "leading dimension < n");
+        cudaStream_t s = F.stream;
+        DevBuf db, dx, dy, dr, dn;
+        const double* bd = b;
+        double* xd = x;
+        int64_t lb = ldb, lx = ldx;
+        if (!on_device) {
+            db.alloc(n * nrhs * sizeof(double), s);
+            dx.alloc(n * nrhs * sizeof(double), s);
+            H2_CUDA_CHECK(cudaMemcpy2DAsync(db.ptr, n * sizeof(double), b, ldb * sizeof(double),
+                                            n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
+            bd = db.as<double>();
+            xd = dx.as<double>();
+            lb = lx = n;
+        }
+        dy.alloc(n * nrhs * sizeof(double), s);
+        dr.alloc(n * nrhs * sizeof(double), s);
+        dn.alloc(2 * nrhs * sizeof(double), s);
+        H2_CUDA_CHECK(cudaMemcpy2DAsync(xd, lx * sizeof(double), bd, lb * sizeof(double), n * sizeof(double),
+                                        nrhs, cudaMemcpyDeviceToDevice, s));
+        F.solve_dev(xd, nrhs, lx);
+        const double nA = F.norm_a_;
+        std::vector<double> h(2 * nrhs);
+        int it = 0;
+        double be = INFINITY;
+        for (;;) {
+            matvec_dev(A->m, nrhs, xd, lx, dy.as<double>(), n, s);
+            residual_dev(bd, lb, dy.as<double>(), n, dr.as<double>(), n, n, nrhs, s);
+            colnorm2_dev(dr.as<double>(), n, n, nrhs, dn.as<double>(), s);
+            colnorm2_dev(xd, lx, n, nrhs, dn.as<double>() + nrhs, s);
+            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+            H2_CUDA_CHECK(cudaStreamSynchronize(s));
+            be = 0;
+            for (int c = 0; c < nrhs; ++c) {
+                const double xn = std::sqrt(h[nrhs + c]);
+                const double e = xn > 0 ? std::sqrt(h[c]) / (nA * xn) : (h[c] > 0 ? INFINITY : 0.0);
+                be = std::max(be, e);
+            }
+            H2_REQUIRE(std::isfinite(be), H2_ERR_NONFINITE, "non-finite residual in refinement");
+            if (be <= tol || it >= maxit) break;
+            F.solve_dev(dr.as<double>(), nrhs, n);
+            add_dev(xd, lx, dr.as<double>(), n, n, nrhs, s);
+            ++it;
+        }
+        if (!on_device)
+            H2_CUDA_CHECK(cudaMemcpy2DAsync(x, ldx * sizeof(double), xd, n * sizeof(double), n * sizeof(double),
+                                            nrhs, cudaMemcpyDeviceToHost, s));
+        H2_CUDA_CHECK(cudaStreamSynchronize(s));
+        if (iters) *iters = it;
+        if (berr) *berr = be;
+        converged = be <= tol;
+    });
+    if (rc != H2_OK) return rc;
+    if (!converged) {
+        set_error("refinement did not reach the tolerance");
+        return H2_ERR_NO_CONVERGENCE;
+    }
+    return H2_OK;
+}
+
+int h2_factor_stats_get(const h2_factor* Z, h2_factor_stats* out) {
+    if (!Z || !out) { set_error("null argument"); return H2_ERR_ARG; }
+    *out = Z->f->stats;
+    return H2_OK;
+}
+
+int h2_layout_counts(const h2_factor* Z, int32_t level, int64_t* nbox, int64_t* nblk) {
+    if (!Z || level < 0 || level >= (int)Z->f->lay_sizes.size()) { set_error("bad level"); return H2_ERR_ARG; }
+    if (nbox) *nbox = (int64_t)Z->f->lay_sizes[level].size();
+    if (nblk) *nblk = (int64_t)Z->f->lay_col[level].size();
+    return H2_OK;
+}
+
+int h2_layout_get(const h2_factor* Z, int32_t level, int64_t* sizes, int64_t* ranks, int32_t* colour,
+                  int64_t* row_ptr, int64_t* col, int32_t* kind, int64_t* offset) {
+    if (!Z || level < 0 || level >= (int)Z->f->lay_sizes.size()) { set_error("bad level"); return H2_ERR_ARG; }
+    const FactorBase& F = *Z->f;
+    auto cp = [](auto* dst, const auto& src) {
+        if (dst) for (size_t q = 0; q < src.size(); ++q) dst[q] = src[q];
+    };
+    cp(sizes, F.lay_sizes[level]);
+    cp(ranks, F.lay_ranks[level]);
+    cp(colour, F.lay_colour[level]);
+    cp(row_ptr, F.lay_rowptr[level]);
+    cp(col, F.lay_col[level]);
+    cp(kind, F.lay_kind[level]);
+    cp(offset, F.lay_offset[level]);
+    return H2_OK;
+}
+
+int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
+                  int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind) {
+    return guard([&] {
+        HostStructure H;
+        read_structure(desc, H);
+        Plan P;
+        build_plan(H, P);
+        H2_REQUIRE(level >= 0 && level < (int)P.levels.size(), H2_ERR_ARG, "bad level");
+        const LevelStruct& S = P.levels[level];
+        if (nbox) *nbox = S.cnt;
+        if (nblk) *nblk = S.nblocks();
+        if (colour) for (int i = 0; i < S.cnt; ++i) colour[i] = S.colour[i];
+        if (row_ptr) for (int i = 0; i <= S.cnt; ++i) row_ptr[i] = S.bptr[i];
+        if (col) for (int b = 0; b < S.nblocks(); ++b) col[b] = S.bcol[b];
+        if (kind) for (int b = 0; b < S.nblocks(); ++b) kind[b] = S.bkind[b];
+    });
+}
+
+}  // extern "C"

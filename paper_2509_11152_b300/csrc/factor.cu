@@ -1,0 +1,693 @@
+// Factorisation driver (Alg. 1): levels from the leaves up, colours in order, the
+// batched kernels of Alg. 2 per colour, the level close, and the float64 dense LU of
+// the top level.  One host synchronisation per level reads back the augmented ranks,
+// which fix the sizes (and prefix-sum offsets) of the parent level.
+#include <algorithm>
+#include <numeric>
+
+#include "factor_impl.h"
+#include "factor_kernels.cuh"
+
+namespace h2rs {
+
+enum { PH_AUG = 0, PH_PROJ = 1, PH_LU = 2, PH_SCHUR = 3, PH_CLOSE = 4, PH_TOP = 5, PH_LOAD = 6,
+       PH_OTHER = 7 };
+
+
+template <class T>
+static LevelArgs<T> args_of(LevelRT& L, DevStatus* st) {
+    LevelArgs<T> a{};
+    a.level = L.l;
+    a.cnt = L.cnt;
+    a.n = L.d_n.as<int>();
+    a.k = L.d_k.as<int>();
+    a.kt = L.d_kt.as<int>();
+    a.colour = L.d_colour.as<int>();
+    a.blk_off = L.d_blk_off.as<int64_t>();
+    a.brow = L.d_brow.as<int>();
+    a.bcol = L.d_bcol.as<int>();
+    a.blk = L.blk.as<T>();
+    a.V_off = L.d_V_off.as<int64_t>();
+    a.V = L.V.as<T>();
+    a.Q_off = L.d_Q_off.as<int64_t>();
+    a.Q = L.Q.as<T>();
+    a.LU_off = L.d_LU_off.as<int64_t>();
+    a.LU = L.LU.as<T>();
+    a.piv_off = L.d_piv_off.as<int64_t>();
+    a.piv = L.piv.as<int>();
+    a.WU_off = L.d_WU_off.as<int64_t>();
+    a.WU = L.WU.as<T>();
+    a.WL_off = L.d_WL_off.as<int64_t>();
+    a.WL = L.WL.as<T>();
+    a.WLld = L.d_WLld.as<int>();
+    a.nb_ptr = L.d_nb_ptr.as<int>();
+    a.nb_col = L.d_nb_col.as<int>();
+    a.nbofs = L.d_nbofs.as<int>();
+    a.Nsum = L.d_Nsum.as<int>();
+    a.nb_blk = L.d_nb_blk.as<int>();
+    a.nb_blkT = L.d_nb_blkT.as<int>();
+    a.diag_blk = L.d_diag_blk.as<int>();
+    a.status = st;
+    return a;
+}
+
+// Raise a kernel's dynamic shared memory limit to what the device allows beside the
+// kernel's static shared memory; returns that limit.
+template <class K>
+static int raise_smem(K kern) {
+    int dev = 0, optin = 0;
+    H2_CUDA_CHECK(cudaGetDevice(&dev));
+    H2_CUDA_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    H2_CUDA_CHECK(cudaFuncGetAttributes(&fa, kern));
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    H2_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return lim;
+}
+
+template <class T>
+struct SmemLimits {
+    int basis, lu, proj_l, proj_r, gather, trsm_u, trsm_l;
+};
+
+template <class T>
+static const SmemLimits<T>& smem_limits() {
+    static SmemLimits<T> lim = [] {
+        SmemLimits<T> x{};
+        x.basis = raise_smem(k_basis<T>);
+        x.lu = raise_smem(k_lu<T>);
+        x.proj_l = raise_smem(k_proj_left<T>);
+        x.proj_r = raise_smem(k_proj_right<T>);
+        x.gather = raise_smem(k_aug_gather<T>);
+        x.trsm_u = raise_smem(k_trsm_u<T>);
+        x.trsm_l = raise_smem(k_trsm_l<T>);
+        return x;
+    }();
+    return lim;
+}
+
+// every launch is checked before anything that depends on it is enqueued
+#define H2_LAUNCHED() H2_CUDA_CHECK(cudaGetLastError())
+
+template <class T>
+FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
+    (void)smem_limits<T>();
+    A = A_;
+    eps_lu = o.eps_lu;
+    norm_a = o.norm_a;
+    norm_a_ = o.norm_a;
+    precision = o.precision;
+    stream = static_cast<cudaStream_t>(o.stream);
+    status.alloc(sizeof(DevStatus), stream);
+}
+
+template <class T>
+FactorImpl<T>::~FactorImpl() {
+    for (auto e : ev) cudaEventDestroy(e);
+}
+
+template <class T>
+void FactorImpl<T>::mark(int phase) {
+    cudaEvent_t e;
+    H2_CUDA_CHECK(cudaEventCreate(&e));
+    H2_CUDA_CHECK(cudaEventRecord(e, stream));
+    ev.push_back(e);
+    ev_phase.push_back(phase);
+}
+
+template <class T>
+void FactorImpl<T>::check_status(const char* where) {
+    DevStatus h{};
+    H2_CUDA_CHECK(cudaMemcpyAsync(&h, status.ptr, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    H2_CUDA_CHECK(cudaStreamSynchronize(stream));
+    H2_CUDA_CHECK(cudaGetLastError());
+    if (h.code != 0) {
+        stats.error_level = h.level;
+        stats.error_box = h.box;
+        throw Error{h.code, std::string(where) + ": device status " + std::to_string(h.code) +
+                                " at level " + std::to_string(h.level) + " box " +
+                                std::to_string(h.box)};
+    }
+}
+
+template <class T>
+static int64_t track(FactorImpl<T>* F, DevBuf& b, size_t bytes, cudaStream_t s) {
+    b.alloc(bytes, s);
+    F->bytes_now += (int64_t)bytes;
+    F->stats.peak_bytes = std::max(F->stats.peak_bytes, F->bytes_now);
+    return (int64_t)bytes;
+}
+
+template <class T>
+static void untrack(FactorImpl<T>* F, DevBuf& b) {
+    F->bytes_now -= (int64_t)b.bytes;
+    b.release();
+}
+
+// ------------------------------------------------------------------ level setup
+template <class T>
+void FactorImpl<T>::setup_level(size_t a) {
+    const Plan& P = A->plan;
+    const HostStructure& H = A->H;
+    const bool is_top = a == P.levels.size();
+    const LevelStruct& S = is_top ? P.toplev : P.levels[a];
+    LevelRT& L = lv[a];
+    L.S = &S;
+    L.l = S.l;
+    L.cnt = S.cnt;
+    L.n.assign(S.cnt, 0);
+    L.k.assign(S.cnt, 0);
+    for (int i = 0; i < S.cnt; ++i) {
+        if (a == 0 && S.l == H.d) L.n[i] = (int)H.node_size[S.first + i];
+        else L.n[i] = lv[a - 1].kt[2 * i] + lv[a - 1].kt[2 * i + 1];
+        L.k[i] = (int)H.rank[S.first + i];
+    }
+    const int nb = S.nblocks();
+    L.brow.resize(nb);
+    L.blk_off.assign(nb + 1, 0);
+    for (int i = 0; i < S.cnt; ++i)
+        for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
+            L.brow[b] = i;
+            L.blk_off[b + 1] = L.blk_off[b] + (int64_t)L.n[i] * L.n[S.bcol[b]];
+        }
+    auto prefix = [&](std::vector<int64_t>& off, auto f) {
+        off.assign(S.cnt + 1, 0);
+        for (int i = 0; i < S.cnt; ++i) off[i + 1] = off[i] + f(i);
+    };
+    prefix(L.V_off, [&](int i) { return (int64_t)L.n[i] * L.k[i]; });
+    prefix(L.voff, [&](int i) { return (int64_t)L.n[i]; });
+    L.vtot = L.voff[S.cnt];
+    cudaStream_t s = stream;
+    upload(L.d_n, L.n, s);
+    upload(L.d_k, L.k, s);
+    upload(L.d_colour, S.colour, s);
+    upload(L.d_blk_off, L.blk_off, s);
+    upload(L.d_brow, L.brow, s);
+    upload(L.d_bcol, S.bcol, s);
+    upload(L.d_V_off, L.V_off, s);
+    upload(L.d_voff, L.voff, s);
+    L.kt.assign(S.cnt, 0);
+    upload(L.d_kt, L.kt, s);
+    track(this, L.blk, std::max<int64_t>(1, L.blk_off[nb]) * sizeof(T), s);
+    if (is_top) return;
+    track(this, L.V, std::max<int64_t>(1, L.V_off[S.cnt]) * sizeof(T), s);
+    prefix(L.Q_off, [&](int i) { return (int64_t)L.n[i] * L.n[i]; });
+    L.LU_off = L.Q_off;
+    prefix(L.piv_off, [&](int i) { return (int64_t)L.n[i]; });
+    L.Nsum.assign(S.cnt, 0);
+    L.nbofs.assign(S.nb_col.size(), 0);
+    L.diag_blk.assign(S.cnt, -1);
+    for (int i = 0; i < S.cnt; ++i) {
+        int o = 0;
+        for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
+            if (S.nb_col[p] != i) { L.nbofs[p] = o; o += L.n[S.nb_col[p]]; }
+        L.Nsum[i] = o;
+        for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
+            if (S.nb_col[p] == i) L.nbofs[p] = o;
+        L.diag_blk[i] = S.find(i, i);
+    }
+    L.WLld.resize(S.cnt);
+    for (int i = 0; i < S.cnt; ++i) L.WLld[i] = L.Nsum[i] + L.n[i];
+    prefix(L.WU_off, [&](int i) { return (int64_t)L.n[i] * L.WLld[i]; });
+    L.WL_off = L.WU_off;
+    upload(L.d_Q_off, L.Q_off, s);
+    upload(L.d_LU_off, L.LU_off, s);
+    upload(L.d_piv_off, L.piv_off, s);
+    upload(L.d_WU_off, L.WU_off, s);
+    upload(L.d_WL_off, L.WL_off, s);
+    upload(L.d_WLld, L.WLld, s);
+    upload(L.d_nb_ptr, S.nb_ptr, s);
+    upload(L.d_nb_col, S.nb_col, s);
+    upload(L.d_nbofs, L.nbofs, s);
+    upload(L.d_Nsum, L.Nsum, s);
+    upload(L.d_nb_blk, S.nb_blk, s);
+    upload(L.d_nb_blkT, S.nb_blkT, s);
+    upload(L.d_diag_blk, L.diag_blk, s);
+    upload(L.d_fl_tbox, S.fl_tbox, s);
+    upload(L.d_fl_tptr, S.fl_tptr, s);
+    upload(L.d_fl_ci, S.fl_ci, s);
+    upload(L.d_fl_cpos, S.fl_cpos, s);
+    track(this, L.Q, std::max<int64_t>(1, L.Q_off[S.cnt]) * sizeof(T), s);
+    track(this, L.LU, std::max<int64_t>(1, L.LU_off[S.cnt]) * sizeof(T), s);
+    track(this, L.piv, std::max<int64_t>(1, L.piv_off[S.cnt]) * sizeof(int), s);
+    track(this, L.WU, std::max<int64_t>(1, L.WU_off[S.cnt]) * sizeof(T), s);
+    track(this, L.WL, std::max<int64_t>(1, L.WL_off[S.cnt]) * sizeof(T), s);
+}
+
+// per-colour work lists of one level (host built, uploaded once)
+struct ColourWork {
+    // basis
+    std::vector<int> boxes, box_cptr;                      // boxes per colour
+    std::vector<int> seg_ptr, seg_blk, seg_j, seg_slot, seg_cptr;
+    std::vector<int64_t> seg_yoff, ybase, ylead, wbase;
+    std::vector<int64_t> scratch_need;                     // per colour (elements)
+    std::vector<int> smem_basis, w_in_smem, smem_gather, nmax;
+    // projection / zeroing
+    std::vector<int> pl_box, pl_blk, pl_pan, pl_cptr;
+    std::vector<int> pr_box, pr_blk, pr_pan, pr_cptr;
+    std::vector<int> zf_box, zf_blk, zf_col, zf_cptr;
+    std::vector<int> zn_box, zn_blk, zn_col, zn_cptr;
+    // trsm
+    std::vector<int> tu_box, tu_c0, tu_cptr;
+    // schur tiles
+    std::vector<int> tile_tgt, tile_mn, tile_cptr;
+};
+
+template <class T>
+void FactorImpl<T>::run_level(size_t a) {
+    LevelRT& L = lv[a];
+    const LevelStruct& S = *L.S;
+    const MatrixObj& M = *A;
+    cudaStream_t s = stream;
+    LevelArgs<T> ar = args_of<T>(L, status.as<DevStatus>());
+    if (a == 0) {
+        DevBuf d_near;
+        upload(d_near, S.near_entry, s);
+        k_leaf_load<T><<<S.nblocks(), 256, 0, s>>>(ar, M.D.as<double>(), M.d_D_off.as<int64_t>(),
+                                                 d_near.as<int64_t>());
+        H2_LAUNCHED();
+        std::vector<int64_t> uoff(M.H.U_off.begin(), M.H.U_off.end());
+        DevBuf d_uoff;
+        upload(d_uoff, uoff, s);
+        k_leaf_basis<T><<<S.cnt, 256, 0, s>>>(ar, L.V.as<T>(), M.U.as<double>(), d_uoff.as<int64_t>());
+        H2_LAUNCHED();
+        H2_CUDA_CHECK(cudaGetLastError());
+        mark(PH_LOAD);
+        double bytes = 0;
+        for (int b = 0; b < S.nblocks(); ++b)
+            bytes += (double)(L.blk_off[b + 1] - L.blk_off[b]) * (S.bkind[b] == 0 ? 8 + sizeof(T) : sizeof(T));
+        account(PH_LOAD, 0, bytes);
+    }
+    // ---------------- work lists
+    ColourWork W;
+    const int nc = S.ncolour;
+    W.box_cptr.push_back(0);
+    W.seg_cptr.push_back(0);
+    W.pl_cptr.push_back(0);
+    W.pr_cptr.push_back(0);
+    W.zf_cptr.push_back(0);
+    W.zn_cptr.push_back(0);
+    W.tu_cptr.push_back(0);
+    W.tile_cptr.push_back(0);
+    W.seg_ptr.push_back(0);
+    const int PW = 32;
+    for (int c = 0; c < nc; ++c) {
+        int64_t ysum = 0, wsum = 0;
+        int nmax = 0, gsm = 0, csz = 0;
+        const size_t wfirst = W.wbase.size();
+        for (int i : S.cboxes[c]) {
+            const int slot = (int)W.boxes.size();
+            W.boxes.push_back(i);
+            const int n = L.n[i];
+            nmax = std::max(nmax, n);
+            int64_t yrows = 0;
+            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
+                if (S.bkind[b] != 1 || S.first_touch[b] >= c) continue;
+                W.seg_blk.push_back(b);
+                W.seg_j.push_back(S.bcol[b]);
+                W.seg_yoff.push_back(yrows);
+                W.seg_slot.push_back(slot - W.box_cptr[c]);
+                yrows += L.n[S.bcol[b]];
+            }
+            W.seg_ptr.push_back((int)W.seg_blk.size());
+            W.ybase.push_back(ysum);
+            W.ylead.push_back(yrows);
+            ysum += yrows * n;
+            W.wbase.push_back(wsum);
+            wsum += (int64_t)n * n;
+            gsm = std::max(gsm, (int)((n + L.k[i]) * 16 * sizeof(T)));
+            const int CH = n <= 192 ? 64 : 32;
+            csz = std::max(csz, CH * n);
+            // projection pairs (near blocks + fill blocks already holding fill)
+            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
+                const bool live = S.bkind[b] == 0 || S.first_touch[b] < c;
+                if (!live) continue;
+                const int j = S.bcol[b];
+                const int bt = S.btr[b];
+                for (int p = 0; p * PW < L.n[j]; ++p) {
+                    W.pl_box.push_back(i); W.pl_blk.push_back(b); W.pl_pan.push_back(p);
+                    W.pr_box.push_back(i); W.pr_blk.push_back(bt); W.pr_pan.push_back(p);
+                }
+                if (S.bkind[b] == 1) {
+                    W.zf_box.push_back(i); W.zf_blk.push_back(b); W.zf_col.push_back(0);
+                    W.zf_box.push_back(i); W.zf_blk.push_back(bt); W.zf_col.push_back(1);
+                } else {
+                    W.zn_box.push_back(i); W.zn_blk.push_back(b); W.zn_col.push_back(0);
+                    W.zn_box.push_back(i); W.zn_blk.push_back(bt); W.zn_col.push_back(1);
+                }
+            }
+            for (int c0 = 0; c0 < L.Nsum[i] + n; c0 += 8) {
+                W.tu_box.push_back(i);
+                W.tu_c0.push_back(c0);
+            }
+        }
+        for (size_t q = wfirst; q < W.wbase.size(); ++q) W.wbase[q] += ysum;   // after the Y^T rows
+        W.box_cptr.push_back((int)W.boxes.size());
+        W.seg_cptr.push_back((int)W.seg_blk.size());
+        W.pl_cptr.push_back((int)W.pl_box.size());
+        W.pr_cptr.push_back((int)W.pr_box.size());
+        W.zf_cptr.push_back((int)W.zf_box.size());
+        W.zn_cptr.push_back((int)W.zn_box.size());
+        W.tu_cptr.push_back((int)W.tu_box.size());
+        // schur tiles
+        for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
+            const int tb = S.sch_tblk[t];
+            const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
+            for (int tm = 0; tm * 64 < m; ++tm)
+                for (int tn = 0; tn * 64 < nn; ++tn) {
+                    W.tile_tgt.push_back(t);
+                    W.tile_mn.push_back((tm << 16) | tn);
+                }
+        }
+        W.tile_cptr.push_back((int)W.tile_tgt.size());
+        const size_t base = (size_t)(csz + 2 * nmax + 33) * sizeof(T) + 16;
+        const size_t wsm = (size_t)nmax * nmax * sizeof(T);
+        const auto& lim = smem_limits<T>();
+        H2_REQUIRE(base <= (size_t)lim.basis && (size_t)gsm <= (size_t)lim.gather &&
+                       (size_t)nmax * 32 * sizeof(T) <= (size_t)std::min(lim.proj_l, lim.proj_r),
+                   H2_ERR_ARG, "box size too large for the shared-memory kernels");
+        const int in_sm = base + wsm <= (size_t)lim.basis;
+        W.w_in_smem.push_back(in_sm);
+        W.smem_basis.push_back((int)(base + (in_sm ? wsm : 0)));
+        W.smem_gather.push_back(gsm);
+        W.nmax.push_back(nmax);
+        W.scratch_need.push_back(ysum + (in_sm ? 0 : wsum));
+    }
+    int64_t scratch_max = 1;
+    for (auto v : W.scratch_need) scratch_max = std::max(scratch_max, v);
+    DevBuf scratch;
+    track(this, scratch, scratch_max * sizeof(T), s);
+    // seg_ptr is per box (global over colours): make it per-colour local
+    DevBuf d_boxes, d_seg_ptr, d_seg_blk, d_seg_j, d_seg_slot, d_seg_yoff, d_ybase, d_ylead, d_wbase;
+    DevBuf d_pl_box, d_pl_blk, d_pl_pan, d_pr_box, d_pr_blk, d_pr_pan;
+    DevBuf d_zf_box, d_zf_blk, d_zf_col, d_zn_box, d_zn_blk, d_zn_col, d_tu_box, d_tu_c0;
+    DevBuf d_tile_tgt, d_tile_mn, d_tgt_blk, d_tgt_ptr, d_c_box, d_c_ablk, d_c_kpos;
+    upload(d_boxes, W.boxes, s);
+    upload(d_seg_ptr, W.seg_ptr, s);
+    upload(d_seg_blk, W.seg_blk, s);
+    upload(d_seg_j, W.seg_j, s);
+    upload(d_seg_slot, W.seg_slot, s);
+    upload(d_seg_yoff, W.seg_yoff, s);
+    upload(d_ybase, W.ybase, s);
+    upload(d_ylead, W.ylead, s);
+    upload(d_wbase, W.wbase, s);
+    upload(d_pl_box, W.pl_box, s);
+    upload(d_pl_blk, W.pl_blk, s);
+    upload(d_pl_pan, W.pl_pan, s);
+    upload(d_pr_box, W.pr_box, s);
+    upload(d_pr_blk, W.pr_blk, s);
+    upload(d_pr_pan, W.pr_pan, s);
+    upload(d_zf_box, W.zf_box, s);
+    upload(d_zf_blk, W.zf_blk, s);
+    upload(d_zf_col, W.zf_col, s);
+    upload(d_zn_box, W.zn_box, s);
+    upload(d_zn_blk, W.zn_blk, s);
+    upload(d_zn_col, W.zn_col, s);
+    upload(d_tu_box, W.tu_box, s);
+    upload(d_tu_c0, W.tu_c0, s);
+    upload(d_tile_tgt, W.tile_tgt, s);
+    upload(d_tile_mn, W.tile_mn, s);
+    upload(d_tgt_blk, S.sch_tblk, s);
+    upload(d_tgt_ptr, S.sch_tptr, s);
+    upload(d_c_box, S.sch_ci, s);
+    upload(d_c_ablk, S.sch_cA, s);
+    upload(d_c_kpos, S.sch_ckpos, s);
+    int nmax_level = 1;
+    for (int v : L.n) nmax_level = std::max(nmax_level, v);
+    const T eps_fill = (T)(eps_lu * norm_a);
+    for (int c = 0; c < nc; ++c) {
+        const int b0 = W.box_cptr[c], nbx = W.box_cptr[c + 1] - b0;
+        if (nbx == 0) continue;
+        ColourLists CL{};
+        CL.boxes = d_boxes.as<int>() + b0;
+        CL.seg_ptr = d_seg_ptr.as<int>() + b0;      // per-box pointers into global seg arrays
+        CL.seg_blk = d_seg_blk.as<int>();
+        CL.seg_j = d_seg_j.as<int>();
+        CL.seg_yoff = d_seg_yoff.as<int64_t>();
+        CL.ybase = d_ybase.as<int64_t>() + b0;
+        CL.ylead = d_ylead.as<int64_t>() + b0;
+        CL.wbase = d_wbase.as<int64_t>() + b0;
+        const int s0 = W.seg_cptr[c], ns = W.seg_cptr[c + 1] - s0;
+        // ---- augmentation
+        if (ns > 0) {
+            ColourLists CG = CL;
+            CG.seg_blk = d_seg_blk.as<int>() + s0;
+            CG.seg_j = d_seg_j.as<int>() + s0;
+            CG.seg_yoff = d_seg_yoff.as<int64_t>() + s0;
+            k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, d_seg_slot.as<int>() + s0,
+                                                              scratch.as<T>());
+            H2_LAUNCHED();
+        }
+        k_basis<T><<<nbx, 256, W.smem_basis[c], s>>>(ar, CL, c, scratch.as<T>(), scratch.as<T>(),
+                                                     eps_fill, W.w_in_smem[c]);
+        H2_LAUNCHED();
+        H2_CUDA_CHECK(cudaGetLastError());
+        mark(PH_AUG);
+        // ---- projection + fill truncation
+        const int pl0 = W.pl_cptr[c], npl = W.pl_cptr[c + 1] - pl0;
+        const int pr0 = W.pr_cptr[c], npr = W.pr_cptr[c + 1] - pr0;
+        const int smp = W.nmax[c] * PW * (int)sizeof(T);
+        if (npl) k_proj_left<T><<<npl, 256, smp, s>>>(ar, d_pl_box.as<int>() + pl0, d_pl_blk.as<int>() + pl0,
+                                                      d_pl_pan.as<int>() + pl0);
+        H2_LAUNCHED();
+        if (npr) k_proj_right<T><<<npr, 256, smp, s>>>(ar, d_pr_box.as<int>() + pr0, d_pr_blk.as<int>() + pr0,
+                                                       d_pr_pan.as<int>() + pr0);
+        H2_LAUNCHED();
+        const int zf0 = W.zf_cptr[c], nzf = W.zf_cptr[c + 1] - zf0;
+        if (nzf) k_zero_redundant<T><<<nzf, 256, 0, s>>>(ar, d_zf_box.as<int>() + zf0, d_zf_blk.as<int>() + zf0,
+                                                        d_zf_col.as<int>() + zf0);
+        H2_LAUNCHED();
+        H2_CUDA_CHECK(cudaGetLastError());
+        mark(PH_PROJ);
+        // ---- partial LU + triangular solves
+        const size_t lu_sm = (size_t)W.nmax[c] * W.nmax[c] * sizeof(T);
+        const int lu_in = lu_sm <= (size_t)smem_limits<T>().lu;
+        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, d_boxes.as<int>() + b0, lu_in);
+        H2_LAUNCHED();
+        const int tu0 = W.tu_cptr[c], ntu = W.tu_cptr[c + 1] - tu0;
+        const int tsm = 8 * W.nmax[c] * (int)sizeof(T);
+        if (ntu) {
+            k_trsm_u<T><<<ntu, 256, tsm, s>>>(ar, d_tu_box.as<int>() + tu0, d_tu_c0.as<int>() + tu0);
+            H2_LAUNCHED();
+            k_trsm_l<T><<<ntu, 256, tsm, s>>>(ar, d_tu_box.as<int>() + tu0, d_tu_c0.as<int>() + tu0);
+            H2_LAUNCHED();
+        }
+        H2_CUDA_CHECK(cudaGetLastError());
+        mark(PH_LU);
+        // ---- Schur update and zeroing of the eliminated rows / columns
+        const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
+        if (ntile)
+            k_schur<T><<<ntile, 256, 0, s>>>(ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(),
+                                             d_c_box.as<int>(), d_c_ablk.as<int>(), d_c_kpos.as<int>(),
+                                             d_tile_tgt.as<int>() + t0, d_tile_mn.as<int>() + t0);
+            H2_LAUNCHED();
+        const int zn0 = W.zn_cptr[c], nzn = W.zn_cptr[c + 1] - zn0;
+        if (nzn) k_zero_redundant<T><<<nzn, 256, 0, s>>>(ar, d_zn_box.as<int>() + zn0, d_zn_blk.as<int>() + zn0,
+                                                        d_zn_col.as<int>() + zn0);
+        H2_LAUNCHED();
+        H2_CUDA_CHECK(cudaGetLastError());
+        mark(PH_SCHUR);
+    }
+    // ---------------- ranks back to the host (sizes of the parent level)
+    check_status("factorize level");
+    H2_CUDA_CHECK(cudaMemcpyAsync(L.kt.data(), L.d_kt.ptr, L.cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H2_CUDA_CHECK(cudaStreamSynchronize(s));
+    untrack(this, scratch);
+    // ---------------- algorithmic counts of this level (for roofline fractions)
+    const double w = sizeof(T);
+    for (int c = 0; c < nc; ++c) {
+        for (int i : S.cboxes[c]) {
+            const double n = L.n[i], kt = L.kt[i], r = n - kt;
+            double live = 0;
+            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b)
+                if (S.bkind[b] == 1 && S.first_touch[b] < c) {
+                    const int j = S.bcol[b];
+                    live += (S.colour[j] < c) ? L.kt[j] : L.n[j];
+                }
+            account(PH_AUG, 4.0 * n * L.k[i] * live + 2.0 * live * n * n + 4.0 * n * n * kt,
+                    w * (live * n + n * n));
+            double nsum = 0, pbytes = 0;
+            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
+                const bool lv_ = S.bkind[b] == 0 || S.first_touch[b] < c;
+                if (!lv_) continue;
+                const double nj = L.n[S.bcol[b]];
+                pbytes += 4.0 * n * nj * w;
+                account(PH_PROJ, 4.0 * n * n * nj, 0);
+            }
+            account(PH_PROJ, 0, pbytes + n * n * w);
+            for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
+                if (S.nb_col[p] != i) nsum += L.n[S.nb_col[p]];
+            const double ncol = nsum + kt;
+            account(PH_LU, 2.0 / 3.0 * r * r * r + 4.0 * r * r * ncol, w * (4.0 * r * ncol + r * r));
+        }
+        for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
+            const int tb = S.sch_tblk[t];
+            const int j = L.brow[tb], kk = S.bcol[tb];
+            const double m = L.n[j] - (S.colour[j] == c ? L.n[j] - L.kt[j] : 0);
+            const double nn = L.n[kk] - (S.colour[kk] == c ? L.n[kk] - L.kt[kk] : 0);
+            double fl = 0, by = 2.0 * m * nn * w;
+            for (int e = S.sch_tptr[t]; e < S.sch_tptr[t + 1]; ++e) {
+                const int i = S.sch_ci[e];
+                const double r = L.n[i] - L.kt[i];
+                fl += 2.0 * m * nn * r;
+                by += w * r * (m + nn);
+            }
+            account(PH_SCHUR, fl, by);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ level close
+template <class T>
+void FactorImpl<T>::close_level(size_t a) {
+    LevelRT& L = lv[a];
+    LevelRT& Pn = lv[a + 1];
+    const LevelStruct& S = *L.S;
+    const MatrixObj& M = *A;
+    cudaStream_t s = stream;
+    LevelArgs<T> ar = args_of<T>(L, status.as<DevStatus>());
+    DevBuf d_cd, d_cf, d_ca;
+    upload(d_cd, S.cl_dblk, s);
+    upload(d_cf, S.cl_fblk, s);
+    upload(d_ca, S.cl_adm, s);
+    const int nbp = Pn.S->nblocks();
+    if (nbp)
+        k_close_blocks<T><<<nbp, 256, 0, s>>>(ar, Pn.blk.as<T>(), Pn.d_blk_off.as<int64_t>(),
+                                              Pn.d_brow.as<int>(), Pn.d_bcol.as<int>(), d_cd.as<int>(),
+                                              d_cf.as<int>(), d_ca.as<int64_t>(), M.S.as<double>(),
+                                              M.d_S_off.as<int64_t>());
+        H2_LAUNCHED();
+    if (a + 1 < lv.size() - 1)
+        k_close_basis<T><<<Pn.cnt, 256, 0, s>>>(ar, Pn.V.as<T>(), Pn.d_V_off.as<int64_t>(),
+                                                Pn.d_k.as<int>(), M.E.as<double>(),
+                                                M.d_E_off.as<int64_t>(), L.S->first);
+        H2_LAUNCHED();
+    H2_CUDA_CHECK(cudaGetLastError());
+    mark(PH_CLOSE);
+    account(PH_CLOSE, 0, 2.0 * sizeof(T) * (double)Pn.blk_off.back());
+    untrack(this, L.blk);
+    untrack(this, L.V);
+}
+
+// ------------------------------------------------------------------ top level
+template <class T>
+void FactorImpl<T>::top_factor() {
+    const Plan& P = A->plan;
+    const MatrixObj& M = *A;
+    cudaStream_t s = stream;
+    LevelRT& Tl = lv.back();
+    const LevelStruct& S = *Tl.S;
+    tn = Tl.n;
+    toff.assign(S.cnt + 1, 0);
+    for (int i = 0; i < S.cnt; ++i) toff[i + 1] = toff[i] + tn[i];
+    nt = toff[S.cnt];
+    upload(d_toff, toff, s);
+    track(this, Dt, std::max<int64_t>(1, nt * nt) * sizeof(double), s);
+    track(this, tpiv, std::max<int64_t>(1, nt) * sizeof(int), s);
+    H2_CUDA_CHECK(cudaMemsetAsync(Dt.ptr, 0, std::max<int64_t>(1, nt * nt) * sizeof(double), s));
+    if (nt > 0) {
+        if (P.top < 0) {
+            std::vector<int64_t> off(S.nblocks());
+            for (int b = 0; b < S.nblocks(); ++b) off[b] = M.H.D_off[S.near_entry[b]];
+            DevBuf d_off;
+            upload(d_off, off, s);
+            k_top_assemble<double><<<S.nblocks(), 256, 0, s>>>(M.D.as<double>(), d_off.as<int64_t>(),
+                                                               Tl.d_brow.as<int>(), Tl.d_bcol.as<int>(),
+                                                               Tl.d_n.as<int>(), d_toff.as<int64_t>(),
+                                                               Dt.as<double>(), nt);
+            H2_LAUNCHED();
+        } else {
+            k_top_assemble<T><<<S.nblocks(), 256, 0, s>>>(Tl.blk.as<T>(), Tl.d_blk_off.as<int64_t>(),
+                                                          Tl.d_brow.as<int>(), Tl.d_bcol.as<int>(),
+                                                          Tl.d_n.as<int>(), d_toff.as<int64_t>(),
+                                                          Dt.as<double>(), nt);
+            H2_LAUNCHED();
+        }
+        H2_CUDA_CHECK(cudaGetLastError());
+        const int NB = 64;
+        for (int64_t j0 = 0; j0 < nt; j0 += NB) {
+            const int jb = (int)std::min<int64_t>(NB, nt - j0);
+            k_top_panel<<<1, 1024, 0, s>>>(Dt.as<double>(), nt, j0, jb, tpiv.as<int>(), status.as<DevStatus>());
+            H2_LAUNCHED();
+            k_top_swap<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(Dt.as<double>(), nt, j0, jb, tpiv.as<int>());
+            H2_LAUNCHED();
+            const int64_t rest = nt - j0 - jb;
+            if (rest > 0) {
+                k_top_trsm<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(Dt.as<double>(), nt, j0, jb);
+                H2_LAUNCHED();
+                dim3 g((unsigned)((rest + 63) / 64), (unsigned)((rest + 63) / 64));
+                k_top_gemm<<<g, 256, 0, s>>>(Dt.as<double>(), nt, j0, jb);
+                H2_LAUNCHED();
+            }
+        }
+        H2_CUDA_CHECK(cudaGetLastError());
+    }
+    untrack(this, Tl.blk);
+    mark(PH_TOP);
+    account(PH_TOP, 2.0 / 3.0 * (double)nt * nt * nt, 16.0 * (double)nt * nt);
+    check_status("top-level LU");
+}
+
+template <class T>
+void FactorImpl<T>::factorize() {
+    const Plan& P = A->plan;
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    ev_phase.clear();
+    for (int p = 0; p < 8; ++p) stats.phase_ms[p] = stats.phase_flops[p] = stats.phase_bytes[p] = 0;
+    stats.error_level = stats.error_box = -1;
+    H2_CUDA_CHECK(cudaMemsetAsync(status.ptr, 0, sizeof(DevStatus), stream));
+    lv.clear();
+    lv.resize(P.levels.size() + 1);
+    bytes_now = 0;
+    stats.peak_bytes = 0;
+    mark(-1);
+    setup_level(0);
+    for (size_t a = 0; a < P.levels.size(); ++a) {
+        run_level(a);
+        setup_level(a + 1);
+        close_level(a);
+    }
+    top_factor();
+    H2_CUDA_CHECK(cudaStreamSynchronize(stream));
+    float total = 0;
+    for (size_t e = 1; e < ev.size(); ++e) {
+        float ms = 0;
+        H2_CUDA_CHECK(cudaEventElapsedTime(&ms, ev[e - 1], ev[e]));
+        const int ph = ev_phase[e] >= 0 ? ev_phase[e] : PH_OTHER;
+        stats.phase_ms[ph] += ms;
+        total += ms;
+    }
+    stats.factor_ms = total;
+    stats.nlevels = (int)P.levels.size();
+    stats.top_level = P.top;
+    stats.top_size = nt;
+    int64_t fb = 0;
+    for (auto& L : lv) fb += L.Q.bytes + L.LU.bytes + L.piv.bytes + L.WU.bytes + L.WL.bytes;
+    fb += Dt.bytes + tpiv.bytes;
+    stats.factor_bytes = fb;
+    // layout export (levels 0 .. nlevels-1)
+    lay_sizes.clear(); lay_ranks.clear(); lay_rowptr.clear(); lay_col.clear(); lay_offset.clear();
+    lay_colour.clear(); lay_kind.clear();
+    for (size_t a = 0; a < P.levels.size(); ++a) {
+        const LevelRT& L = lv[a];
+        const LevelStruct& S = *L.S;
+        lay_sizes.emplace_back(L.n.begin(), L.n.end());
+        lay_ranks.emplace_back(L.kt.begin(), L.kt.end());
+        lay_rowptr.emplace_back(S.bptr.begin(), S.bptr.end());
+        lay_col.emplace_back(S.bcol.begin(), S.bcol.end());
+        lay_offset.emplace_back(L.blk_off.begin(), L.blk_off.end());
+        lay_colour.emplace_back(S.colour.begin(), S.colour.end());
+        lay_kind.emplace_back(S.bkind.begin(), S.bkind.end());
+    }
+}
+
+std::unique_ptr<FactorBase> make_factor(const MatrixObj* A, const h2_factor_opts& o) {
+    if (o.precision == H2_PREC_FP32) return std::make_unique<FactorImpl<float>>(A, o);
+    return std::make_unique<FactorImpl<double>>(A, o);
+}
+
+template struct FactorImpl<double>;
+template struct FactorImpl<float>;
+
+}  // namespace h2rs

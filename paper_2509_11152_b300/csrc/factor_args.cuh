@@ -1,0 +1,65 @@
+// Device kernels of the factorisation (templated on the working type T).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "h2rs_internal.h"
+
+namespace h2rs {
+
+template <class T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
+template <> struct Eps<float> { static constexpr float v = FLT_EPSILON; };
+
+// Per-level device view shared by the kernels.
+template <class T>
+struct LevelArgs {
+    int level;
+    int cnt;
+    const int* n;          // box sizes
+    const int* k;          // basis ranks before augmentation
+    int* kt;               // augmented ranks (written by the basis kernel)
+    const int* colour;
+    const int64_t* blk_off;
+    const int* brow;
+    const int* bcol;
+    T* blk;
+    const int64_t* V_off;
+    const T* V;
+    const int64_t* Q_off;
+    T* Q;
+    const int64_t* LU_off;
+    T* LU;
+    const int64_t* piv_off;
+    int* piv;
+    const int64_t* WU_off;
+    T* WU;
+    const int64_t* WL_off;
+    T* WL;
+    const int* WLld;
+    const int* nb_ptr;
+    const int* nb_col;
+    const int* nbofs;      // column offset of neighbour (by N(i) position) in W_U^i
+    const int* Nsum;       // sum of n_j over N(i) without i
+    const int* nb_blk;     // block id of (i, j) per N(i) position
+    const int* nb_blkT;    // block id of (j, i) per N(i) position
+    const int* diag_blk;   // block id of (i, i)
+    DevStatus* status;
+};
+
+// Per-colour work lists of the basis kernels (device pointers).
+struct ColourLists {
+    const int* boxes;          // boxes of the colour
+    const int* seg_ptr;        // nbox+1: fill segments of each box
+    const int* seg_blk;        // fill block (i, j)
+    const int* seg_j;          // column box j
+    const int64_t* seg_yoff;   // row offset of the segment in the box's Y^T
+    const int64_t* ybase;      // scratch offset of the box's Y^T
+    const int64_t* ylead;      // leading dimension (total rows) of the box's Y^T
+    const int64_t* wbase;      // scratch offset of the box's n x n work matrix
+};
+
+}  // namespace h2rs

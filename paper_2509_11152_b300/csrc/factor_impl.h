@@ -1,0 +1,83 @@
+// Host-side factor object: per-level device buffers and the drivers of the
+// factorisation (factor.cu) and of the solve / refinement (solve.cu).
+#pragma once
+
+#include <memory>
+
+#include "factor_args.cuh"
+
+namespace h2rs {
+
+// Per-level state kept by the factor (the solve needs most of it).
+struct LevelRT {
+    int l = 0, cnt = 0;
+    const LevelStruct* S = nullptr;
+    std::vector<int> n, k, kt;
+    std::vector<int64_t> blk_off, V_off, Q_off, LU_off, piv_off, WU_off, WL_off, voff;
+    std::vector<int> WLld, Nsum, nbofs, diag_blk, brow;
+    int64_t vtot = 0;
+    // device: structure and offsets
+    DevBuf d_n, d_k, d_kt, d_colour, d_blk_off, d_brow, d_bcol;
+    DevBuf d_V_off, d_Q_off, d_LU_off, d_piv_off, d_WU_off, d_WL_off, d_WLld;
+    DevBuf d_nb_ptr, d_nb_col, d_nbofs, d_Nsum, d_nb_blk, d_nb_blkT, d_diag_blk, d_voff;
+    DevBuf d_fl_tbox, d_fl_tptr, d_fl_ci, d_fl_cpos;
+    // device: factor data
+    DevBuf Q, LU, piv, WU, WL;
+    // device: working data (freed after the level close)
+    DevBuf blk, V;
+};
+
+struct FactorBase {
+    virtual ~FactorBase() = default;
+    virtual void factorize() = 0;
+    // x <- A^-1 b in place; b is float64, device, n x nrhs with leading dimension ldb
+    virtual void solve_dev(double* b, int nrhs, int64_t ldb) = 0;
+    h2_factor_stats stats{};
+    int64_t bytes_now = 0;
+    int precision = H2_PREC_FP64;
+    double norm_a_ = 0;
+    cudaStream_t stream = nullptr;
+    const MatrixObj* A = nullptr;
+    std::vector<std::vector<int64_t>> lay_sizes, lay_ranks, lay_rowptr, lay_col, lay_offset;
+    std::vector<std::vector<int32_t>> lay_colour, lay_kind;
+};
+
+std::unique_ptr<FactorBase> make_factor(const MatrixObj* A, const h2_factor_opts& o);
+
+template <class T>
+struct FactorImpl : FactorBase {
+    double eps_lu = 0, norm_a = 0;
+    std::vector<LevelRT> lv;
+    // top level (float64)
+    int64_t nt = 0;
+    std::vector<int64_t> toff;
+    std::vector<int> tn;
+    DevBuf Dt, tpiv, d_toff;
+    DevBuf status;
+    // events for phase timing
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_phase;
+
+    FactorImpl(const MatrixObj* A_, const h2_factor_opts& o);
+    ~FactorImpl() override;
+    void factorize() override;
+    void solve_dev(double* b, int nrhs, int64_t ldb) override;
+
+   private:
+    void setup_level(size_t a);
+    void run_level(size_t a);
+    void close_level(size_t a);
+    void top_factor();
+    void mark(int phase);
+    void check_status(const char* where);
+    void account(int phase, double flops, double bytes) {
+        stats.phase_flops[phase] += flops;
+        stats.phase_bytes[phase] += bytes;
+    }
+};
+
+}  // namespace h2rs
+
+struct h2_factor {
+    std::unique_ptr<h2rs::FactorBase> f;
+};

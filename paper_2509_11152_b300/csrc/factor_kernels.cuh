@@ -1,0 +1,898 @@
+// Factorisation kernels (Alg. 2 per colour, level close, top-level LU).
+// Included by factor.cu only: a kernel is compiled in the translation unit that
+// launches it.
+//
+// All per-box kernels run one thread block per box of the colour; box data
+// (blocks, bases, factors) sit at prefix-sum offsets inside per-level buffers
+// (Sec. 2.2: no per-box allocation).  Shapes are data dependent (augmented ranks are
+// only known on the device), so every kernel reads n_i and k~_i from device arrays.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "factor_args.cuh"
+
+namespace h2rs {
+
+// ------------------------------------------------------------------ helpers
+__device__ inline void dev_fail(DevStatus* st, int code, int level, int box) {
+    if (atomicCAS(&st->code, 0, code) == 0) {
+        st->level = level;
+        st->box = box;
+    }
+}
+
+template <class T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum; every thread gets the result.  red: 33 T of shared memory.
+template <class T>
+__device__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T x = lane < nw ? red[lane] : T(0);
+        x = warp_sum(x);
+        if (lane == 0) red[32] = x;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <class T> __device__ inline T t_abs(T x) { return x < T(0) ? -x : x; }
+template <class T> __device__ inline bool t_finite(T x) { return isfinite((double)x); }
+
+// ================================================================== leaf load
+template <class T>
+__global__ void k_leaf_load(LevelArgs<T> a, const double* __restrict__ D,
+                            const int64_t* __restrict__ D_off,
+                            const int64_t* __restrict__ near_entry) {
+    const int b = blockIdx.x;
+    const int i = a.brow[b], j = a.bcol[b];
+    const int64_t cnt = (int64_t)a.n[i] * a.n[j];
+    T* dst = a.blk + a.blk_off[b];
+    const int64_t e = near_entry[b];
+    if (e < 0) {
+        for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) dst[x] = T(0);
+        return;
+    }
+    const double* src = D + D_off[e];
+    for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) dst[x] = (T)src[x];
+}
+
+template <class T>
+__global__ void k_leaf_basis(LevelArgs<T> a, T* V, const double* __restrict__ U,
+                             const int64_t* __restrict__ U_off) {
+    const int i = blockIdx.x;
+    const int64_t cnt = (int64_t)a.n[i] * a.k[i];
+    const double* src = U + U_off[i];
+    T* dst = V + a.V_off[i];
+    for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) dst[x] = (T)src[x];
+}
+
+// ================================================================== augmentation
+// Y = (I - V V^T) F for the live columns of one fill block of box i; Y^T is written
+// into the box's scratch rows (Alg. 2 truncSVD input).
+template <class T>
+__global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* __restrict__ seg_slot,
+                             T* __restrict__ scratch) {
+    constexpr int PC = 16;
+    const int s = blockIdx.x;
+    const int slot = seg_slot[s];
+    const int i = L.boxes[slot];
+    const int b = L.seg_blk[s], j = L.seg_j[s];
+    const int n = a.n[i], k = a.k[i], nj = a.n[j];
+    const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
+    const T* F = a.blk + a.blk_off[b];
+    const T* V = a.V + a.V_off[i];
+    const int64_t ld = L.ylead[slot];
+    T* Yt = scratch + L.ybase[slot] + L.seg_yoff[s];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* Fs = reinterpret_cast<T*>(sm_raw);
+    T* Ps = Fs + (size_t)n * PC;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    for (int c0 = skip; c0 < nj; c0 += PC) {
+        const int pc = min(PC, nj - c0);
+        for (int x = tid; x < n * pc; x += bs) {
+            const int r = x % n, c = x / n;
+            Fs[r + c * n] = F[r + (int64_t)(c0 + c) * n];
+        }
+        __syncthreads();
+        for (int x = tid; x < k * pc; x += bs) {
+            const int r = x % k, c = x / k;
+            const T* vr = V + (int64_t)r * n;
+            T acc = 0;
+            for (int q = 0; q < n; ++q) acc += vr[q] * Fs[q + c * n];
+            Ps[r + c * k] = acc;
+        }
+        __syncthreads();
+        for (int x = tid; x < n * pc; x += bs) {
+            const int c = x % pc, r = x / pc;
+            T acc = Fs[r + c * n];
+            for (int q = 0; q < k; ++q) acc -= V[r + (int64_t)q * n] * Ps[q + c * k];
+            Yt[(c0 + c) + (int64_t)r * ld] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Basis augmentation + completion of one box (Alg. 2, truncSVD option 2):
+//   R  = R-factor of Y^T (Householder, streamed over row chunks, R kept row-major)
+//   one-sided Jacobi on M = R^T: its converged columns are sigma_p w_p with w_p the
+//   left singular vectors of Y; w_p with sigma_p > eps_fill (largest first, at most
+//   n-k of them) form Vbar
+//   Householder QR of [V, Vbar]: its Q columns k.. give Vbar orthonormalised against
+//   V and the complement V~perp; Q~ = [V~perp, V, Vbar].
+template <class T>
+__global__ void __launch_bounds__(256)
+k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
+        T* __restrict__ gwork, T eps_fill, int w_in_smem) {
+    const int slot = blockIdx.x;
+    const int i = L.boxes[slot];
+    const int n = a.n[i], k = a.k[i];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const int CH = (n <= 192) ? 64 : 32;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* C = reinterpret_cast<T*>(sm_raw);            // CH x n chunk (col-major, ld CH)
+    T* tau = C + (size_t)CH * n;                    // n
+    T* sig = tau + n;                               // n
+    T* red = sig + n;                               // 33
+    int* ired = reinterpret_cast<int*>(red + 33);   // 4
+    T* W = w_in_smem ? reinterpret_cast<T*>(ired + 4) : gwork + L.wbase[slot];
+    T* Qs = a.Q + a.Q_off[i];
+    const T* V = a.V + a.V_off[i];
+    const int64_t ld = L.ylead[slot];
+    const T* Yt = scratch + L.ybase[slot];
+
+    // live fill rows of this box
+    const int s0 = L.seg_ptr[slot], s1 = L.seg_ptr[slot + 1];
+    int64_t live = 0;
+    for (int s = s0; s < s1; ++s) {
+        const int j = L.seg_j[s];
+        const int nj = a.n[j];
+        live += nj - ((a.colour[j] < cur) ? (nj - a.kt[j]) : 0);
+    }
+    int keep = 0;
+    if (live > 0 && k < n) {
+        // ---------------- R-factor of Y^T
+        for (int x = tid; x < n * n; x += blockDim.x) W[x] = T(0);
+        __syncthreads();
+        for (int s = s0; s < s1; ++s) {
+            const int j = L.seg_j[s];
+            const int nj = a.n[j];
+            const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
+            const int64_t yoff = L.seg_yoff[s];
+            for (int r0 = skip; r0 < nj; r0 += CH) {
+                const int rows = min(CH, nj - r0);
+                for (int x = tid; x < CH * n; x += blockDim.x) {
+                    const int rr = x % CH, col = x / CH;
+                    C[x] = rr < rows ? Yt[(yoff + r0 + rr) + (int64_t)col * ld] : T(0);
+                }
+                __syncthreads();
+                for (int jj = 0; jj < n; ++jj) {
+                    const T c0v = C[lane + jj * CH];
+                    const T c1v = (CH == 64) ? C[lane + 32 + jj * CH] : T(0);
+                    const T ss = warp_sum(c0v * c0v + c1v * c1v);
+                    if (ss == T(0)) continue;                       // uniform
+                    const T x0 = W[(int64_t)jj * n + jj];
+                    const T nrm = sqrt(x0 * x0 + ss);
+                    const T beta = x0 > T(0) ? -nrm : nrm;
+                    const T v0 = x0 - beta;
+                    const T tw = -v0 / beta;
+                    const T vr0 = c0v / v0, vr1 = c1v / v0;
+                    for (int col = jj + 1 + wid; col < n; col += nwarp) {
+                        const T e0 = C[lane + col * CH];
+                        const T e1 = (CH == 64) ? C[lane + 32 + col * CH] : T(0);
+                        const T w = W[(int64_t)jj * n + col] + warp_sum(vr0 * e0 + vr1 * e1);
+                        const T tww = tw * w;
+                        C[lane + col * CH] = e0 - tww * vr0;
+                        if (CH == 64) C[lane + 32 + col * CH] = e1 - tww * vr1;
+                        if (lane == 0) W[(int64_t)jj * n + col] -= tww;
+                    }
+                    __syncthreads();
+                    if (tid == 0) W[(int64_t)jj * n + jj] = beta;
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        // ---------------- one-sided Jacobi on M = R^T (column p of M = row p of R)
+        const int meff = (int)(live < (int64_t)n ? live : (int64_t)n);
+        const int m = meff + (meff & 1);
+        const T tol = T(4) * Eps<T>::v;
+        for (int sweep = 0; sweep < 60; ++sweep) {
+            if (tid == 0) ired[0] = 0;
+            __syncthreads();
+            for (int round = 0; round < m - 1; ++round) {
+                for (int pr = wid; pr < m / 2; pr += nwarp) {
+                    const int x1 = pr, x2 = m - 1 - pr;
+                    const int p = x1 == 0 ? 0 : ((x1 - 1 + round) % (m - 1)) + 1;
+                    const int q = x2 == 0 ? 0 : ((x2 - 1 + round) % (m - 1)) + 1;
+                    if (p >= meff || q >= meff) continue;
+                    T* Mp = W + (int64_t)p * n;
+                    T* Mq = W + (int64_t)q * n;
+                    T al = 0, be = 0, ga = 0;
+                    for (int r = lane; r < n; r += 32) {
+                        const T u = Mp[r], v = Mq[r];
+                        al += u * u; be += v * v; ga += u * v;
+                    }
+                    al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+                    if (al > T(0) && be > T(0) && t_abs(ga) > tol * sqrt(al * be)) {
+                        const T zeta = (be - al) / (T(2) * ga);
+                        const T t = (zeta >= T(0) ? T(1) : T(-1)) /
+                                    (t_abs(zeta) + sqrt(T(1) + zeta * zeta));
+                        const T c = T(1) / sqrt(T(1) + t * t);
+                        const T sn = c * t;
+                        for (int r = lane; r < n; r += 32) {
+                            const T u = Mp[r], v = Mq[r];
+                            Mp[r] = c * u - sn * v;
+                            Mq[r] = sn * u + c * v;
+                        }
+                        if (lane == 0) atomicAdd(&ired[0], 1);
+                    }
+                }
+                __syncthreads();
+            }
+            if (ired[0] == 0) break;
+            __syncthreads();
+        }
+        // ---------------- singular values, selection (largest first)
+        for (int p = wid; p < meff; p += nwarp) {
+            T s2 = 0;
+            for (int r = lane; r < n; r += 32) s2 += W[(int64_t)p * n + r] * W[(int64_t)p * n + r];
+            s2 = warp_sum(s2);
+            if (lane == 0) sig[p] = sqrt(s2);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int cnt = 0;
+            for (int p = 0; p < meff; ++p) cnt += sig[p] > eps_fill;
+            ired[1] = min(cnt, n - k);
+        }
+        __syncthreads();
+        keep = ired[1];
+        // stage Vbar (unnormalised order by rank) in the last keep columns of Q~
+        for (int p = wid; p < meff; p += nwarp) {
+            const T sp = sig[p];
+            int rank = 0;
+            for (int q = 0; q < meff; ++q) rank += (sig[q] > sp) || (sig[q] == sp && q < p);
+            if (rank < keep) {
+                T* dst = Qs + (int64_t)(n - keep + rank) * n;
+                const T inv = T(1) / sp;
+                for (int r = lane; r < n; r += 32) dst[r] = W[(int64_t)p * n + r] * inv;
+            }
+        }
+        __syncthreads();
+    }
+    // ---------------- Householder QR of V~ = [V, Vbar] (n x kt) in W
+    const int kt = k + keep;
+    const int r_red = n - kt;
+    for (int x = tid; x < n * kt; x += blockDim.x) {
+        const int row = x % n, col = x / n;
+        W[x] = col < k ? V[row + (int64_t)col * n] : Qs[row + (int64_t)(n - keep + col - k) * n];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < kt; ++jj) {
+        T part = 0;
+        for (int r = jj + 1 + tid; r < n; r += blockDim.x) part += W[r + (int64_t)jj * n] * W[r + (int64_t)jj * n];
+        const T ss = block_sum(part, red);
+        const T x0 = W[jj + (int64_t)jj * n];
+        if (ss == T(0)) {
+            if (tid == 0) tau[jj] = T(0);
+            __syncthreads();
+            continue;
+        }
+        const T nrm = sqrt(x0 * x0 + ss);
+        const T beta = x0 > T(0) ? -nrm : nrm;
+        const T v0 = x0 - beta;
+        const T tw = -v0 / beta;
+        for (int r = jj + 1 + tid; r < n; r += blockDim.x) W[r + (int64_t)jj * n] /= v0;
+        __syncthreads();
+        for (int col = jj + 1 + wid; col < kt; col += nwarp) {
+            T w = 0;
+            for (int r = jj + 1 + lane; r < n; r += 32) w += W[r + (int64_t)jj * n] * W[r + (int64_t)col * n];
+            w = warp_sum(w) + W[jj + (int64_t)col * n];
+            const T tww = tw * w;
+            for (int r = jj + 1 + lane; r < n; r += 32) W[r + (int64_t)col * n] -= tww * W[r + (int64_t)jj * n];
+            if (lane == 0) W[jj + (int64_t)col * n] -= tww;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            tau[jj] = tw;
+            W[jj + (int64_t)jj * n] = beta;
+        }
+        __syncthreads();
+    }
+    // Q_h[:, k + t], t in [0, n-k): t < keep -> Vbar (Q~ col r+k+t), else V~perp (col t-keep)
+    const int nout = n - k;
+    const int cw = CH;                               // columns per chunk (C holds n x CH)
+    for (int t0 = 0; t0 < nout; t0 += cw) {
+        const int tw_ = min(cw, nout - t0);
+        for (int x = tid; x < n * tw_; x += blockDim.x) {
+            const int row = x % n, t = x / n;
+            C[row + (int64_t)t * n] = (row == k + t0 + t) ? T(1) : T(0);
+        }
+        __syncthreads();
+        for (int jj = kt - 1; jj >= 0; --jj) {
+            const T tw = tau[jj];
+            if (tw == T(0)) continue;
+            for (int t = wid; t < tw_; t += nwarp) {
+                T* E = C + (int64_t)t * n;
+                T w = 0;
+                for (int r = jj + 1 + lane; r < n; r += 32) w += W[r + (int64_t)jj * n] * E[r];
+                w = warp_sum(w) + E[jj];
+                const T tww = tw * w;
+                for (int r = jj + 1 + lane; r < n; r += 32) E[r] -= tww * W[r + (int64_t)jj * n];
+                if (lane == 0) E[jj] -= tww;
+            }
+            __syncthreads();
+        }
+        for (int x = tid; x < n * tw_; x += blockDim.x) {
+            const int row = x % n, t = t0 + x / n;
+            const int dcol = t < keep ? (r_red + k + t) : (t - keep);
+            Qs[row + (int64_t)dcol * n] = C[row + (int64_t)(t - t0) * n];
+        }
+        __syncthreads();
+    }
+    for (int x = tid; x < n * k; x += blockDim.x) {
+        const int row = x % n, col = x / n;
+        Qs[row + (int64_t)(r_red + col) * n] = V[row + (int64_t)col * n];
+    }
+    if (tid == 0) a.kt[i] = kt;
+}
+
+// ================================================================== projection
+// Left: B <- Q~_i^T B for a block in row i, by column panels of 32 (in place).
+template <class T>
+__global__ void k_proj_left(LevelArgs<T> a, const int* __restrict__ wl_box,
+                            const int* __restrict__ wl_blk, const int* __restrict__ wl_panel) {
+    constexpr int PW = 32;
+    const int w = blockIdx.x;
+    const int i = wl_box[w], b = wl_blk[w], c0 = wl_panel[w] * PW;
+    const int n = a.n[i];
+    const int nj = a.n[a.bcol[b]];
+    const int pc = min(PW, nj - c0);
+    const T* Q = a.Q + a.Q_off[i];
+    T* B = a.blk + a.blk_off[b];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* P = reinterpret_cast<T*>(sm_raw);            // n x PW
+    for (int x = threadIdx.x; x < n * pc; x += blockDim.x) {
+        const int r = x % n, c = x / n;
+        P[r + c * n] = B[r + (int64_t)(c0 + c) * n];
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < n * pc; x += blockDim.x) {
+        const int r = x % n, c = x / n;
+        const T* qr = Q + (int64_t)r * n;
+        T acc = 0;
+        for (int q = 0; q < n; ++q) acc += qr[q] * P[q + c * n];
+        B[r + (int64_t)(c0 + c) * n] = acc;
+    }
+}
+
+// Right: B <- B Q~_i for a block in column i, by row panels of 32 (in place).
+template <class T>
+__global__ void k_proj_right(LevelArgs<T> a, const int* __restrict__ wr_box,
+                             const int* __restrict__ wr_blk, const int* __restrict__ wr_panel) {
+    constexpr int PW = 32;
+    const int w = blockIdx.x;
+    const int i = wr_box[w], b = wr_blk[w], r0 = wr_panel[w] * PW;
+    const int n = a.n[i];
+    const int nj = a.n[a.brow[b]];
+    const int pr = min(PW, nj - r0);
+    const T* Q = a.Q + a.Q_off[i];
+    T* B = a.blk + a.blk_off[b];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* P = reinterpret_cast<T*>(sm_raw);            // PW x n, P[r + c*PW]
+    for (int x = threadIdx.x; x < pr * n; x += blockDim.x) {
+        const int r = x % pr, c = x / pr;
+        P[r + c * PW] = B[(r0 + r) + (int64_t)c * nj];
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < pr * n; x += blockDim.x) {
+        const int r = x % pr, c = x / pr;
+        const T* qc = Q + (int64_t)c * n;
+        T acc = 0;
+        for (int q = 0; q < n; ++q) acc += P[r + q * PW] * qc[q];
+        B[(r0 + r) + (int64_t)c * nj] = acc;
+    }
+}
+
+// F truncation after projection: redundant rows (is_col = 0) or columns (1) of a
+// fill block of box i are dropped (set to zero).  Same kernel zeroes the eliminated
+// rows / columns of near-field blocks after the Schur update.
+template <class T>
+__global__ void k_zero_redundant(LevelArgs<T> a, const int* __restrict__ z_box,
+                                 const int* __restrict__ z_blk, const int* __restrict__ z_col) {
+    const int w = blockIdx.x;
+    const int i = z_box[w], b = z_blk[w];
+    const int r = a.n[i] - a.kt[i];
+    if (r <= 0) return;
+    const int rows = a.n[a.brow[b]], cols = a.n[a.bcol[b]];
+    T* B = a.blk + a.blk_off[b];
+    if (z_col[w] == 0) {
+        for (int x = threadIdx.x; x < r * cols; x += blockDim.x) {
+            const int rr = x % r, c = x / r;
+            B[rr + (int64_t)c * rows] = T(0);
+        }
+    } else {
+        for (int64_t x = threadIdx.x; x < (int64_t)rows * r; x += blockDim.x) B[x] = T(0);
+    }
+}
+
+// ================================================================== partial LU
+// LU with partial pivoting of D_RR = D_ii[0:r, 0:r] (first maximal |value| wins).
+template <class T>
+__global__ void __launch_bounds__(256)
+k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
+    const int i = boxes[blockIdx.x];
+    const int n = a.n[i];
+    const int r = n - a.kt[i];
+    if (r <= 0) return;
+    const int tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ T rv[32];
+    __shared__ int ri[32];
+    __shared__ int piv_s;
+    __shared__ T pv_s;
+    T* G = a.LU + a.LU_off[i];
+    T* W = in_smem ? reinterpret_cast<T*>(sm_raw) : G;
+    const T* Dii = a.blk + a.blk_off[a.diag_blk[i]];
+    for (int x = tid; x < r * r; x += blockDim.x) {
+        const int rr = x % r, c = x / r;
+        W[x] = Dii[rr + (int64_t)c * n];
+    }
+    __syncthreads();
+    int* pv = a.piv + a.piv_off[i];
+    for (int j = tid; j < r; j += blockDim.x) pv[j] = j;   // defined even if we stop early
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+        // argmax |W[a][j]|, a >= j, ties to the lowest index
+        T best = T(-1);
+        int bi = INT_MAX;
+        for (int x = j + tid; x < r; x += blockDim.x) {
+            const T v = t_abs(W[x + (int64_t)j * r]);
+            if (v > best || (v == best && x < bi)) { best = v; bi = x; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            T bb = T(-1);
+            int bx = INT_MAX;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (rv[w] > bb || (rv[w] == bb && ri[w] < bx)) { bb = rv[w]; bx = ri[w]; }
+            piv_s = bx;
+            pv_s = bb;
+            pv[j] = bx;
+        }
+        __syncthreads();
+        const int p = piv_s;
+        if (!(pv_s > T(0)) || !t_finite(pv_s)) {
+            if (tid == 0) dev_fail(a.status, H2_ERR_SINGULAR, a.level, i);
+            return;
+        }
+        if (p != j)
+            for (int c = tid; c < r; c += blockDim.x) {
+                const T t0 = W[j + (int64_t)c * r];
+                W[j + (int64_t)c * r] = W[p + (int64_t)c * r];
+                W[p + (int64_t)c * r] = t0;
+            }
+        __syncthreads();
+        const T d = W[j + (int64_t)j * r];
+        for (int x = j + 1 + tid; x < r; x += blockDim.x) W[x + (int64_t)j * r] /= d;
+        __syncthreads();
+        const int m = r - j - 1;
+        for (int x = tid; x < m * m; x += blockDim.x) {
+            const int rr = j + 1 + x % m, c = j + 1 + x / m;
+            W[rr + (int64_t)c * r] -= W[rr + (int64_t)j * r] * W[j + (int64_t)c * r];
+        }
+        __syncthreads();
+    }
+    if (in_smem)
+        for (int x = tid; x < r * r; x += blockDim.x) G[x] = W[x];
+}
+
+// W_U^i = D_RR^-1 [D_{i_R, j} ..., D_{i_R, i_S}]: one warp per column (8 per block).
+template <class T>
+__global__ void k_trsm_u(LevelArgs<T> a, const int* __restrict__ w_box,
+                         const int* __restrict__ w_col0) {
+    const int i = w_box[blockIdx.x];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = w_col0[blockIdx.x] + wid;
+    const int n = a.n[i], kt = a.kt[i], r = n - kt;
+    const int ns = a.Nsum[i];
+    if (r <= 0 || col >= ns + kt) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* buf = reinterpret_cast<T*>(sm_raw) + (size_t)wid * n;
+    const T* src;
+    if (col >= ns) {
+        src = a.blk + a.blk_off[a.diag_blk[i]] + (int64_t)(r + col - ns) * n;
+    } else {
+        int pos = a.nb_ptr[i];
+        for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
+            const int j = a.nb_col[p];
+            if (j != i && a.nbofs[p] <= col && col < a.nbofs[p] + a.n[j]) { pos = p; break; }
+        }
+        src = a.blk + a.blk_off[a.nb_blk[pos]] + (int64_t)(col - a.nbofs[pos]) * n;
+    }
+    for (int x = lane; x < r; x += 32) buf[x] = src[x];
+    __syncwarp();
+    const T* LU = a.LU + a.LU_off[i];
+    const int* pv = a.piv + a.piv_off[i];
+    if (lane == 0)
+        for (int j = 0; j < r; ++j) {
+            const int p = pv[j];
+            if (p < j || p >= r) { dev_fail(a.status, H2_ERR_SINGULAR, a.level, i); break; }
+            if (p != j) { const T t0 = buf[j]; buf[j] = buf[p]; buf[p] = t0; }
+        }
+    __syncwarp();
+    for (int j = 0; j < r; ++j) {
+        const T xj = buf[j];
+        for (int x = j + 1 + lane; x < r; x += 32) buf[x] -= LU[x + (int64_t)j * r] * xj;
+        __syncwarp();
+    }
+    for (int j = r - 1; j >= 0; --j) {
+        if (lane == 0) buf[j] /= LU[j + (int64_t)j * r];
+        __syncwarp();
+        const T xj = buf[j];
+        for (int x = lane; x < j; x += 32) buf[x] -= LU[x + (int64_t)j * r] * xj;
+        __syncwarp();
+    }
+    T* out = a.WU + a.WU_off[i] + (int64_t)col * r;
+    for (int x = lane; x < r; x += 32) out[x] = buf[x];
+}
+
+// W_L^i = [D_{j, i_R}; D_{i_S, i_R}] D_RR^-1: one warp per row (8 per block).
+template <class T>
+__global__ void k_trsm_l(LevelArgs<T> a, const int* __restrict__ w_box,
+                         const int* __restrict__ w_row0) {
+    const int i = w_box[blockIdx.x];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = w_row0[blockIdx.x] + wid;
+    const int n = a.n[i], kt = a.kt[i], r = n - kt;
+    const int ns = a.Nsum[i];
+    if (r <= 0 || row >= ns + kt) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* buf = reinterpret_cast<T*>(sm_raw) + (size_t)wid * n;
+    const T* src;
+    int64_t stride;
+    if (row >= ns) {
+        src = a.blk + a.blk_off[a.diag_blk[i]] + (r + row - ns);
+        stride = n;
+    } else {
+        int pos = a.nb_ptr[i];
+        for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
+            const int j = a.nb_col[p];
+            if (j != i && a.nbofs[p] <= row && row < a.nbofs[p] + a.n[j]) { pos = p; break; }
+        }
+        stride = a.n[a.nb_col[pos]];
+        src = a.blk + a.blk_off[a.nb_blkT[pos]] + (row - a.nbofs[pos]);
+    }
+    for (int x = lane; x < r; x += 32) buf[x] = src[(int64_t)x * stride];
+    __syncwarp();
+    const T* LU = a.LU + a.LU_off[i];
+    const int* pv = a.piv + a.piv_off[i];
+    // x U = y
+    for (int j = 0; j < r; ++j) {
+        if (lane == 0) buf[j] /= LU[j + (int64_t)j * r];
+        __syncwarp();
+        const T xj = buf[j];
+        for (int b = j + 1 + lane; b < r; b += 32) buf[b] -= xj * LU[j + (int64_t)b * r];
+        __syncwarp();
+    }
+    // z L = x (unit lower)
+    for (int j = r - 1; j >= 0; --j) {
+        const T zj = buf[j];
+        for (int b = lane; b < j; b += 32) buf[b] -= zj * LU[j + (int64_t)b * r];
+        __syncwarp();
+    }
+    if (lane == 0)
+        for (int j = r - 1; j >= 0; --j) {
+            const int p = pv[j];
+            if (p < j || p >= r) { dev_fail(a.status, H2_ERR_SINGULAR, a.level, i); break; }
+            if (p != j) { const T t0 = buf[j]; buf[j] = buf[p]; buf[p] = t0; }
+        }
+    __syncwarp();
+    T* out = a.WL + a.WL_off[i] + row;
+    const int64_t ldw = a.WLld[i];
+    for (int x = lane; x < r; x += 32) out[(int64_t)x * ldw] = buf[x];
+}
+
+// ================================================================== Schur update
+// Target-owned accumulation: X_jk -= sum_{i in colour, j,k in N(i)} D_{j,i_R} W_U^i[k]
+// as one GEMM per target whose K dimension runs over the contributors.  64x64 tiles,
+// 256 threads, 4x4 outputs per thread.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
+        const int* __restrict__ c_box, const int* __restrict__ c_ablk, const int* __restrict__ c_kpos,
+        const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const int tt = tile_tgt[blockIdx.x];
+    const int mn = tile_mn[blockIdx.x];
+    const int tb = tgt_blk[tt];
+    const int j = a.brow[tb], kb = a.bcol[tb];
+    const int nj = a.n[j], nk = a.n[kb];
+    const int row_lo = (a.colour[j] == cur) ? nj - a.kt[j] : 0;
+    const int col_lo = (a.colour[kb] == cur) ? nk - a.kt[kb] : 0;
+    const int m = nj - row_lo, nn = nk - col_lo;
+    const int m0 = (mn >> 16) * BM, n0 = (mn & 0xffff) * BN;
+    if (m0 >= m || n0 >= nn) return;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int c = tgt_ptr[tt]; c < tgt_ptr[tt + 1]; ++c) {
+        const int i = c_box[c];
+        const int ri = a.n[i] - a.kt[i];
+        if (ri <= 0) continue;
+        const T* A = a.blk + a.blk_off[c_ablk[c]] + row_lo;           // m x ri, ld nj
+        const int pos = a.nb_ptr[i] + c_kpos[c];
+        const T* B = a.WU + a.WU_off[i] + (int64_t)a.nbofs[pos] * ri;  // ri x nn, ld ri
+        for (int k0 = 0; k0 < ri; k0 += BK) {
+            for (int x = tid; x < BK * BM; x += 256) {
+                const int kk = x / BM, rr = x % BM;
+                const int gr = m0 + rr, gk = k0 + kk;
+                As[kk][rr] = (gr < m && gk < ri) ? A[gr + (int64_t)gk * nj] : T(0);
+            }
+            for (int x = tid; x < BK * BN; x += 256) {
+                const int kk = x % BK, cc = x / BK;
+                const int gc = n0 + cc, gk = k0 + kk;
+                Bs[kk][cc] = (gc < nn && gk < ri) ? B[gk + (int64_t)gc * ri] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) av[u] = As[kk][tx + 16 * u];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][ty + 16 * v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+            }
+            __syncthreads();
+        }
+    }
+    T* Cm = a.blk + a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int gr = m0 + tx + 16 * u, gc = n0 + ty + 16 * v;
+            if (gr < m && gc < nn) Cm[gr + (int64_t)gc * nj] -= acc[u][v];
+        }
+}
+
+// ================================================================== level close
+// Parent block (p, q) from its four child pairs: skeleton x skeleton parts of the
+// near-field / fill blocks plus the zero-padded couplings S~ (Sec. 2.1, level close).
+template <class T>
+__global__ void k_close_blocks(LevelArgs<T> a, T* __restrict__ pblk, const int64_t* __restrict__ pblk_off,
+                               const int* __restrict__ pbrow, const int* __restrict__ pbcol,
+                               const int* __restrict__ cl_dblk, const int* __restrict__ cl_fblk,
+                               const int64_t* __restrict__ cl_adm, const double* __restrict__ S,
+                               const int64_t* __restrict__ S_off) {
+    const int pb = blockIdx.x;
+    const int p = pbrow[pb], q = pbcol[pb];
+    const int c1 = 2 * p, c2 = 2 * p + 1, e1 = 2 * q, e2 = 2 * q + 1;
+    const int kc1 = a.kt[c1], kc2 = a.kt[c2], ke1 = a.kt[e1], ke2 = a.kt[e2];
+    const int np = kc1 + kc2, nq = ke1 + ke2;
+    T* out = pblk + pblk_off[pb];
+    for (int64_t x = threadIdx.x; x < (int64_t)np * nq; x += blockDim.x) {
+        const int ar = (int)(x % np), bc = (int)(x / np);
+        const int ca = ar < kc1 ? 0 : 1, ea = bc < ke1 ? 0 : 1;
+        const int c = ca ? c2 : c1, e = ea ? e2 : e1;
+        const int a1 = ca ? ar - kc1 : ar, b1 = ea ? bc - ke1 : bc;
+        const int slot = 4 * pb + 2 * ca + ea;
+        const int nc = a.n[c], ne = a.n[e];
+        const int rc = nc - a.kt[c], re = ne - a.kt[e];
+        T v = T(0);
+        const int db = cl_dblk[slot];
+        if (db >= 0) v += a.blk[a.blk_off[db] + (rc + a1) + (int64_t)(re + b1) * nc];
+        const int fb = cl_fblk[slot];
+        if (fb >= 0) v += a.blk[a.blk_off[fb] + (rc + a1) + (int64_t)(re + b1) * nc];
+        const int64_t ad = cl_adm[slot];
+        if (ad >= 0) {
+            const int kc = a.k[c], ke = a.k[e];
+            if (a1 < kc && b1 < ke) v += (T)S[S_off[ad] + a1 + (int64_t)b1 * kc];
+        }
+        out[x] = v;
+    }
+}
+
+// Parent basis V_p = [T~_c1; T~_c2], T~_c = [E_c; 0] (nested basis after projection).
+template <class T>
+__global__ void k_close_basis(LevelArgs<T> a, T* __restrict__ pV, const int64_t* __restrict__ pV_off,
+                              const int* __restrict__ pk, const double* __restrict__ E,
+                              const int64_t* __restrict__ E_off, int64_t child_first) {
+    const int p = blockIdx.x;
+    const int c1 = 2 * p, c2 = 2 * p + 1;
+    const int kc1 = a.kt[c1], kc2 = a.kt[c2];
+    const int np = kc1 + kc2, kp = pk[p];
+    T* out = pV + pV_off[p];
+    for (int64_t x = threadIdx.x; x < (int64_t)np * kp; x += blockDim.x) {
+        const int ar = (int)(x % np), col = (int)(x / np);
+        const int c = ar < kc1 ? c1 : c2;
+        const int a1 = ar < kc1 ? ar : ar - kc1;
+        const int kc = a.k[c];
+        T v = T(0);
+        if (a1 < kc) v = (T)E[E_off[child_first + c] + a1 + (int64_t)col * kc];
+        out[x] = v;
+    }
+}
+
+// ================================================================== top level
+// Dense float64 matrix of the top level from its blocks.
+template <class T>
+__global__ void k_top_assemble(const T* __restrict__ blk, const int64_t* __restrict__ blk_off,
+                               const int* __restrict__ brow, const int* __restrict__ bcol,
+                               const int* __restrict__ n, const int64_t* __restrict__ toff,
+                               double* __restrict__ Dt, int64_t nt) {
+    const int b = blockIdx.x;
+    const int p = brow[b], q = bcol[b];
+    const int np = n[p], nq = n[q];
+    const T* src = blk + blk_off[b];
+    double* dst = Dt + toff[p] + toff[q] * nt;
+    for (int64_t x = threadIdx.x; x < (int64_t)np * nq; x += blockDim.x) {
+        const int rr = (int)(x % np), c = (int)(x / np);
+        dst[rr + (int64_t)c * nt] = (double)src[x];
+    }
+}
+
+// Panel factorisation (columns j0..j0+jb of rows j0..nt) with partial pivoting.
+__global__ void __launch_bounds__(1024)
+k_top_panel(double* __restrict__ A, int64_t nt, int64_t j0, int jb, int* __restrict__ piv,
+            DevStatus* st) {
+    __shared__ double rv[32];
+    __shared__ int64_t ri[32];
+    __shared__ int64_t psel;
+    __shared__ double pval;
+    const int tid = threadIdx.x;
+    for (int jj = 0; jj < jb; ++jj) {
+        const int64_t j = j0 + jj;
+        double best = -1.0;
+        int64_t bi = INT64_MAX;
+        for (int64_t x = j + tid; x < nt; x += blockDim.x) {
+            const double v = fabs(A[x + j * nt]);
+            if (v > best || (v == best && x < bi)) { best = v; bi = x; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bb = -1.0;
+            int64_t bx = INT64_MAX;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (rv[w] > bb || (rv[w] == bb && ri[w] < bx)) { bb = rv[w]; bx = ri[w]; }
+            psel = bx;
+            pval = bb;
+            piv[j] = (int)bx;
+        }
+        __syncthreads();
+        if (!(pval > 0.0) || !isfinite(pval)) {
+            if (tid == 0) dev_fail(st, H2_ERR_SINGULAR, -1, (int)j);
+            return;
+        }
+        const int64_t p = psel;
+        if (p != j)
+            for (int c = tid; c < jb; c += blockDim.x) {
+                const double t0 = A[j + (j0 + c) * nt];
+                A[j + (j0 + c) * nt] = A[p + (j0 + c) * nt];
+                A[p + (j0 + c) * nt] = t0;
+            }
+        __syncthreads();
+        const double d = A[j + j * nt];
+        for (int64_t x = j + 1 + tid; x < nt; x += blockDim.x) A[x + j * nt] /= d;
+        __syncthreads();
+        const int rem = jb - jj - 1;
+        const int64_t mrows = nt - j - 1;
+        for (int64_t x = tid; x < mrows * rem; x += blockDim.x) {
+            const int64_t rr = j + 1 + x % mrows;
+            const int64_t c = j + 1 + x / mrows;
+            A[rr + c * nt] -= A[rr + j * nt] * A[j + c * nt];
+        }
+        __syncthreads();
+    }
+}
+
+// Apply the panel's row interchanges to the columns outside the panel.
+__global__ void k_top_swap(double* __restrict__ A, int64_t nt, int64_t j0, int jb,
+                           const int* __restrict__ piv) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nt || (c >= j0 && c < j0 + jb)) return;
+    for (int jj = 0; jj < jb; ++jj) {
+        const int64_t j = j0 + jj, p = piv[j];
+        if (p < j || p >= nt) return;   // panel stopped at a singular pivot (status set)
+        if (p != j) {
+            const double t0 = A[j + c * nt];
+            A[j + c * nt] = A[p + c * nt];
+            A[p + c * nt] = t0;
+        }
+    }
+}
+
+// U12 = L11^-1 A12 (unit lower L11 of the panel), one thread per column.
+__global__ void k_top_trsm(double* __restrict__ A, int64_t nt, int64_t j0, int jb) {
+    const int64_t c = j0 + jb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nt) return;
+    double* col = A + c * nt;
+    for (int jj = 0; jj < jb; ++jj) {
+        const double x = col[j0 + jj];
+        for (int r = jj + 1; r < jb; ++r) col[j0 + r] -= A[(j0 + r) + (j0 + jj) * nt] * x;
+    }
+}
+
+// A22 -= L21 U12 (64x64 tiles, float64).
+__global__ void __launch_bounds__(256)
+k_top_gemm(double* __restrict__ A, int64_t nt, int64_t j0, int jb) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int64_t base = j0 + jb;
+    const int64_t m0 = base + (int64_t)blockIdx.x * BM, n0 = base + (int64_t)blockIdx.y * BN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < jb; k0 += BK) {
+        for (int x = tid; x < BK * BM; x += 256) {
+            const int kk = x / BM, rr = x % BM;
+            const int64_t gr = m0 + rr;
+            const int gk = k0 + kk;
+            As[kk][rr] = (gr < nt && gk < jb) ? A[gr + (j0 + gk) * nt] : 0.0;
+        }
+        for (int x = tid; x < BK * BN; x += 256) {
+            const int kk = x % BK, cc = x / BK;
+            const int64_t gc = n0 + cc;
+            const int gk = k0 + kk;
+            Bs[kk][cc] = (gc < nt && gk < jb) ? A[(j0 + gk) + gc * nt] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = As[kk][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][ty + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t gr = m0 + tx + 16 * u, gc = n0 + ty + 16 * v;
+            if (gr < nt && gc < nt) A[gr + gc * nt] -= acc[u][v];
+        }
+}
+
+}  // namespace h2rs

@@ -1,0 +1,151 @@
+// Internal declarations of the h2rs library (not part of the public C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/h2rs.h"
+
+namespace h2rs {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void set_error(const std::string& msg);
+
+#define H2_CUDA_CHECK(call)                                                          \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            throw ::h2rs::Error{H2_ERR_CUDA, std::string(#call) + ": " +             \
+                                                 cudaGetErrorString(e_)};            \
+    } while (0)
+
+#define H2_REQUIRE(cond, code, msg)                                                  \
+    do {                                                                             \
+        if (!(cond)) throw ::h2rs::Error{(code), (msg)};                            \
+    } while (0)
+
+// device status word written by kernels (never trapped on)
+struct DevStatus {
+    int code;       // 0 ok, else an H2_ERR_* value
+    int level;
+    int box;
+    int pad;
+};
+
+// ------------------------------------------------------------------ memory
+// Stream-ordered device buffer (cudaMallocAsync from the default pool).
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        release();
+        ptr = o.ptr; bytes = o.bytes; stream = o.stream;
+        o.ptr = nullptr; o.bytes = 0;
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t nbytes, cudaStream_t s);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// upload a host vector into a fresh device buffer
+template <class T>
+void upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
+    b.alloc(std::max<size_t>(1, v.size()) * sizeof(T), s);
+    if (!v.empty())
+        H2_CUDA_CHECK(cudaMemcpyAsync(b.ptr, v.data(), v.size() * sizeof(T),
+                                      cudaMemcpyHostToDevice, s));
+}
+
+// ------------------------------------------------------------------ host copy of A
+struct HostStructure {
+    int64_t n = 0;
+    int d = 0;
+    int64_t nnodes = 0;
+    std::vector<int64_t> node_start, node_size, rank;
+    std::vector<int64_t> U_off, E_off, adm_ptr, adm_col, S_off, inad_ptr, inad_col, D_off;
+};
+
+// ------------------------------------------------------------------ plan
+// Structure-only (rank independent) plan of one level, built once per matrix.
+struct LevelStruct {
+    int l = 0;
+    int cnt = 0;               // boxes at the level
+    int64_t first = 0;         // global id of the first box
+    std::vector<int> nb_ptr, nb_col;          // near field N(i), sorted, includes i
+    std::vector<int> colour;
+    int ncolour = 0;
+    std::vector<std::vector<int>> cboxes;     // boxes of each colour, ascending
+    // merged block list: near field + fill pattern, CSR, columns ascending
+    std::vector<int> bptr, bcol;
+    std::vector<int8_t> bkind;                // 0 near, 1 fill
+    std::vector<int> btr;                     // index of the transposed block
+    std::vector<int> first_touch;             // fill: -1 carried, c = first colour
+                                              // writing it, INT_MAX never
+    std::vector<int64_t> near_entry;          // near block -> entry of A's inad CSR
+    // Schur target lists, per colour: targets (block ids) and their contributors
+    std::vector<int> sch_cptr;                // ncolour+1 -> ranges of targets
+    std::vector<int> sch_tblk;                // target block
+    std::vector<int> sch_tptr;                // ntargets+1 -> ranges of contributors
+    std::vector<int> sch_ci;                  // contributor box i
+    std::vector<int> sch_cA;                  // block (j, i)  (A operand)
+    std::vector<int> sch_ckpos;               // position of k in N(i)
+    // per near-field position (nb_ptr order): block ids of (i, j) and (j, i)
+    std::vector<int> nb_blk, nb_blkT;
+    // forward-solve L updates, per colour: target boxes j and contributors i
+    std::vector<int> fl_cptr;                 // ncolour+1 -> ranges of targets
+    std::vector<int> fl_tbox;                 // target box j
+    std::vector<int> fl_tptr;                 // ntargets+1 -> ranges of contributors
+    std::vector<int> fl_ci;                   // contributor box i
+    std::vector<int> fl_cpos;                 // position of j in N(i)
+    // level close to the parent level (l-1): per parent block, 4 child sources
+    std::vector<int> cl_dblk;                 // 4 per parent block, near block or -1
+    std::vector<int> cl_fblk;                 // 4 per parent block, fill block or -1
+    std::vector<int64_t> cl_adm;              // 4 per parent block, adm entry or -1
+
+    int find(int i, int j) const;             // merged block id of (i, j) or -1
+    int nblocks() const { return (int)bcol.size(); }
+};
+
+struct Plan {
+    int d = 0;
+    int top = -1;                             // t, or -1 when nothing is admissible
+    std::vector<LevelStruct> levels;          // index 0 = level d (leaves) ... level t
+    LevelStruct toplev;                       // the level holding the dense top matrix
+};
+
+void build_plan(const HostStructure& H, Plan& P);
+
+// ------------------------------------------------------------------ objects
+struct MatrixObj {
+    HostStructure H;
+    Plan plan;
+    cudaStream_t stream = nullptr;
+    DevBuf U, E, S, D;                        // float64 values on the device
+    DevBuf d_node_start, d_node_size, d_rank, d_U_off, d_E_off, d_S_off, d_D_off;
+    DevBuf d_adm_ptr, d_adm_col, d_inad_ptr, d_inad_col;
+    // matvec helpers: per node offsets of the coefficient vectors (rank prefix)
+    std::vector<int64_t> coef_off;
+    DevBuf d_coef_off;
+};
+
+}  // namespace h2rs
+
+struct h2_matrix {
+    h2rs::MatrixObj m;
+};

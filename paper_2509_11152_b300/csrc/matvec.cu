@@ -1,0 +1,208 @@
+// Float64 H^2 matrix-vector product y = A x (upsweep, couplings, downsweep, near
+// field) and the vector kernels of iterative refinement.  Coefficient vectors of
+// node g live at coef_off[g]*nrhs, rank_g x nrhs column-major.
+#include "h2rs_internal.h"
+#include "matvec.cuh"
+
+namespace h2rs {
+
+__global__ void mv_leaf_up(const double* __restrict__ U, const int64_t* __restrict__ U_off,
+                           const int64_t* __restrict__ start, const int64_t* __restrict__ size,
+                           const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off,
+                           int64_t first, const double* __restrict__ x, int64_t ldx,
+                           double* __restrict__ xh, int nrhs) {
+    const int i = blockIdx.x;
+    const int64_t g = first + i;
+    const int n = (int)size[g], k = (int)rank[g];
+    const double* Ui = U + U_off[i];
+    const double* xi = x + start[g];
+    double* out = xh + coef_off[g] * nrhs;
+    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
+        const int a = e % k, c = e / k;
+        const double* u = Ui + (int64_t)a * n;
+        const double* xc = xi + (int64_t)c * ldx;
+        double acc = 0;
+        for (int q = 0; q < n; ++q) acc += u[q] * xc[q];
+        out[e] = acc;
+    }
+}
+
+// xh_p = sum_c E_c^T xh_c for the nodes p of one level (first = first node id)
+__global__ void mv_up(const double* __restrict__ E, const int64_t* __restrict__ E_off,
+                      const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off, int64_t first,
+                      double* __restrict__ xh, int nrhs) {
+    const int64_t p = first + blockIdx.x;
+    const int kp = (int)rank[p];
+    double* out = xh + coef_off[p] * nrhs;
+    for (int e = threadIdx.x; e < kp * nrhs; e += blockDim.x) {
+        const int a = e % kp, c = e / kp;
+        double acc = 0;
+        for (int64_t ch = 2 * p + 1; ch <= 2 * p + 2; ++ch) {
+            const int kc = (int)rank[ch];
+            const double* Ec = E + E_off[ch] + (int64_t)a * kc;   // column a of E_c
+            const double* xc = xh + coef_off[ch] * nrhs + (int64_t)c * kc;
+            for (int q = 0; q < kc; ++q) acc += Ec[q] * xc[q];
+        }
+        out[e] = acc;
+    }
+}
+
+// yh_s = sum_{t admissible} S_st xh_t for every node s
+__global__ void mv_couple(const double* __restrict__ S, const int64_t* __restrict__ S_off,
+                          const int64_t* __restrict__ adm_ptr, const int64_t* __restrict__ adm_col,
+                          const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off,
+                          const double* __restrict__ xh, double* __restrict__ yh, int nrhs) {
+    const int64_t s = blockIdx.x;
+    const int ks = (int)rank[s];
+    double* out = yh + coef_off[s] * nrhs;
+    for (int e = threadIdx.x; e < ks * nrhs; e += blockDim.x) {
+        const int a = e % ks, c = e / ks;
+        double acc = 0;
+        for (int64_t q = adm_ptr[s]; q < adm_ptr[s + 1]; ++q) {
+            const int64_t t = adm_col[q];
+            const int kt = (int)rank[t];
+            const double* St = S + S_off[q] + a;
+            const double* xt = xh + coef_off[t] * nrhs + (int64_t)c * kt;
+            for (int b = 0; b < kt; ++b) acc += St[(int64_t)b * ks] * xt[b];
+        }
+        out[e] = acc;
+    }
+}
+
+// yh_c += E_c yh_parent for the nodes c of one level
+__global__ void mv_down(const double* __restrict__ E, const int64_t* __restrict__ E_off,
+                        const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off, int64_t first,
+                        double* __restrict__ yh, int nrhs) {
+    const int64_t g = first + blockIdx.x;
+    const int64_t p = (g - 1) / 2;
+    const int kc = (int)rank[g], kp = (int)rank[p];
+    double* out = yh + coef_off[g] * nrhs;
+    const double* yp = yh + coef_off[p] * nrhs;
+    const double* Eg = E + E_off[g];
+    for (int e = threadIdx.x; e < kc * nrhs; e += blockDim.x) {
+        const int a = e % kc, c = e / kc;
+        double acc = 0;
+        for (int b = 0; b < kp; ++b) acc += Eg[a + (int64_t)b * kc] * yp[b + (int64_t)c * kp];
+        out[e] += acc;
+    }
+}
+
+// y_i = U_i yh_i + sum_{t near} D_it x_t on the leaves
+__global__ void mv_leaf_down(const double* __restrict__ U, const int64_t* __restrict__ U_off,
+                             const double* __restrict__ D, const int64_t* __restrict__ D_off,
+                             const int64_t* __restrict__ inad_ptr, const int64_t* __restrict__ inad_col,
+                             const int64_t* __restrict__ start, const int64_t* __restrict__ size,
+                             const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off,
+                             int64_t first, const double* __restrict__ yh, const double* __restrict__ x,
+                             int64_t ldx, double* __restrict__ y, int64_t ldy, int nrhs) {
+    const int i = blockIdx.x;
+    const int64_t g = first + i;
+    const int n = (int)size[g], k = (int)rank[g];
+    const double* Ui = U + U_off[i];
+    const double* yi = yh + coef_off[g] * nrhs;
+    const int64_t base = inad_ptr[first];
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
+        const int a = e % n, c = e / n;
+        double acc = 0;
+        for (int b = 0; b < k; ++b) acc += Ui[a + (int64_t)b * n] * yi[b + (int64_t)c * k];
+        for (int64_t q = inad_ptr[g]; q < inad_ptr[g + 1]; ++q) {
+            const int64_t t = inad_col[q];
+            const int nt = (int)size[t];
+            const double* Dq = D + D_off[q - base] + a;
+            const double* xt = x + start[t] + (int64_t)c * ldx;
+            for (int b = 0; b < nt; ++b) acc += Dq[(int64_t)b * n] * xt[b];
+        }
+        y[start[g] + a + (int64_t)c * ldy] = acc;
+    }
+}
+
+// r = b - y (column-major n x nrhs)
+__global__ void v_residual(const double* __restrict__ b, int64_t ldb, const double* __restrict__ y,
+                           int64_t ldy, double* __restrict__ r, int64_t ldr, int64_t n, int nrhs) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nrhs) return;
+    const int64_t a = e % n, c = e / n;
+    r[a + c * ldr] = b[a + c * ldb] - y[a + c * ldy];
+}
+
+// x += d
+__global__ void v_add(double* __restrict__ x, int64_t ldx, const double* __restrict__ d, int64_t ldd,
+                      int64_t n, int nrhs) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nrhs) return;
+    const int64_t a = e % n, c = e / n;
+    x[a + c * ldx] += d[a + c * ldd];
+}
+
+// out[c] = ||v_c||^2 (one block per column)
+__global__ void v_colnorm2(const double* __restrict__ v, int64_t ldv, int64_t n, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double acc = 0;
+    for (int64_t a = threadIdx.x; a < n; a += blockDim.x) {
+        const double t = v[a + c * ldv];
+        acc += t * t;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        out[c] = s;
+    }
+}
+
+void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, double* r, int64_t ldr,
+                  int64_t n, int nrhs, cudaStream_t s) {
+    const unsigned g = (unsigned)((n * nrhs + 255) / 256);
+    v_residual<<<g, 256, 0, s>>>(b, ldb, y, ldy, r, ldr, n, nrhs);
+}
+
+void add_dev(double* x, int64_t ldx, const double* d, int64_t ldd, int64_t n, int nrhs, cudaStream_t s) {
+    const unsigned g = (unsigned)((n * nrhs + 255) / 256);
+    v_add<<<g, 256, 0, s>>>(x, ldx, d, ldd, n, nrhs);
+}
+
+void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s) {
+    v_colnorm2<<<nrhs, 256, 0, s>>>(v, ldv, n, out);
+}
+
+// ------------------------------------------------------------------ driver
+void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
+                cudaStream_t s) {
+    const HostStructure& H = M.H;
+    const int d = H.d;
+    const int64_t ncoef = M.coef_off.back();
+    DevBuf xh, yh;
+    xh.alloc(std::max<int64_t>(1, ncoef * nrhs) * sizeof(double), s);
+    yh.alloc(std::max<int64_t>(1, ncoef * nrhs) * sizeof(double), s);
+    const int64_t first_leaf = (int64_t(1) << d) - 1;
+    const int nleaf = 1 << d;
+    const int64_t* rank = M.d_rank.as<int64_t>();
+    const int64_t* coef = M.d_coef_off.as<int64_t>();
+    mv_leaf_up<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
+                                     M.d_node_size.as<int64_t>(), rank, coef, first_leaf, x, ldx,
+                                     xh.as<double>(), nrhs);
+    for (int l = d; l >= 1; --l) {
+        const int64_t pf = (int64_t(1) << (l - 1)) - 1;
+        mv_up<<<1 << (l - 1), 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, pf,
+                                           xh.as<double>(), nrhs);
+    }
+    mv_couple<<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
+                                                  M.d_adm_ptr.as<int64_t>(), M.d_adm_col.as<int64_t>(), rank,
+                                                  coef, xh.as<double>(), yh.as<double>(), nrhs);
+    for (int l = 1; l <= d; ++l) {
+        const int64_t f = (int64_t(1) << l) - 1;
+        mv_down<<<1 << l, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, f,
+                                       yh.as<double>(), nrhs);
+    }
+    mv_leaf_down<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),
+                                       M.d_D_off.as<int64_t>(), M.d_inad_ptr.as<int64_t>(),
+                                       M.d_inad_col.as<int64_t>(), M.d_node_start.as<int64_t>(),
+                                       M.d_node_size.as<int64_t>(), rank, coef, first_leaf,
+                                       yh.as<double>(), x, ldx, y, ldy, nrhs);
+    H2_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace h2rs

@@ -1,0 +1,17 @@
+// H^2 matvec and refinement vector kernels (float64).
+#pragma once
+
+#include "h2rs_internal.h"
+
+namespace h2rs {
+
+void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
+                cudaStream_t s);
+
+// r = b - y;  x += d;  out[c] = ||v_c||^2  (all n x nrhs column-major, device)
+void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, double* r, int64_t ldr,
+                  int64_t n, int nrhs, cudaStream_t s);
+void add_dev(double* x, int64_t ldx, const double* d, int64_t ldd, int64_t n, int nrhs, cudaStream_t s);
+void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s);
+
+}  // namespace h2rs

@@ -1,0 +1,295 @@
+// Level planner: integer structure of the strong recursive skeletonisation.
+//
+// Sec. 2.2: at every level the inadmissible (near-field) blocks form a block-sparse
+// graph; a greedy colouring of it gives sets of boxes that can be skeletonised
+// concurrently.  Eliminating box i updates every block (j, k) with j, k in N(i)
+// (Sec. 2.1 step 3), so the blocks a level can touch are its near field plus the
+// "distance two" pairs outside it, plus fill carried from the level below whose
+// parent pair is not in the near field (moved to D or kept in F at the level
+// close).  Everything here depends only on the block partition, so it is built once
+// per matrix; box sizes and ranks are applied per level by the driver.
+#include <algorithm>
+#include <unordered_set>
+
+#include "h2rs_internal.h"
+
+namespace h2rs {
+
+int LevelStruct::find(int i, int j) const {
+    auto b = bcol.begin() + bptr[i];
+    auto e = bcol.begin() + bptr[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    if (it == e || *it != j) return -1;
+    return (int)(it - bcol.begin());
+}
+
+static inline uint64_t key(int a, int b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
+
+// near-field CSR of level l (local indices), from A's inadmissible CSR
+static void near_graph(const HostStructure& H, int l, LevelStruct& L) {
+    L.l = l;
+    L.first = (int64_t(1) << l) - 1;
+    L.cnt = 1 << l;
+    L.nb_ptr.assign(L.cnt + 1, 0);
+    L.nb_col.clear();
+    for (int i = 0; i < L.cnt; ++i) {
+        int64_t g = L.first + i;
+        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e)
+            L.nb_col.push_back((int)(H.inad_col[e] - L.first));
+        std::sort(L.nb_col.begin() + L.nb_ptr[i], L.nb_col.end());
+        L.nb_ptr[i + 1] = (int)L.nb_col.size();
+    }
+}
+
+// first-fit colouring in ascending box index, self loops ignored
+static void colour_level(LevelStruct& L) {
+    L.colour.assign(L.cnt, -1);
+    std::vector<int> mark;
+    for (int i = 0; i < L.cnt; ++i) {
+        mark.assign(L.nb_ptr[i + 1] - L.nb_ptr[i] + 2, 0);
+        for (int e = L.nb_ptr[i]; e < L.nb_ptr[i + 1]; ++e) {
+            int j = L.nb_col[e];
+            if (j == i) continue;
+            int c = L.colour[j];
+            if (c >= 0 && c < (int)mark.size()) mark[c] = 1;
+        }
+        int c = 0;
+        while (mark[c]) ++c;
+        L.colour[i] = c;
+    }
+    L.ncolour = L.cnt ? *std::max_element(L.colour.begin(), L.colour.end()) + 1 : 0;
+    L.cboxes.assign(L.ncolour, {});
+    for (int i = 0; i < L.cnt; ++i) L.cboxes[L.colour[i]].push_back(i);
+}
+
+static bool is_near(const LevelStruct& L, int i, int j) {
+    auto b = L.nb_col.begin() + L.nb_ptr[i];
+    auto e = L.nb_col.begin() + L.nb_ptr[i + 1];
+    return std::binary_search(b, e, j);
+}
+
+// merged block list = near field U fill pattern (distance-two pairs + carried)
+static void block_list(LevelStruct& L, const std::vector<std::pair<int, int>>& carried) {
+    std::vector<std::vector<int>> rows(L.cnt);
+    for (int i = 0; i < L.cnt; ++i)
+        for (int e = L.nb_ptr[i]; e < L.nb_ptr[i + 1]; ++e) rows[i].push_back(L.nb_col[e]);
+    std::vector<std::vector<int>> fill(L.cnt);
+    for (int i = 0; i < L.cnt; ++i)
+        for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
+            int j = L.nb_col[a];
+            for (int b = L.nb_ptr[i]; b < L.nb_ptr[i + 1]; ++b) {
+                int k = L.nb_col[b];
+                if (!is_near(L, j, k)) fill[j].push_back(k);
+            }
+        }
+    std::vector<std::vector<int>> carr(L.cnt);
+    for (auto& pq : carried)
+        if (!is_near(L, pq.first, pq.second)) {
+            fill[pq.first].push_back(pq.second);
+            carr[pq.first].push_back(pq.second);
+        }
+    L.bptr.assign(L.cnt + 1, 0);
+    L.bcol.clear();
+    L.bkind.clear();
+    for (int i = 0; i < L.cnt; ++i) {
+        auto& f = fill[i];
+        std::sort(f.begin(), f.end());
+        f.erase(std::unique(f.begin(), f.end()), f.end());
+        std::vector<int> merged;
+        merged.reserve(rows[i].size() + f.size());
+        std::merge(rows[i].begin(), rows[i].end(), f.begin(), f.end(), std::back_inserter(merged));
+        for (int j : merged) {
+            L.bcol.push_back(j);
+            L.bkind.push_back(is_near(L, i, j) ? 0 : 1);
+        }
+        L.bptr[i + 1] = (int)L.bcol.size();
+        std::sort(carr[i].begin(), carr[i].end());
+    }
+    int nb = L.nblocks();
+    L.btr.assign(nb, -1);
+    L.first_touch.assign(nb, INT_MAX);
+    for (int i = 0; i < L.cnt; ++i)
+        for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
+            L.btr[b] = L.find(L.bcol[b], i);
+            if (L.bkind[b] == 1 &&
+                std::binary_search(carr[i].begin(), carr[i].end(), L.bcol[b]))
+                L.first_touch[b] = -1;
+        }
+}
+
+// Schur targets per colour (target-owned accumulation) and first touches of fill
+static void schur_lists(LevelStruct& L) {
+    L.sch_cptr.assign(1, 0);
+    L.sch_tblk.clear();
+    L.sch_tptr.assign(1, 0);
+    L.sch_ci.clear();
+    L.sch_cA.clear();
+    L.sch_ckpos.clear();
+    struct Rec { int t, i, a, kpos; };
+    std::vector<Rec> recs;
+    for (int c = 0; c < L.ncolour; ++c) {
+        recs.clear();
+        for (int i : L.cboxes[c]) {
+            int n0 = L.nb_ptr[i], n1 = L.nb_ptr[i + 1];
+            for (int a = n0; a < n1; ++a) {
+                int j = L.nb_col[a];
+                int ablk = L.find(j, i);
+                for (int b = n0; b < n1; ++b) {
+                    int k = L.nb_col[b];
+                    int t = L.find(j, k);
+                    recs.push_back({t, i, ablk, b - n0});
+                    if (L.bkind[t] == 1 && L.first_touch[t] == INT_MAX) L.first_touch[t] = c;
+                }
+            }
+        }
+        std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) {
+            return x.t != y.t ? x.t < y.t : x.i < y.i;
+        });
+        for (size_t r = 0; r < recs.size(); ++r) {
+            if (r == 0 || recs[r].t != recs[r - 1].t) {
+                if (r) L.sch_tptr.push_back((int)L.sch_ci.size());
+                L.sch_tblk.push_back(recs[r].t);
+            }
+            L.sch_ci.push_back(recs[r].i);
+            L.sch_cA.push_back(recs[r].a);
+            L.sch_ckpos.push_back(recs[r].kpos);
+        }
+        if (!recs.empty()) L.sch_tptr.push_back((int)L.sch_ci.size());
+        L.sch_cptr.push_back((int)L.sch_tblk.size());
+    }
+}
+
+// block ids per near-field position and forward-solve target lists
+static void solve_lists(LevelStruct& L) {
+    L.nb_blk.resize(L.nb_col.size());
+    L.nb_blkT.resize(L.nb_col.size());
+    for (int i = 0; i < L.cnt; ++i)
+        for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
+            L.nb_blk[a] = L.find(i, L.nb_col[a]);
+            L.nb_blkT[a] = L.find(L.nb_col[a], i);
+        }
+    L.fl_cptr.assign(1, 0);
+    L.fl_tbox.clear();
+    L.fl_tptr.assign(1, 0);
+    L.fl_ci.clear();
+    L.fl_cpos.clear();
+    struct Rec { int j, i, pos; };
+    std::vector<Rec> recs;
+    for (int c = 0; c < L.ncolour; ++c) {
+        recs.clear();
+        for (int i : L.cboxes[c])
+            for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a)
+                recs.push_back({L.nb_col[a], i, a - L.nb_ptr[i]});
+        std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) {
+            return x.j != y.j ? x.j < y.j : x.i < y.i;
+        });
+        for (size_t r = 0; r < recs.size(); ++r) {
+            if (r == 0 || recs[r].j != recs[r - 1].j) {
+                if (r) L.fl_tptr.push_back((int)L.fl_ci.size());
+                L.fl_tbox.push_back(recs[r].j);
+            }
+            L.fl_ci.push_back(recs[r].i);
+            L.fl_cpos.push_back(recs[r].pos);
+        }
+        if (!recs.empty()) L.fl_tptr.push_back((int)L.fl_ci.size());
+        L.fl_cptr.push_back((int)L.fl_tbox.size());
+    }
+}
+
+static int64_t adm_entry(const HostStructure& H, int64_t gs, int64_t gt) {
+    auto b = H.adm_col.begin() + H.adm_ptr[gs];
+    auto e = H.adm_col.begin() + H.adm_ptr[gs + 1];
+    for (auto it = b; it != e; ++it)
+        if (*it == gt) return (int64_t)(it - H.adm_col.begin());
+    return -1;
+}
+
+// sources of each parent block from the four child pairs (level close)
+static void close_lists(const HostStructure& H, LevelStruct& C, const LevelStruct& P) {
+    int nb = P.nblocks();
+    C.cl_dblk.assign(4 * (size_t)nb, -1);
+    C.cl_fblk.assign(4 * (size_t)nb, -1);
+    C.cl_adm.assign(4 * (size_t)nb, -1);
+    for (int p = 0; p < P.cnt; ++p)
+        for (int b = P.bptr[p]; b < P.bptr[p + 1]; ++b) {
+            int q = P.bcol[b];
+            for (int a = 0; a < 2; ++a)
+                for (int bb = 0; bb < 2; ++bb) {
+                    int c = 2 * p + a, e = 2 * q + bb;
+                    int slot = 4 * b + 2 * a + bb;
+                    int blk = C.find(c, e);
+                    if (blk >= 0) {
+                        if (C.bkind[blk] == 0) C.cl_dblk[slot] = blk;
+                        else C.cl_fblk[slot] = blk;
+                    }
+                    C.cl_adm[slot] = adm_entry(H, C.first + c, C.first + e);
+                }
+        }
+}
+
+void build_plan(const HostStructure& H, Plan& P) {
+    P.d = H.d;
+    P.top = -1;
+    for (int l = 0; l <= H.d && P.top < 0; ++l) {
+        int64_t first = (int64_t(1) << l) - 1, last = (int64_t(1) << (l + 1)) - 1;
+        if (H.adm_ptr[last] - H.adm_ptr[first] > 0) P.top = l;
+    }
+    P.levels.clear();
+    std::vector<std::pair<int, int>> carried;
+    int lowest = P.top < 0 ? H.d + 1 : P.top;       // skeletonised levels d .. t
+    for (int l = H.d; l >= lowest; --l) {
+        LevelStruct L;
+        near_graph(H, l, L);
+        colour_level(L);
+        block_list(L, carried);
+        schur_lists(L);
+        solve_lists(L);
+        for (int i = 0; i < L.cnt; ++i)
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) L.near_entry.push_back(-1);
+        if (l == H.d) {                              // leaf near blocks come from A
+            for (int i = 0; i < L.cnt; ++i) {
+                int64_t g = L.first + i;
+                for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
+                    int j = (int)(H.inad_col[e] - L.first);
+                    L.near_entry[L.find(i, j)] = e - H.inad_ptr[L.first];
+                }
+            }
+        }
+        // fill carried to the parent level: parents of fill pairs
+        carried.clear();
+        for (int i = 0; i < L.cnt; ++i)
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b)
+                if (L.bkind[b] == 1) carried.push_back({i / 2, L.bcol[b] / 2});
+        std::sort(carried.begin(), carried.end());
+        carried.erase(std::unique(carried.begin(), carried.end()), carried.end());
+        P.levels.push_back(std::move(L));
+    }
+    // the level holding the dense top matrix: t-1 (or the leaves if nothing is
+    // admissible, in which case no level is skeletonised)
+    int lt = P.top < 0 ? H.d : P.top - 1;
+    LevelStruct T;
+    near_graph(H, lt, T);
+    colour_level(T);
+    if (P.top < 0) {
+        block_list(T, {});
+        for (int i = 0; i < T.cnt; ++i)
+            for (int b = T.bptr[i]; b < T.bptr[i + 1]; ++b) T.near_entry.push_back(-1);
+        for (int i = 0; i < T.cnt; ++i) {
+            int64_t g = T.first + i;
+            for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
+                int j = (int)(H.inad_col[e] - T.first);
+                T.near_entry[T.find(i, j)] = e - H.inad_ptr[T.first];
+            }
+        }
+    } else {
+        block_list(T, carried);
+    }
+    P.toplev = std::move(T);
+    // close lists: level l -> l-1 (parent of the last skeletonised level is toplev)
+    for (size_t a = 0; a < P.levels.size(); ++a) {
+        const LevelStruct& par = (a + 1 < P.levels.size()) ? P.levels[a + 1] : P.toplev;
+        close_lists(H, P.levels[a], par);
+    }
+}
+
+}  // namespace h2rs

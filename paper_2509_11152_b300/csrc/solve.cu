@@ -1,0 +1,335 @@
+// Solve (Alg. 3): forward sweep over the levels in elimination order (Q~^T, then the
+// L update per colour), diagonal L solves and upsweep; float64 dense top solve;
+// downsweep, diagonal U solves and the backward sweep in reverse colour order (U
+// update, then Q~).  Vectors of a level hold each box's coordinates contiguously:
+// box i at offset voff[i]*nrhs, n_i x nrhs column-major.
+#include "factor_impl.h"
+
+namespace h2rs {
+
+// ------------------------------------------------------------------ kernels
+template <class T>
+__global__ void s_load(const double* __restrict__ b, int64_t ldb, int nrhs, const int64_t* __restrict__ start,
+                       const int* __restrict__ n, const int64_t* __restrict__ voff, T* __restrict__ x) {
+    const int i = blockIdx.x;
+    const int ni = n[i];
+    T* xi = x + voff[i] * nrhs;
+    const double* bi = b + start[i];
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int a = e % ni, c = e / ni;
+        xi[e] = (T)bi[a + (int64_t)c * ldb];
+    }
+}
+
+template <class T>
+__global__ void s_store(double* __restrict__ b, int64_t ldb, int nrhs, const int64_t* __restrict__ start,
+                        const int* __restrict__ n, const int64_t* __restrict__ voff, const T* __restrict__ x) {
+    const int i = blockIdx.x;
+    const int ni = n[i];
+    const T* xi = x + voff[i] * nrhs;
+    double* bi = b + start[i];
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int a = e % ni, c = e / ni;
+        bi[a + (int64_t)c * ldb] = (double)xi[e];
+    }
+}
+
+// x_i <- Q~_i^T x_i (trans = 1) or Q~_i x_i (trans = 0) for the boxes of a colour
+template <class T>
+__global__ void s_apply_q(const int* __restrict__ boxes, const int* __restrict__ n, const T* __restrict__ Q,
+                          const int64_t* __restrict__ Q_off, const int64_t* __restrict__ voff, T* __restrict__ x,
+                          int nrhs, int trans) {
+    const int i = boxes[blockIdx.x];
+    const int ni = n[i];
+    if (ni == 0) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* xs = reinterpret_cast<T*>(sm_raw);
+    T* xi = x + voff[i] * nrhs;
+    const T* Qi = Q + Q_off[i];
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) xs[e] = xi[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int a = e % ni, c = e / ni;
+        T acc = 0;
+        if (trans) {
+            const T* qa = Qi + (int64_t)a * ni;
+            for (int q = 0; q < ni; ++q) acc += qa[q] * xs[q + c * ni];
+        } else {
+            for (int q = 0; q < ni; ++q) acc += Qi[a + (int64_t)q * ni] * xs[q + c * ni];
+        }
+        xi[e] = acc;
+    }
+}
+
+// forward L update of a colour, target owned: x_j -= sum_i W_L^i[j] x_{i_R}
+template <class T>
+__global__ void s_fwd_l(const int* __restrict__ tbox, const int* __restrict__ tptr, const int* __restrict__ ci,
+                        const int* __restrict__ cpos, int cur, const int* __restrict__ colour,
+                        const int* __restrict__ n, const int* __restrict__ kt, const int* __restrict__ nb_ptr,
+                        const int* __restrict__ nbofs, const T* __restrict__ WL,
+                        const int64_t* __restrict__ WL_off, const int* __restrict__ WLld,
+                        const int64_t* __restrict__ voff, T* __restrict__ x, int nrhs) {
+    const int t = blockIdx.x;
+    const int j = tbox[t];
+    const int nj = n[j];
+    const int lo = (colour[j] == cur) ? nj - kt[j] : 0;
+    const int m = nj - lo;
+    T* xj = x + voff[j] * nrhs;
+    for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+        const int a = e % m, c = e / m;
+        T acc = 0;
+        for (int q = tptr[t]; q < tptr[t + 1]; ++q) {
+            const int i = ci[q];
+            const int ri = n[i] - kt[i];
+            if (ri <= 0) continue;
+            const int row = nbofs[nb_ptr[i] + cpos[q]] + a;
+            const T* W = WL + WL_off[i] + row;
+            const int64_t ld = WLld[i];
+            const T* xr = x + voff[i] * nrhs + (int64_t)c * n[i];
+            for (int b = 0; b < ri; ++b) acc += W[(int64_t)b * ld] * xr[b];
+        }
+        xj[lo + a + (int64_t)c * nj] -= acc;
+    }
+}
+
+// backward U update of a colour: x_{i_R} -= sum_k W_U^i[k] x_k (box owned)
+template <class T>
+__global__ void s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n, const int* __restrict__ kt,
+                        const int* __restrict__ nb_ptr, const int* __restrict__ nb_col,
+                        const int* __restrict__ nbofs, const T* __restrict__ WU,
+                        const int64_t* __restrict__ WU_off, const int64_t* __restrict__ voff,
+                        T* __restrict__ x, int nrhs) {
+    const int i = boxes[blockIdx.x];
+    const int ni = n[i], ri = ni - kt[i];
+    if (ri <= 0) return;
+    T* xi = x + voff[i] * nrhs;
+    const T* Wi = WU + WU_off[i];
+    for (int e = threadIdx.x; e < ri * nrhs; e += blockDim.x) {
+        const int a = e % ri, c = e / ri;
+        T acc = 0;
+        for (int p = nb_ptr[i]; p < nb_ptr[i + 1]; ++p) {
+            const int j = nb_col[p];
+            const int o = nbofs[p];
+            const T* xs;
+            int w;
+            if (j == i) { xs = xi + (int64_t)c * ni + ri; w = kt[i]; }
+            else { xs = x + voff[j] * nrhs + (int64_t)c * n[j]; w = n[j]; }
+            const T* Wc = Wi + a + (int64_t)o * ri;
+            for (int b = 0; b < w; ++b) acc += Wc[(int64_t)b * ri] * xs[b];
+        }
+        xi[a + (int64_t)c * ni] -= acc;
+    }
+}
+
+// diagonal solves with the redundant blocks: lower (P, L) or upper (U); one warp per
+// (box, right-hand side)
+template <class T>
+__global__ void s_diag(const int* __restrict__ n, const int* __restrict__ kt, const T* __restrict__ LU,
+                       const int64_t* __restrict__ LU_off, const int* __restrict__ piv,
+                       const int64_t* __restrict__ piv_off, const int64_t* __restrict__ voff,
+                       T* __restrict__ x, int nrhs, int cnt, int upper) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= cnt * nrhs) return;
+    const int i = w / nrhs, c = w % nrhs;
+    const int ni = n[i], r = ni - kt[i];
+    if (r <= 0) return;
+    T* xr = x + voff[i] * nrhs + (int64_t)c * ni;
+    const T* F = LU + LU_off[i];
+    if (!upper) {
+        const int* pv = piv + piv_off[i];
+        if (lane == 0)
+            for (int j = 0; j < r; ++j) {
+                const int p = pv[j];
+                if (p < j || p >= r) break;        // never produced by the LU kernel
+                if (p != j) { const T t0 = xr[j]; xr[j] = xr[p]; xr[p] = t0; }
+            }
+        __syncwarp();
+        for (int j = 0; j < r; ++j) {
+            const T xj = xr[j];
+            for (int a = j + 1 + lane; a < r; a += 32) xr[a] -= F[a + (int64_t)j * r] * xj;
+            __syncwarp();
+        }
+    } else {
+        for (int j = r - 1; j >= 0; --j) {
+            if (lane == 0) xr[j] /= F[j + (int64_t)j * r];
+            __syncwarp();
+            const T xj = xr[j];
+            for (int a = lane; a < j; a += 32) xr[a] -= F[a + (int64_t)j * r] * xj;
+            __syncwarp();
+        }
+    }
+}
+
+// skeleton parts of the two children <-> parent box (up: gather, down: scatter)
+template <class T>
+__global__ void s_sweep(const int* __restrict__ cn, const int* __restrict__ ckt, const int64_t* __restrict__ cvoff,
+                        T* __restrict__ cx, const int64_t* __restrict__ pvoff, T* __restrict__ px,
+                        int nrhs, int up) {
+    const int p = blockIdx.x;
+    const int c1 = 2 * p, c2 = 2 * p + 1;
+    const int k1 = ckt[c1], k2 = ckt[c2];
+    const int np = k1 + k2;
+    T* xp = px + pvoff[p] * nrhs;
+    for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+        const int a = e % np, c = e / np;
+        const int ch = a < k1 ? c1 : c2;
+        const int a1 = a < k1 ? a : a - k1;
+        const int nc = cn[ch];
+        T* xc = cx + cvoff[ch] * nrhs + (int64_t)c * nc + (nc - ckt[ch]) + a1;
+        if (up) xp[e] = *xc;
+        else *xc = xp[e];
+    }
+}
+
+// top level: gather into a float64 dense vector, solve with L_t U_t, scatter back
+template <class T>
+__global__ void s_top_io(const int* __restrict__ n, const int64_t* __restrict__ voff,
+                         const int64_t* __restrict__ toff, T* __restrict__ x, double* __restrict__ xt,
+                         int64_t nt, int nrhs, int to_dense) {
+    const int p = blockIdx.x;
+    const int np = n[p];
+    T* xp = x + voff[p] * nrhs;
+    for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
+        const int a = e % np, c = e / np;
+        double* d = xt + toff[p] + a + (int64_t)c * nt;
+        if (to_dense) *d = (double)xp[e];
+        else xp[e] = (T)*d;
+    }
+}
+
+__global__ void s_top_solve(const double* __restrict__ LU, const int* __restrict__ piv, int64_t nt,
+                            double* __restrict__ xt) {
+    double* x = xt + (int64_t)blockIdx.x * nt;
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        for (int64_t j = 0; j < nt; ++j) {
+            const int64_t p = piv[j];
+            if (p < j || p >= nt) break;           // never produced by the panel kernel
+            if (p != j) { const double t0 = x[j]; x[j] = x[p]; x[p] = t0; }
+        }
+    __syncthreads();
+    for (int64_t j = 0; j < nt; ++j) {
+        const double xj = x[j];
+        for (int64_t a = j + 1 + tid; a < nt; a += blockDim.x) x[a] -= LU[a + j * nt] * xj;
+        __syncthreads();
+    }
+    for (int64_t j = nt - 1; j >= 0; --j) {
+        if (tid == 0) x[j] /= LU[j + j * nt];
+        __syncthreads();
+        const double xj = x[j];
+        for (int64_t a = tid; a < j; a += blockDim.x) x[a] -= LU[a + j * nt] * xj;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ driver
+template <class T>
+void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
+    cudaStream_t s = stream;
+    const Plan& P = A->plan;
+    const size_t nl = P.levels.size();
+    std::vector<DevBuf> vec(nl + 1);
+    for (size_t a = 0; a <= nl; ++a)
+        vec[a].alloc(std::max<int64_t>(1, lv[a].vtot * nrhs) * sizeof(T), s);
+    // leaf starts (tree order) of the first level's boxes
+    LevelRT& L0 = lv[0];
+    DevBuf d_start;
+    {
+        std::vector<int64_t> st(L0.cnt);
+        for (int i = 0; i < L0.cnt; ++i) st[i] = A->H.node_start[L0.S->first + i];
+        upload(d_start, st, s);
+    }
+    s_load<T><<<L0.cnt, 256, 0, s>>>(b, ldb, nrhs, d_start.as<int64_t>(), L0.d_n.as<int>(),
+                                     L0.d_voff.as<int64_t>(), vec[0].as<T>());
+    DevBuf d_boxes;
+    std::vector<std::vector<int>> cptr(nl);
+    {
+        std::vector<int> all;
+        for (size_t a = 0; a < nl; ++a) {
+            cptr[a].push_back((int)all.size());
+            for (auto& cb : P.levels[a].cboxes) {
+                all.insert(all.end(), cb.begin(), cb.end());
+                cptr[a].push_back((int)all.size());
+            }
+        }
+        upload(d_boxes, all, s);
+    }
+    // forward
+    for (size_t a = 0; a < nl; ++a) {
+        LevelRT& L = lv[a];
+        const LevelStruct& S = *L.S;
+        int nmax = 1;
+        for (int v : L.n) nmax = std::max(nmax, v);
+        const int qsm = nmax * nrhs * (int)sizeof(T);
+        for (int c = 0; c < S.ncolour; ++c) {
+            const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;
+            s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
+                                              L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
+                                              vec[a].as<T>(), nrhs, 1);
+            const int t0 = S.fl_cptr[c], nt_ = S.fl_cptr[c + 1] - t0;
+            if (nt_)
+                s_fwd_l<T><<<nt_, 256, 0, s>>>(L.d_fl_tbox.as<int>() + t0, L.d_fl_tptr.as<int>() + t0,
+                                               L.d_fl_ci.as<int>(), L.d_fl_cpos.as<int>(), c,
+                                               L.d_colour.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(),
+                                               L.d_nb_ptr.as<int>(), L.d_nbofs.as<int>(), L.WL.as<T>(),
+                                               L.d_WL_off.as<int64_t>(), L.d_WLld.as<int>(),
+                                               L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
+        }
+        const int nw = L.cnt * nrhs;
+        s_diag<T><<<(nw + 7) / 8, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.LU.as<T>(),
+                                               L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
+                                               L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(),
+                                               vec[a].as<T>(), nrhs, L.cnt, 0);
+        LevelRT& Pn = lv[a + 1];
+        s_sweep<T><<<Pn.cnt, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.d_voff.as<int64_t>(),
+                                          vec[a].as<T>(), Pn.d_voff.as<int64_t>(), vec[a + 1].as<T>(),
+                                          nrhs, 1);
+    }
+    // top
+    LevelRT& Tl = lv[nl];
+    if (nt > 0) {
+        DevBuf xt;
+        xt.alloc(nt * nrhs * sizeof(double), s);
+        s_top_io<T><<<Tl.cnt, 256, 0, s>>>(Tl.d_n.as<int>(), Tl.d_voff.as<int64_t>(), d_toff.as<int64_t>(),
+                                           vec[nl].as<T>(), xt.as<double>(), nt, nrhs, 1);
+        s_top_solve<<<nrhs, 1024, 0, s>>>(Dt.as<double>(), tpiv.as<int>(), nt, xt.as<double>());
+        s_top_io<T><<<Tl.cnt, 256, 0, s>>>(Tl.d_n.as<int>(), Tl.d_voff.as<int64_t>(), d_toff.as<int64_t>(),
+                                           vec[nl].as<T>(), xt.as<double>(), nt, nrhs, 0);
+    }
+    // backward
+    for (size_t a = nl; a-- > 0;) {
+        LevelRT& L = lv[a];
+        const LevelStruct& S = *L.S;
+        LevelRT& Pn = lv[a + 1];
+        s_sweep<T><<<Pn.cnt, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.d_voff.as<int64_t>(),
+                                          vec[a].as<T>(), Pn.d_voff.as<int64_t>(), vec[a + 1].as<T>(),
+                                          nrhs, 0);
+        const int nw = L.cnt * nrhs;
+        s_diag<T><<<(nw + 7) / 8, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.LU.as<T>(),
+                                               L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
+                                               L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(),
+                                               vec[a].as<T>(), nrhs, L.cnt, 1);
+        int nmax = 1;
+        for (int v : L.n) nmax = std::max(nmax, v);
+        const int qsm = nmax * nrhs * (int)sizeof(T);
+        for (int c = S.ncolour - 1; c >= 0; --c) {
+            const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;
+            s_bwd_u<T><<<nb, 256, 0, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.d_kt.as<int>(),
+                                          L.d_nb_ptr.as<int>(), L.d_nb_col.as<int>(), L.d_nbofs.as<int>(),
+                                          L.WU.as<T>(), L.d_WU_off.as<int64_t>(), L.d_voff.as<int64_t>(),
+                                          vec[a].as<T>(), nrhs);
+            s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
+                                              L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
+                                              vec[a].as<T>(), nrhs, 0);
+        }
+    }
+    s_store<T><<<L0.cnt, 256, 0, s>>>(b, ldb, nrhs, d_start.as<int64_t>(), L0.d_n.as<int>(),
+                                      L0.d_voff.as<int64_t>(), vec[0].as<T>());
+    H2_CUDA_CHECK(cudaGetLastError());
+}
+
+template void FactorImpl<double>::solve_dev(double*, int, int64_t);
+template void FactorImpl<float>::solve_dev(double*, int, int64_t);
+
+}  // namespace h2rs

@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA library (through its C-ABI) against the CPU oracle.
+
+Bars (stated by the method's specification for this build):
+  * float64 factor + solve at the same eps_lu: relative solution difference <= 1e-10,
+    identical augmented ranks, colours, block pattern and prefix-sum offsets;
+  * float32 factor + float64 refinement: backward error ||Ax-b||/(||A|| ||x||) <= 1e-10,
+    measured with the oracle's own H^2 matvec;
+  * float64 H^2 matvec: relative difference <= 1e-13.
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+from h2gen import rhs
+from oracle import dense, rs
+
+from conftest import problem
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+BERR_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_11152_b300 import build
+    build.build()
+    import paper_2509_11152_b300 as h2
+    return h2
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_solution(name, eps, nrhs, seed, **over):
+    pb = problem(name, **over)
+    A = pb.A.numpy()
+    b = rhs(A.n, nrhs, seed=seed)
+    Z = rs.factorize(A, eps, pb.norm_a)
+    return pb, A, b, Z, rs.solve(Z, b)
+
+
+CASES = [
+    ("cov2d", dict(n=1024, leaf=32), 1e-8),
+    ("cov2d", {}, 1e-8),                                  # the 4,096-point workload itself
+    ("laplace2d", dict(n=4096, leaf=32, eta=0.7), 1e-6),
+    ("matern3d", dict(n=2048, leaf=32), 1e-6),
+    ("sphere", dict(n=4096, leaf=64), 1e-5),
+    ("gauss3d", dict(n=1500, leaf=32), 1e-6),            # ragged leaves (46/47 points)
+]
+IDS = [f"{c[0]}-{c[1].get('n', 'full')}" for c in CASES]
+
+
+def _gpu_solve(h, pb, b, eps, prec):
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, eps, pb.norm_a, prec)
+    x = h.colmajor(torch.from_numpy(b).cuda())
+    h.h2_solve(Z, x)
+    return M, Z, x.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,over,eps", CASES, ids=IDS)
+def test_fp64_factor_solve_matches_oracle(h, name, over, eps):
+    pb, A, b, Z0, x0 = oracle_solution(name, eps, 2, 1, **over)
+    M, Z, x = _gpu_solve(h, pb, b, eps, h.H2_PREC_FP64)
+    rel = np.linalg.norm(x - x0) / np.linalg.norm(x0)
+    assert rel <= FP64_TOL, rel
+    st = h.h2_factor_stats_get(Z)
+    assert st["nlevels"] == len(Z0.levels)
+    assert st["top_size"] == sum(Z0.top_sizes)
+    for li, lv in enumerate(Z0.levels):
+        lay = h.h2_layout_get(Z, li)
+        assert np.array_equal(lay["sizes"], np.asarray(lv.sizes))
+        assert np.array_equal(lay["ranks"], np.asarray([bx.kt for bx in lv.boxes]))
+        assert np.array_equal(lay["colour"], np.asarray(lv.colour, np.int32))
+        assert np.array_equal(lay["row_ptr"], lv.layout["row_ptr"])
+        assert np.array_equal(lay["col"], lv.layout["col"])
+        assert np.array_equal(lay["kind"], lv.layout["kind"].astype(np.int32))
+        assert np.array_equal(lay["offset"], lv.layout["offset"])
+
+
+@pytest.mark.parametrize("name,over,eps", CASES, ids=IDS)
+def test_fp32_factor_with_refinement(h, name, over, eps):
+    pb, A, b, Z0, x0 = oracle_solution(name, eps, 2, 1, **over)
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_FP32)
+    bt = h.colmajor(torch.from_numpy(b).cuda())
+    xt = h.colmajor(torch.zeros_like(bt))
+    it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
+    assert ok and berr <= BERR_TOL
+    x = xt.cpu().numpy()
+    nw, _ = dense.backward_error(A, x, b, pb.norm_a)       # the oracle's own matvec
+    assert nw <= BERR_TOL, nw
+    # ranks of the float32 factor stay those of the float64 oracle almost everywhere
+    lay = h.h2_layout_get(Z, 0)
+    r0 = np.asarray([bx.kt for bx in Z0.levels[0].boxes])
+    assert np.mean(lay["ranks"] == r0) > 0.9
+
+
+@pytest.mark.parametrize("name,over", [("cov2d", dict(n=1024, leaf=32)), ("sphere", dict(n=4096, leaf=64)),
+                                       ("gauss3d", dict(n=1500, leaf=32))])
+def test_matvec_matches_oracle(h, name, over):
+    pb = problem(name, **over)
+    A = pb.A.numpy()
+    x = rhs(A.n, 3, seed=5)
+    y0 = dense.matvec(A, x)
+    M = h.h2_matrix_create(pb.A)
+    xt = h.colmajor(torch.from_numpy(x).cuda())
+    yt = h.colmajor(torch.zeros_like(xt))
+    h.h2_matvec(M, xt, yt)
+    y = yt.cpu().numpy()
+    assert np.linalg.norm(y - y0) / np.linalg.norm(y0) <= 1e-13
+
+
+def test_zero_truncation_matches_dense_solve(h):
+    pb = problem("cov2d", n=1024, leaf=32)
+    A = pb.A.numpy()
+    b = rhs(A.n, 2, seed=3)
+    xd = np.linalg.solve(dense.expand(A), b)
+    _, _, x = _gpu_solve(h, pb, b, 1e-13, h.H2_PREC_FP64)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-11
+
+
+def test_no_admissible_block_is_dense_lu(h):
+    pb = problem("cov2d", n=256, leaf=16, eta=1e-6)
+    A = pb.A.numpy()
+    assert A.top_level() is None
+    b = rhs(A.n, 2, seed=4)
+    xd = np.linalg.solve(dense.expand(A), b)
+    M, Z, x = _gpu_solve(h, pb, b, 1e-6, h.H2_PREC_FP64)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-13
+    assert h.h2_factor_stats_get(Z)["nlevels"] == 0
+
+
+def test_single_box_depth_zero(h):
+    pb = problem("cov2d", n=50, leaf=64)
+    assert pb.A.depth == 0
+    A = pb.A.numpy()
+    b = rhs(A.n, 1, seed=6)
+    xd = np.linalg.solve(dense.expand(A), b)
+    _, _, x = _gpu_solve(h, pb, b, 1e-8, h.H2_PREC_FP64)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-13
+
+
+def test_many_rhs_and_host_pointers(h):
+    name, over, eps = "laplace2d", dict(n=4096, leaf=32, eta=0.7), 1e-6
+    pb, A, b, Z0, x0 = oracle_solution(name, eps, 8, 2, **over)
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_FP64)
+    xh = h.colmajor(torch.from_numpy(b))              # host memory: copied by the library
+    h.h2_solve(Z, xh)
+    xd = h.colmajor(torch.from_numpy(b).cuda())
+    h.h2_solve(Z, xd)
+    assert np.array_equal(xh.numpy(), xd.cpu().numpy())
+    assert np.linalg.norm(xh.numpy() - x0) / np.linalg.norm(x0) <= FP64_TOL
+
+
+def test_refinement_without_corrections_reports_no_convergence(h):
+    pb = problem("cov2d", n=1024, leaf=32)
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, 1e-4, pb.norm_a, h.H2_PREC_FP32)
+    b = torch.from_numpy(rhs(pb.A.n, 1, seed=7)).cuda()
+    x = torch.zeros_like(b)
+    it, berr, ok = h.h2_refine_solve(Z, M, b, x, 1e-14, 0)
+    assert not ok and it == 0 and 1e-12 < berr < 1e-2
+
+
+def test_singular_matrix_reports_error_and_context_survives(h):
+    pb = problem("cov2d", n=512, leaf=32)
+    Azero = pb.A.to("cpu")
+    Azero.D = torch.zeros_like(Azero.D)
+    Azero.S = torch.zeros_like(Azero.S)
+    M = h.h2_matrix_create(Azero)
+    with pytest.raises(h.H2Error) as e:
+        h.h2_factor_create(M, 1e-8, pb.norm_a, h.H2_PREC_FP64)
+    assert e.value.code == -3                       # H2_ERR_SINGULAR
+    # the CUDA context is still usable
+    b = rhs(pb.A.n, 1, seed=8)
+    _, _, x = _gpu_solve(h, pb, b, 1e-8, h.H2_PREC_FP64)
+    assert np.isfinite(x).all()
