@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the H^2 strong recursive skeletonisation solver on one B300.
+
+One step = factorise the H^2 matrix in float32 (float64 top level) and solve with
+float64 iterative refinement until the normwise backward error
+||Ax-b|| / (||A|| ||x||) <= 1e-10, on the 1,048,576-point Fibonacci-sphere problem
+(kernel 1/(4 pi r), leaf 128, eta 1, eps_lu 1e-5, one N(0,1) right-hand side).
+
+Prints one JSON line (rank 0).  ``value`` is the device time of a step with the
+matrix and right-hand side resident in HBM; ``e2e`` repeats the step through the
+C-ABI with host buffers (matrix upload and solution download inside the timing).
+``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
+Several GPUs run independent replicas (a single system does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+solve s at N=1M: mixed vs FP64 at bwd err≤1e-10; HBM/FLOP roofline %"
+BERR_TOL = 1e-10
+MAXIT = 50
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="sphere")
+    p.add_argument("--n", type=int, default=0, help="override the problem size (testing only)")
+    p.add_argument("--fp64-arm", type=int, default=1, help="also time the float64 factor arm once")
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-baseline", type=int, default=1)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ distributed
+def _dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    rank = int(os.environ.get("RANK", "0"))
+    if backend == "nccl":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist.init_process_group(backend)
+    return dist, rank, ws
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ helpers
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak of a B300: 148 SMs x 128 FP32 lanes x 2 flop per clock."""
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _problem(args, device):
+    from h2gen import make_problem
+    over = {} if not args.n else {"n": args.n}
+    return make_problem(args.workload, device=device, **over)
+
+
+def _rhs(n, nrhs, device):
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(0)
+    b = torch.randn(n, nrhs, generator=g, dtype=torch.float64)
+    return b.to(device)
+
+
+# ------------------------------------------------------------------ oracle timing
+def _oracle_sample(workload: str, n_sample: int):
+    """Oracle factor + float64 refined solve on a smaller member of the workload's
+    family; returns (seconds, n_sample, iterations, berr)."""
+    from h2gen import make_problem, rhs
+    from oracle import dense, rs
+    pb = make_problem(workload, n=n_sample)
+    A = pb.A.numpy()
+    b = rhs(A.n, pb.workload.nrhs, seed=0)
+    t0 = time.perf_counter()
+    Z = rs.factorize(A, pb.workload.tol, pb.norm_a)
+    x = rs.solve(Z, b)
+    it = 0
+    while True:
+        r = b - dense.matvec(A, x)
+        berr = float(np.max(np.linalg.norm(r, axis=0) / (pb.norm_a * np.linalg.norm(x, axis=0))))
+        if berr <= BERR_TOL or it >= MAXIT:
+            break
+        x = x + rs.solve(Z, r)
+        it += 1
+    return time.perf_counter() - t0, A.n, it, berr
+
+
+def _blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [1])
+    except Exception:
+        return 1
+
+
+def _cpu_baseline(workload: str, n_full: int, n_sample: int) -> dict:
+    sec, ns, it, berr = _oracle_sample(workload, n_sample)
+    return {"value": sec * n_full / ns, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"oracle (float64 numpy) factor + refined solve of the same family at N={ns} "
+                      f"({sec:.1f} s, {it} corrections, berr {berr:.1e}), scaled linearly to N={n_full}"}
+
+
+def run_reference(args, dist, rank, ws):
+    if rank != 0:
+        return
+    from h2gen import WORKLOADS
+    n_full = args.n or WORKLOADS[args.workload].n
+    n_sample = min(n_full, 16384)
+    for _ in range(args.warmup):
+        _oracle_sample(args.workload, min(n_sample, 4096))
+    times = []
+    info = None
+    for _ in range(args.steps):
+        sec, ns, it, berr = _oracle_sample(args.workload, n_sample)
+        times.append(sec * n_full / ns)
+        info = (sec, ns, it, berr)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} N={n_full}", "precision": "float64 oracle"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
+                             "sample": f"each step: oracle factor + refined solve at N={info[1]} "
+                                       f"({info[0]:.1f} s), scaled linearly to N={n_full}"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, dist, rank, ws):
+    import torch
+    from paper_2509_11152_b300 import build
+    build.build()
+    import paper_2509_11152_b300 as h
+    from paper_2509_11152_b300 import binding
+
+    dev_index = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev_index)
+    t0 = time.perf_counter()
+    pb = _problem(args, "cuda")
+    A = pb.A
+    w = pb.workload
+    nrhs = w.nrhs
+    setup_s = time.perf_counter() - t0
+    M = h.h2_matrix_create(A)
+    b = h.colmajor(_rhs(A.n, nrhs, "cuda"))
+    x = h.colmajor(torch.zeros_like(b))
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def step(prec, flags=0):
+        Z = h.h2_factor_create(M, w.tol, pb.norm_a, prec, stream=stream, flags=flags)
+        x.zero_()
+        it, berr, ok = h.h2_refine_solve(Z, M, b, x, BERR_TOL, MAXIT)
+        return Z, it, berr, ok
+
+    for _ in range(max(args.warmup, 0)):
+        Z, it, berr, ok = step(h.H2_PREC_FP32)
+        del Z
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    _barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = binding.lib().h2_kernel_launch_count()
+    e0.record()
+    results = []
+    kernel = {}
+    for s in range(args.steps):
+        Z, it, berr, ok = step(h.H2_PREC_FP32, flags=binding.H2_FLAG_TIME_KERNELS)
+        results.append((it, berr, ok))
+        st = h.h2_factor_stats_get(Z)
+        for k, v in st["kernel_ms"].items():
+            kernel.setdefault(k, [0.0, 0])
+            kernel[k][0] += v
+            kernel[k][1] += st["kernel_launches"][k]
+        last_stats = st
+        del Z
+    e1.record()
+    torch.cuda.synchronize()
+    launches = binding.lib().h2_kernel_launch_count() - launches0
+    _barrier(dist)
+    clk = clocks.stop()
+    t_step = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_step = _max_over_ranks(dist, t_step)
+    value = t_step / ws
+
+    # dominant factorisation kernel and its roofline
+    peaks, peak_kind = _peaks()
+    names = {"basis": "augment", "proj": "project", "schur": "schur", "lu": "lu_trsm", "trsm": "lu_trsm"}
+    dom = max(kernel, key=lambda k: kernel[k][0])
+    dom_ms = kernel[dom][0] / args.steps
+    phase = names.get(dom)
+    flops = last_stats["phase_flops"].get(phase, 0.0) if phase else 0.0
+    bytes_ = last_stats["phase_bytes"].get(phase, 0.0) if phase else 0.0
+    sm_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    alu = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    hbm = peaks["hbm_gbs"]
+    ach_gbs = bytes_ / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    ach_tf = flops / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
+    ai = flops / bytes_ if bytes_ else float("inf")
+    if ai * hbm / 1e3 < alu:          # bandwidth roof is the lower one
+        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm}
+    else:
+        roof = {"bound": "alu", "achieved": ach_tf, "peak": alu, "unit": "TFLOP/s", "frac": ach_tf / alu}
+    roof.update({"kernel": dom, "ms_per_step": dom_ms, "launches_per_step": kernel[dom][1] / args.steps,
+                 "algorithmic_flops": flops, "algorithmic_bytes": bytes_,
+                 "peak_source": peak_kind + (" (alu: 148 SMs x 128 FP32 lanes x 2 x max SM clock)"
+                                            if roof["bound"] == "alu" else ""),
+                 "traffic": None})
+
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{w.name} N={A.n} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={nrhs}",
+                       "precision": "float32 factor/solve, float64 top LU + refinement",
+                       "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (matrix "
+                       f"{A.nbytes() / 1e9:.1f} GB)", "setup_s": round(setup_s, 1),
+                       "csp": pb.stats["csp"], "kmax": pb.stats["kmax"]},
+            "refinement": {"iters": [r[0] for r in results], "berr": [r[1] for r in results],
+                           "converged": all(r[2] for r in results)},
+            "phase_ms": {k: round(v, 2) for k, v in last_stats["phase_ms"].items()},
+            "kernel_ms_per_step": {k: round(v[0] / args.steps, 2) for k, v in kernel.items()},
+            "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
+
+    # float64 factor arm (mixed vs float64 at the same backward error)
+    if args.fp64_arm:
+        torch.cuda.synchronize()
+        Z, it, berr, ok = step(h.H2_PREC_FP64)
+        del Z
+        torch.cuda.synchronize()
+        f0 = time.perf_counter()
+        Z, it, berr, ok = step(h.H2_PREC_FP64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - f0
+        st64 = h.h2_factor_stats_get(Z)
+        del Z
+        line["fp64_arm"] = {"value": t64, "unit": "s", "iters": it, "berr": berr, "converged": ok,
+                            "factor_ms": st64["factor_ms"], "speedup_mixed": t64 / t_step}
+
+    # end to end through the C-ABI with host buffers
+    if args.e2e_steps > 0:
+        from dataclasses import replace
+        host = {k: getattr(A, k).cpu().pin_memory() for k in ("U", "E", "S", "D")}
+        bh = b.cpu().t().contiguous().pin_memory().t()           # column-major, pinned
+        Ah = replace(A, **host)
+        del M
+        torch.cuda.synchronize()
+        e2e = []
+        for _ in range(args.e2e_steps):
+            xh = torch.zeros_like(bh)
+            torch.cuda.synchronize()
+            f0 = time.perf_counter()
+            Mh = h.h2_matrix_create(Ah, stream=stream)
+            Z = h.h2_factor_create(Mh, w.tol, pb.norm_a, h.H2_PREC_FP32, stream=stream)
+            it, berr, ok = h.h2_refine_solve(Z, Mh, bh, xh, BERR_TOL, MAXIT)
+            torch.cuda.synchronize()
+            e2e.append(time.perf_counter() - f0)
+            del Z, Mh
+        idx_bytes = sum(np.asarray(getattr(A, k)).nbytes for k in
+                        ("node_start", "node_size", "rank", "U_off", "E_off", "adm_ptr", "adm_col", "S_off",
+                         "inad_ptr", "inad_col", "D_off"))
+        h2d = A.nbytes() + idx_bytes + bh.numel() * 8
+        line["e2e"] = {"value": _max_over_ranks(dist, statistics.mean(e2e)) / ws, "unit": "s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(bh.numel() * 8)}
+
+    if args.cpu_baseline and rank == 0 and ws == 1:
+        line["cpu_baseline"] = _cpu_baseline(w.name, A.n, min(A.n, 16384))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    dist, rank, ws = _dist_init()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist, rank, ws)
+        else:
+            run_ours(args, dist, rank, ws)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -88,6 +88,18 @@ def _cheb_points(c: torch.Tensor, h: torch.Tensor, p: int) -> torch.Tensor:
 
 
 # ---------------------------------------------------------------- helpers
+def _qr(x: torch.Tensor, mode: str = "reduced"):
+    """Batched QR; small dense factorisations run on the host (batched CUDA QR of
+    many small matrices is far slower than LAPACK on the CPU)."""
+    q, r = torch.linalg.qr(x.cpu(), mode=mode)
+    return q.to(x.device), r.to(x.device)
+
+
+def _svd(x: torch.Tensor):
+    u, s, vh = torch.linalg.svd(x.cpu(), full_matrices=False)
+    return u.to(x.device), s.to(x.device), vh.to(x.device)
+
+
 def _level_ids(l: int) -> np.ndarray:
     return np.arange((1 << l) - 1, (1 << (l + 1)) - 1)
 
@@ -117,11 +129,32 @@ class _Pairs:
         self.maxdeg = int(self.deg.max()) if cnt else 0
 
 
+class _Clock:
+    """Wall-clock per construction phase (synchronising the device)."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.t = {}
+        self.t0 = self._now()
+
+    def _now(self):
+        if self.dev.type == "cuda":
+            torch.cuda.synchronize(self.dev)
+        import time
+        return time.perf_counter()
+
+    def lap(self, name):
+        now = self._now()
+        self.t[name] = self.t.get(name, 0.0) + now - self.t0
+        self.t0 = now
+
+
 def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, kern: Kernel,
                  p0: int, eps: float, device="cpu", chunk: int = 2048):
     """Build the H^2 matrix; returns a dict of per-level padded tensors (see
     ``h2matrix.H2Matrix.from_levels``)."""
     dev = torch.device(device)
+    clock = _Clock(dev)
     d = tree.depth
     dim = points.shape[1]
     pts = torch.as_tensor(points[tree.perm], dtype=torch.float64, device=dev)
@@ -138,7 +171,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
     L0 = _lagrange_nd(xl, centre[leaf_ids], half[leaf_ids], order[d])   # (nl, mmax, k0)
     _, valid = _pad_points(pts, tree, leaf_ids, mmax)
     L0 = L0 * valid.unsqueeze(-1)
-    Uq, Rr = torch.linalg.qr(L0, mode="reduced")
+    Uq, Rr = _qr(L0)
     U = {d: Uq}                   # orthonormal leaf basis (nl, mmax, r_d)
     R = {d: Rr}                   # (cnt, r_l, k0_l)
     E = {}                        # E[l]: (cnt_l, r_l, r_{l-1}) orthonormal transfers
@@ -151,7 +184,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
         E0 = _lagrange_nd(xi, centre[pidx], half[pidx], order[l - 1])   # (cnt, k0_l, k0_{l-1})
         RE = R[l] @ E0                                                  # (cnt, r_l, k0_{l-1})
         stacked = torch.cat([RE[0::2], RE[1::2]], dim=1)                # (cntp, 2 r_l, k0_{l-1})
-        Qp, Rp = torch.linalg.qr(stacked, mode="reduced")
+        Qp, Rp = _qr(stacked)
         r_l = RE.shape[1]
         E[l] = torch.stack([Qp[:, :r_l], Qp[:, r_l:]], dim=1).reshape(len(ids), r_l, Qp.shape[2])
         R[l - 1] = Rp
@@ -168,6 +201,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
         Rt = R[l][t - first]
         return Rs @ S0 @ Rt.transpose(1, 2)
 
+    clock.lap("orthogonalise")
     # ---- 3a: total far-field weights, root to leaves
     W = {0: torch.zeros((1, R[0].shape[1], R[0].shape[1]), dtype=torch.float64, device=dev)}
     for l in range(1, d + 1):
@@ -196,10 +230,11 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
             if Gt.shape[1] < r_l:
                 Gt = torch.cat([Gt, torch.zeros((Gt.shape[0], r_l - Gt.shape[1], r_l),
                                                 dtype=Gt.dtype, device=dev)], dim=1)
-            _, Rg = torch.linalg.qr(Gt, mode="reduced")                  # (B, r_l, r_l)
+            Rg = torch.linalg.qr(Gt.cpu(), mode="r")[1].to(dev)          # (B, r_l, r_l)
             Wl[c0:c1] = Rg.transpose(1, 2)
         W[l] = Wl
 
+    clock.lap("weights")
     # ---- 3b: truncation, leaves to root
     rank = {}
     P = {}                       # P[l]: (cnt, rows_l, kpad_l) new basis in child coords
@@ -214,7 +249,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
             Ehat = Bc.transpose(1, 2) @ E[l + 1]                          # (2cnt, kpc, r_l)
             Ehat = Ehat.reshape(cnt, 2 * Ehat.shape[1], Ehat.shape[2])
             M = Ehat @ W[l]
-        Ul, sv, _ = torch.linalg.svd(M, full_matrices=False)
+        Ul, sv, _ = _svd(M)
         keep = sv > eps * sv[:, :1]
         kk = keep.sum(dim=1)
         kpad = max(1, int(kk.max()))
@@ -230,6 +265,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
             B[l] = (Ec[:, 0].transpose(1, 2) @ Bc[:, 0] @ Pl[:, :kpc]
                     + Ec[:, 1].transpose(1, 2) @ Bc[:, 1] @ Pl[:, kpc:])
 
+    clock.lap("truncate")
     # ---- outputs: new leaf bases, transfers and couplings (padded per level)
     Unew = U[d] @ P[d]                                                   # (nl, mmax, kpad_d)
     Enew = {}
@@ -253,6 +289,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
             outs.append(Bs.transpose(1, 2) @ S @ Bt)
         Snew[l] = torch.cat(outs, dim=0)
 
+    clock.lap("couplings")
     # dense near field on inadmissible leaf pairs
     inad = part.inad[d]
     Dn = []
@@ -267,7 +304,8 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
         blk = blk * (vs.unsqueeze(2) & vt.unsqueeze(1))
         Dn.append(blk)
     Dnear = torch.cat(Dn, dim=0) if Dn else torch.zeros((0, mmax, mmax), dtype=torch.float64, device=dev)
-    return dict(rank=rank, U=Unew, E=Enew, S=Snew, D=Dnear, mmax=mmax)
+    clock.lap("near_field")
+    return dict(rank=rank, U=Unew, E=Enew, S=Snew, D=Dnear, mmax=mmax, seconds=clock.t)
 
 
 def matvec_levels(tree: ClusterTree, part: BlockPartition, lev: dict, x: torch.Tensor) -> torch.Tensor:

@@ -88,9 +88,14 @@ def make_problem(name: str, device="cpu", **over) -> Problem:
     pts, kern = family_points_kernel(w)
     tree = build_kdtree(pts, w.leaf)
     part = dual_traversal(tree, w.eta)
+    t_tree = time.perf_counter() - t0
     lev = construct_h2(pts, tree, part, kern, w.p0, w.tol / 10.0, device=device)
+    t1 = time.perf_counter()
     norm_a = spectral_norm(tree, part, lev)
+    t_norm = time.perf_counter() - t1
+    t2 = time.perf_counter()
     A = H2Matrix.from_levels(tree, part, lev)
+    seconds = dict(tree=t_tree, **lev["seconds"], norm=t_norm, flatten=time.perf_counter() - t2)
     del lev
     if torch.cuda.is_available() and str(device).startswith("cuda"):
         torch.cuda.synchronize()
@@ -101,7 +106,8 @@ def make_problem(name: str, device="cpu", **over) -> Problem:
         deg = A.inad_ptr[ids + 1] - A.inad_ptr[ids]
         csp = max(csp, int(deg.max()))
     stats = dict(depth=tree.depth, top_level=part.top_level(), csp=csp,
-                 kmax=int(A.rank.max()), nbytes=A.nbytes())
+                 kmax=int(A.rank.max()), nbytes=A.nbytes(),
+                 seconds={k: round(v, 2) for k, v in seconds.items()})
     A.meta = dict(workload=w.name, norm_a=norm_a)
     return Problem(w, A, norm_a, t1 - t0, stats)
 

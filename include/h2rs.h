@@ -127,9 +127,28 @@ typedef struct {
     double eps_lu;              /* truncation threshold of the fill (Alg. 1)           */
     double norm_a;              /* ||A||_2 supplied by the caller: eps_fill = eps_lu*norm_a */
     int32_t precision;          /* H2_PREC_*                                           */
-    int32_t reserved;
+    int32_t flags;              /* H2_FLAG_* bits, 0 by default                        */
     void* stream;               /* cudaStream_t for every kernel of this factor        */
 } h2_factor_opts;
+
+/* h2_factor_opts.flags: time every factorisation kernel launch with CUDA events
+ * (h2_factor_stats.kernel_ms / kernel_launches); adds about a microsecond per launch */
+#define H2_FLAG_TIME_KERNELS 1
+
+/* kernel ids of h2_factor_stats.kernel_* */
+enum {
+    H2_K_GATHER = 0,            /* fill-row gather Y = (I - V V^T) F                   */
+    H2_K_BASIS = 1,             /* R-factor of Y^T + Jacobi SVD + completion          */
+    H2_K_PROJ = 2,              /* Q~^T B and B Q~ projections                         */
+    H2_K_ZERO = 3,              /* truncation / eliminated rows and columns           */
+    H2_K_LU = 4,                /* LU of the redundant blocks                          */
+    H2_K_TRSM = 5,              /* W_U and W_L triangular solves                       */
+    H2_K_SCHUR = 6,             /* target-owned Schur update                           */
+    H2_K_CLOSE = 7,             /* level close (blocks and bases)                      */
+    H2_K_TOP = 8,               /* top-level assembly and float64 LU                   */
+    H2_K_LOAD = 9,              /* leaf near-field and basis load                      */
+    H2_K_COUNT = 10
+};
 
 /* Factorise A (Alg. 1): levels d..t, greedy colours in order, per colour the
  * batched basis augmentation (QR of the fill row + one-sided Jacobi SVD), orthogonal
@@ -169,6 +188,8 @@ typedef struct {
                                    top, leaf load, other                              */
     double phase_flops[8];      /* algorithmic flops of the same phases                */
     double phase_bytes[8];      /* algorithmic bytes of the same phases                */
+    double kernel_ms[16];       /* H2_FLAG_TIME_KERNELS: summed launch times per H2_K_* */
+    int64_t kernel_launches[16];
 } h2_factor_stats;
 
 H2_API int h2_factor_stats_get(const h2_factor* Z, h2_factor_stats* out);
@@ -192,6 +213,10 @@ H2_API int h2_layout_get(const h2_factor* Z, int32_t level, int64_t* sizes, int6
  * NULL (counts only).  Errors: H2_ERR_ARG. */
 H2_API int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
                   int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind);
+
+/* Number of CUDA kernels this library has launched in the process so far (all
+ * entry points; for counting launches inside a timed region). */
+H2_API int64_t h2_kernel_launch_count(void);
 
 H2_API const char* h2_last_error(void);
 H2_API const char* h2_version(void);

@@ -40,7 +40,7 @@ class h2_matrix_desc(ctypes.Structure):
 
 class h2_factor_opts(ctypes.Structure):
     _fields_ = [("eps_lu", ctypes.c_double), ("norm_a", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class h2_factor_stats(ctypes.Structure):
@@ -48,10 +48,13 @@ class h2_factor_stats(ctypes.Structure):
                 ("factor_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
                 ("error_level", ctypes.c_int32), ("error_box", ctypes.c_int32),
                 ("factor_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
-                ("phase_flops", ctypes.c_double * 8), ("phase_bytes", ctypes.c_double * 8)]
+                ("phase_flops", ctypes.c_double * 8), ("phase_bytes", ctypes.c_double * 8),
+                ("kernel_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_int64 * 16)]
 
 
 PHASES = ["augment", "project", "lu_trsm", "schur", "close", "top", "leaf_load", "other"]
+KERNELS = ["gather", "basis", "proj", "zero", "lu", "trsm", "schur", "close", "top", "load"]
+H2_FLAG_TIME_KERNELS = 1
 
 # (name, restype, argtypes) of every exported entry point
 _SIGS = [
@@ -73,6 +76,7 @@ _SIGS = [
                                      _i32p, _i64p]),
     ("h2_plan_query", ctypes.c_int, [ctypes.POINTER(h2_matrix_desc), ctypes.c_int32, _i64p, _i64p, _i32p,
                                      _i64p, _i64p, _i32p]),
+    ("h2_kernel_launch_count", ctypes.c_int64, []),
     ("h2_last_error", ctypes.c_char_p, []),
     ("h2_version", ctypes.c_char_p, []),
 ]
@@ -200,11 +204,12 @@ def h2_matrix_create(A, stream=None) -> Matrix:
 
 
 def h2_factor_create(M: Matrix, eps_lu: float, norm_a: float, precision: int = H2_PREC_FP64,
-                     stream=None) -> Factor:
+                     stream=None, flags: int = 0) -> Factor:
     o = h2_factor_opts()
     o.eps_lu = float(eps_lu)
     o.norm_a = float(norm_a)
     o.precision = int(precision)
+    o.flags = int(flags)
     o.stream = ctypes.c_void_p(stream) if stream else None
     h = ctypes.c_void_p()
     _check(lib().h2_factor_create(M.handle, ctypes.byref(o), ctypes.byref(h)))
@@ -250,7 +255,9 @@ def h2_factor_stats_get(Z: Factor) -> dict:
                 peak_bytes=s.peak_bytes, error_level=s.error_level, error_box=s.error_box,
                 factor_ms=s.factor_ms, phase_ms=dict(zip(PHASES, list(s.phase_ms))),
                 phase_flops=dict(zip(PHASES, list(s.phase_flops))),
-                phase_bytes=dict(zip(PHASES, list(s.phase_bytes))))
+                phase_bytes=dict(zip(PHASES, list(s.phase_bytes))),
+                kernel_ms=dict(zip(KERNELS, list(s.kernel_ms))),
+                kernel_launches=dict(zip(KERNELS, list(s.kernel_launches))))
 
 
 def h2_layout_get(Z: Factor, level: int) -> dict:

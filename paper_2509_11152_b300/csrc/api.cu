@@ -1,4 +1,5 @@
 // C-ABI of the library: object lifetimes, argument checks, error codes.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -10,6 +11,9 @@ namespace h2rs {
 
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void DevBuf::alloc(size_t nbytes, cudaStream_t s) {
     release();
@@ -148,6 +152,7 @@ using namespace h2rs;
 extern "C" {
 
 const char* h2_last_error(void) { return g_err.c_str(); }
+int64_t h2_kernel_launch_count(void) { return g_launches.load(); }
 const char* h2_version(void) { return "h2rs 0.1 (sm_103a)"; }
 
 int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out) {

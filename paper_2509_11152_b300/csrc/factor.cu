@@ -97,6 +97,7 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
     norm_a = o.norm_a;
     norm_a_ = o.norm_a;
     precision = o.precision;
+    time_kernels = (o.flags & H2_FLAG_TIME_KERNELS) != 0;
     stream = static_cast<cudaStream_t>(o.stream);
     status.alloc(sizeof(DevStatus), stream);
 }
@@ -104,6 +105,28 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
 template <class T>
 FactorImpl<T>::~FactorImpl() {
     for (auto e : ev) cudaEventDestroy(e);
+    for (auto e : kev) cudaEventDestroy(e);
+}
+
+template <class T>
+void FactorImpl<T>::kbegin(int id) {
+    count_launch();
+    if (!time_kernels) return;
+    cudaEvent_t e;
+    H2_CUDA_CHECK(cudaEventCreate(&e));
+    H2_CUDA_CHECK(cudaEventRecord(e, stream));
+    kev.push_back(e);
+    kev_id.push_back(id);
+}
+
+template <class T>
+void FactorImpl<T>::kend() {
+    if (!time_kernels) return;
+    cudaEvent_t e;
+    H2_CUDA_CHECK(cudaEventCreate(&e));
+    H2_CUDA_CHECK(cudaEventRecord(e, stream));
+    kev.push_back(e);
+    kev_id.push_back(-1);
 }
 
 template <class T>
@@ -263,13 +286,17 @@ void FactorImpl<T>::run_level(size_t a) {
     if (a == 0) {
         DevBuf d_near;
         upload(d_near, S.near_entry, s);
+        kbegin(H2_K_LOAD);
         k_leaf_load<T><<<S.nblocks(), 256, 0, s>>>(ar, M.D.as<double>(), M.d_D_off.as<int64_t>(),
                                                  d_near.as<int64_t>());
+        kend();
         H2_LAUNCHED();
         std::vector<int64_t> uoff(M.H.U_off.begin(), M.H.U_off.end());
         DevBuf d_uoff;
         upload(d_uoff, uoff, s);
+        kbegin(H2_K_LOAD);
         k_leaf_basis<T><<<S.cnt, 256, 0, s>>>(ar, L.V.as<T>(), M.U.as<double>(), d_uoff.as<int64_t>());
+        kend();
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_LOAD);
@@ -434,12 +461,16 @@ void FactorImpl<T>::run_level(size_t a) {
             CG.seg_blk = d_seg_blk.as<int>() + s0;
             CG.seg_j = d_seg_j.as<int>() + s0;
             CG.seg_yoff = d_seg_yoff.as<int64_t>() + s0;
+            kbegin(H2_K_GATHER);
             k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, d_seg_slot.as<int>() + s0,
                                                               scratch.as<T>());
+            kend();
             H2_LAUNCHED();
         }
+        kbegin(H2_K_BASIS);
         k_basis<T><<<nbx, 256, W.smem_basis[c], s>>>(ar, CL, c, scratch.as<T>(), scratch.as<T>(),
                                                      eps_fill, W.w_in_smem[c]);
+        kend();
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_AUG);
@@ -447,29 +478,47 @@ void FactorImpl<T>::run_level(size_t a) {
         const int pl0 = W.pl_cptr[c], npl = W.pl_cptr[c + 1] - pl0;
         const int pr0 = W.pr_cptr[c], npr = W.pr_cptr[c + 1] - pr0;
         const int smp = W.nmax[c] * PW * (int)sizeof(T);
-        if (npl) k_proj_left<T><<<npl, 256, smp, s>>>(ar, d_pl_box.as<int>() + pl0, d_pl_blk.as<int>() + pl0,
-                                                      d_pl_pan.as<int>() + pl0);
+        if (npl) {
+            kbegin(H2_K_PROJ);
+            k_proj_left<T><<<npl, 256, smp, s>>>(ar, d_pl_box.as<int>() + pl0, d_pl_blk.as<int>() + pl0,
+                                                          d_pl_pan.as<int>() + pl0);
+            kend();
+        }
         H2_LAUNCHED();
-        if (npr) k_proj_right<T><<<npr, 256, smp, s>>>(ar, d_pr_box.as<int>() + pr0, d_pr_blk.as<int>() + pr0,
-                                                       d_pr_pan.as<int>() + pr0);
+        if (npr) {
+            kbegin(H2_K_PROJ);
+            k_proj_right<T><<<npr, 256, smp, s>>>(ar, d_pr_box.as<int>() + pr0, d_pr_blk.as<int>() + pr0,
+                                                           d_pr_pan.as<int>() + pr0);
+            kend();
+        }
         H2_LAUNCHED();
         const int zf0 = W.zf_cptr[c], nzf = W.zf_cptr[c + 1] - zf0;
-        if (nzf) k_zero_redundant<T><<<nzf, 256, 0, s>>>(ar, d_zf_box.as<int>() + zf0, d_zf_blk.as<int>() + zf0,
-                                                        d_zf_col.as<int>() + zf0);
+        if (nzf) {
+            kbegin(H2_K_ZERO);
+            k_zero_redundant<T><<<nzf, 256, 0, s>>>(ar, d_zf_box.as<int>() + zf0, d_zf_blk.as<int>() + zf0,
+                                                            d_zf_col.as<int>() + zf0);
+            kend();
+        }
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_PROJ);
         // ---- partial LU + triangular solves
         const size_t lu_sm = (size_t)W.nmax[c] * W.nmax[c] * sizeof(T);
         const int lu_in = lu_sm <= (size_t)smem_limits<T>().lu;
+        kbegin(H2_K_LU);
         k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, d_boxes.as<int>() + b0, lu_in);
+        kend();
         H2_LAUNCHED();
         const int tu0 = W.tu_cptr[c], ntu = W.tu_cptr[c + 1] - tu0;
         const int tsm = 8 * W.nmax[c] * (int)sizeof(T);
         if (ntu) {
+            kbegin(H2_K_TRSM);
             k_trsm_u<T><<<ntu, 256, tsm, s>>>(ar, d_tu_box.as<int>() + tu0, d_tu_c0.as<int>() + tu0);
+            kend();
             H2_LAUNCHED();
+            kbegin(H2_K_TRSM);
             k_trsm_l<T><<<ntu, 256, tsm, s>>>(ar, d_tu_box.as<int>() + tu0, d_tu_c0.as<int>() + tu0);
+            kend();
             H2_LAUNCHED();
         }
         H2_CUDA_CHECK(cudaGetLastError());
@@ -477,13 +526,19 @@ void FactorImpl<T>::run_level(size_t a) {
         // ---- Schur update and zeroing of the eliminated rows / columns
         const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
         if (ntile)
+            kbegin(H2_K_SCHUR);
             k_schur<T><<<ntile, 256, 0, s>>>(ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(),
                                              d_c_box.as<int>(), d_c_ablk.as<int>(), d_c_kpos.as<int>(),
                                              d_tile_tgt.as<int>() + t0, d_tile_mn.as<int>() + t0);
+            kend();
             H2_LAUNCHED();
         const int zn0 = W.zn_cptr[c], nzn = W.zn_cptr[c + 1] - zn0;
-        if (nzn) k_zero_redundant<T><<<nzn, 256, 0, s>>>(ar, d_zn_box.as<int>() + zn0, d_zn_blk.as<int>() + zn0,
-                                                        d_zn_col.as<int>() + zn0);
+        if (nzn) {
+            kbegin(H2_K_ZERO);
+            k_zero_redundant<T><<<nzn, 256, 0, s>>>(ar, d_zn_box.as<int>() + zn0, d_zn_blk.as<int>() + zn0,
+                                                            d_zn_col.as<int>() + zn0);
+            kend();
+        }
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_SCHUR);
@@ -552,15 +607,19 @@ void FactorImpl<T>::close_level(size_t a) {
     upload(d_ca, S.cl_adm, s);
     const int nbp = Pn.S->nblocks();
     if (nbp)
+        kbegin(H2_K_CLOSE);
         k_close_blocks<T><<<nbp, 256, 0, s>>>(ar, Pn.blk.as<T>(), Pn.d_blk_off.as<int64_t>(),
                                               Pn.d_brow.as<int>(), Pn.d_bcol.as<int>(), d_cd.as<int>(),
                                               d_cf.as<int>(), d_ca.as<int64_t>(), M.S.as<double>(),
                                               M.d_S_off.as<int64_t>());
+        kend();
         H2_LAUNCHED();
     if (a + 1 < lv.size() - 1)
+        kbegin(H2_K_CLOSE);
         k_close_basis<T><<<Pn.cnt, 256, 0, s>>>(ar, Pn.V.as<T>(), Pn.d_V_off.as<int64_t>(),
                                                 Pn.d_k.as<int>(), M.E.as<double>(),
                                                 M.d_E_off.as<int64_t>(), L.S->first);
+        kend();
         H2_LAUNCHED();
     H2_CUDA_CHECK(cudaGetLastError());
     mark(PH_CLOSE);
@@ -591,32 +650,44 @@ void FactorImpl<T>::top_factor() {
             for (int b = 0; b < S.nblocks(); ++b) off[b] = M.H.D_off[S.near_entry[b]];
             DevBuf d_off;
             upload(d_off, off, s);
+            kbegin(H2_K_TOP);
             k_top_assemble<double><<<S.nblocks(), 256, 0, s>>>(M.D.as<double>(), d_off.as<int64_t>(),
                                                                Tl.d_brow.as<int>(), Tl.d_bcol.as<int>(),
                                                                Tl.d_n.as<int>(), d_toff.as<int64_t>(),
                                                                Dt.as<double>(), nt);
+            kend();
             H2_LAUNCHED();
         } else {
+            kbegin(H2_K_TOP);
             k_top_assemble<T><<<S.nblocks(), 256, 0, s>>>(Tl.blk.as<T>(), Tl.d_blk_off.as<int64_t>(),
                                                           Tl.d_brow.as<int>(), Tl.d_bcol.as<int>(),
                                                           Tl.d_n.as<int>(), d_toff.as<int64_t>(),
                                                           Dt.as<double>(), nt);
+            kend();
             H2_LAUNCHED();
         }
         H2_CUDA_CHECK(cudaGetLastError());
         const int NB = 64;
         for (int64_t j0 = 0; j0 < nt; j0 += NB) {
             const int jb = (int)std::min<int64_t>(NB, nt - j0);
+            kbegin(H2_K_TOP);
             k_top_panel<<<1, 1024, 0, s>>>(Dt.as<double>(), nt, j0, jb, tpiv.as<int>(), status.as<DevStatus>());
+            kend();
             H2_LAUNCHED();
+            kbegin(H2_K_TOP);
             k_top_swap<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(Dt.as<double>(), nt, j0, jb, tpiv.as<int>());
+            kend();
             H2_LAUNCHED();
             const int64_t rest = nt - j0 - jb;
             if (rest > 0) {
+                kbegin(H2_K_TOP);
                 k_top_trsm<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(Dt.as<double>(), nt, j0, jb);
+                kend();
                 H2_LAUNCHED();
                 dim3 g((unsigned)((rest + 63) / 64), (unsigned)((rest + 63) / 64));
+                kbegin(H2_K_TOP);
                 k_top_gemm<<<g, 256, 0, s>>>(Dt.as<double>(), nt, j0, jb);
+                kend();
                 H2_LAUNCHED();
             }
         }
@@ -659,6 +730,17 @@ void FactorImpl<T>::factorize() {
         total += ms;
     }
     stats.factor_ms = total;
+    for (int q = 0; q < 16; ++q) { stats.kernel_ms[q] = 0; stats.kernel_launches[q] = 0; }
+    for (size_t e = 0; e + 1 < kev.size(); ++e)
+        if (kev_id[e] >= 0 && kev_id[e + 1] < 0) {
+            float ms = 0;
+            H2_CUDA_CHECK(cudaEventElapsedTime(&ms, kev[e], kev[e + 1]));
+            stats.kernel_ms[kev_id[e]] += ms;
+            stats.kernel_launches[kev_id[e]] += 1;
+        }
+    for (auto e : kev) cudaEventDestroy(e);
+    kev.clear();
+    kev_id.clear();
     stats.nlevels = (int)P.levels.size();
     stats.top_level = P.top;
     stats.top_size = nt;

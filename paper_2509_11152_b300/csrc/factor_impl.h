@@ -57,6 +57,12 @@ struct FactorImpl : FactorBase {
     // events for phase timing
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_phase;
+    // optional per-launch events (H2_FLAG_TIME_KERNELS)
+    bool time_kernels = false;
+    std::vector<cudaEvent_t> kev;
+    std::vector<int> kev_id;
+    void kbegin(int id);
+    void kend();
 
     FactorImpl(const MatrixObj* A_, const h2_factor_opts& o);
     ~FactorImpl() override;

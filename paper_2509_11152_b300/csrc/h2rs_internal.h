@@ -20,6 +20,9 @@ struct Error {
 
 void set_error(const std::string& msg);
 
+// process-wide count of kernel launches (h2_kernel_launch_count)
+void count_launch(int64_t n = 1);
+
 #define H2_CUDA_CHECK(call)                                                          \
     do {                                                                             \
         cudaError_t e_ = (call);                                                     \

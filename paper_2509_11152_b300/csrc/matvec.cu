@@ -157,15 +157,18 @@ void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, do
                   int64_t n, int nrhs, cudaStream_t s) {
     const unsigned g = (unsigned)((n * nrhs + 255) / 256);
     v_residual<<<g, 256, 0, s>>>(b, ldb, y, ldy, r, ldr, n, nrhs);
+    count_launch();
 }
 
 void add_dev(double* x, int64_t ldx, const double* d, int64_t ldd, int64_t n, int nrhs, cudaStream_t s) {
     const unsigned g = (unsigned)((n * nrhs + 255) / 256);
     v_add<<<g, 256, 0, s>>>(x, ldx, d, ldd, n, nrhs);
+    count_launch();
 }
 
 void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s) {
     v_colnorm2<<<nrhs, 256, 0, s>>>(v, ldv, n, out);
+    count_launch();
 }
 
 // ------------------------------------------------------------------ driver
@@ -184,24 +187,29 @@ void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, doub
     mv_leaf_up<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
                                      M.d_node_size.as<int64_t>(), rank, coef, first_leaf, x, ldx,
                                      xh.as<double>(), nrhs);
+    count_launch();
     for (int l = d; l >= 1; --l) {
         const int64_t pf = (int64_t(1) << (l - 1)) - 1;
         mv_up<<<1 << (l - 1), 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, pf,
                                            xh.as<double>(), nrhs);
+        count_launch();
     }
     mv_couple<<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
                                                   M.d_adm_ptr.as<int64_t>(), M.d_adm_col.as<int64_t>(), rank,
                                                   coef, xh.as<double>(), yh.as<double>(), nrhs);
+    count_launch();
     for (int l = 1; l <= d; ++l) {
         const int64_t f = (int64_t(1) << l) - 1;
         mv_down<<<1 << l, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, f,
                                        yh.as<double>(), nrhs);
+        count_launch();
     }
     mv_leaf_down<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),
                                        M.d_D_off.as<int64_t>(), M.d_inad_ptr.as<int64_t>(),
                                        M.d_inad_col.as<int64_t>(), M.d_node_start.as<int64_t>(),
                                        M.d_node_size.as<int64_t>(), rank, coef, first_leaf,
                                        yh.as<double>(), x, ldx, y, ldy, nrhs);
+    count_launch();
     H2_CUDA_CHECK(cudaGetLastError());
 }
 

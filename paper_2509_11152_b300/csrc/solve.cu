@@ -242,6 +242,7 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
     }
     s_load<T><<<L0.cnt, 256, 0, s>>>(b, ldb, nrhs, d_start.as<int64_t>(), L0.d_n.as<int>(),
                                      L0.d_voff.as<int64_t>(), vec[0].as<T>());
+    count_launch();
     DevBuf d_boxes;
     std::vector<std::vector<int>> cptr(nl);
     {
@@ -267,24 +268,29 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
             s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
                                               L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                               vec[a].as<T>(), nrhs, 1);
+            count_launch();
             const int t0 = S.fl_cptr[c], nt_ = S.fl_cptr[c + 1] - t0;
-            if (nt_)
+            if (nt_) {
                 s_fwd_l<T><<<nt_, 256, 0, s>>>(L.d_fl_tbox.as<int>() + t0, L.d_fl_tptr.as<int>() + t0,
                                                L.d_fl_ci.as<int>(), L.d_fl_cpos.as<int>(), c,
                                                L.d_colour.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(),
                                                L.d_nb_ptr.as<int>(), L.d_nbofs.as<int>(), L.WL.as<T>(),
                                                L.d_WL_off.as<int64_t>(), L.d_WLld.as<int>(),
                                                L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
+                count_launch();
+            }
         }
         const int nw = L.cnt * nrhs;
         s_diag<T><<<(nw + 7) / 8, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.LU.as<T>(),
                                                L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
                                                L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                                vec[a].as<T>(), nrhs, L.cnt, 0);
+        count_launch();
         LevelRT& Pn = lv[a + 1];
         s_sweep<T><<<Pn.cnt, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.d_voff.as<int64_t>(),
                                           vec[a].as<T>(), Pn.d_voff.as<int64_t>(), vec[a + 1].as<T>(),
                                           nrhs, 1);
+        count_launch();
     }
     // top
     LevelRT& Tl = lv[nl];
@@ -293,9 +299,12 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         xt.alloc(nt * nrhs * sizeof(double), s);
         s_top_io<T><<<Tl.cnt, 256, 0, s>>>(Tl.d_n.as<int>(), Tl.d_voff.as<int64_t>(), d_toff.as<int64_t>(),
                                            vec[nl].as<T>(), xt.as<double>(), nt, nrhs, 1);
+        count_launch();
         s_top_solve<<<nrhs, 1024, 0, s>>>(Dt.as<double>(), tpiv.as<int>(), nt, xt.as<double>());
+        count_launch();
         s_top_io<T><<<Tl.cnt, 256, 0, s>>>(Tl.d_n.as<int>(), Tl.d_voff.as<int64_t>(), d_toff.as<int64_t>(),
                                            vec[nl].as<T>(), xt.as<double>(), nt, nrhs, 0);
+        count_launch();
     }
     // backward
     for (size_t a = nl; a-- > 0;) {
@@ -305,11 +314,13 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         s_sweep<T><<<Pn.cnt, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.d_voff.as<int64_t>(),
                                           vec[a].as<T>(), Pn.d_voff.as<int64_t>(), vec[a + 1].as<T>(),
                                           nrhs, 0);
+        count_launch();
         const int nw = L.cnt * nrhs;
         s_diag<T><<<(nw + 7) / 8, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.LU.as<T>(),
                                                L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
                                                L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                                vec[a].as<T>(), nrhs, L.cnt, 1);
+        count_launch();
         int nmax = 1;
         for (int v : L.n) nmax = std::max(nmax, v);
         const int qsm = nmax * nrhs * (int)sizeof(T);
@@ -319,13 +330,16 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
                                           L.d_nb_ptr.as<int>(), L.d_nb_col.as<int>(), L.d_nbofs.as<int>(),
                                           L.WU.as<T>(), L.d_WU_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                           vec[a].as<T>(), nrhs);
+            count_launch();
             s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
                                               L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                               vec[a].as<T>(), nrhs, 0);
+            count_launch();
         }
     }
     s_store<T><<<L0.cnt, 256, 0, s>>>(b, ldb, nrhs, d_start.as<int64_t>(), L0.d_n.as<int>(),
                                       L0.d_voff.as<int64_t>(), vec[0].as<T>());
+    count_launch();
     H2_CUDA_CHECK(cudaGetLastError());
 }
 
