@@ -65,6 +65,16 @@ static int raise_smem(K kern) {
     return lim;
 }
 
+template <class T, bool RIGHT>
+static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<T> ar, const int* box,
+                        const int* blk, const int* pan) {
+    if (rpt <= 1) k_proj<T, 1, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
+    else if (rpt <= 2) k_proj<T, 2, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
+    else if (rpt <= 4) k_proj<T, 4, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
+    else if (rpt <= 8) k_proj<T, 8, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
+    else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
+}
+
 template <class T>
 struct SmemLimits {
     int basis, lu, proj_l, proj_r, gather, trsm_u, trsm_l;
@@ -76,8 +86,10 @@ static const SmemLimits<T>& smem_limits() {
         SmemLimits<T> x{};
         x.basis = raise_smem(k_basis<T>);
         x.lu = raise_smem(k_lu<T>);
-        x.proj_l = raise_smem(k_proj_left<T>);
-        x.proj_r = raise_smem(k_proj_right<T>);
+        x.proj_l = std::min({raise_smem(k_proj<T, 1, false>), raise_smem(k_proj<T, 2, false>),
+                             raise_smem(k_proj<T, 4, false>), raise_smem(k_proj<T, 8, false>)});
+        x.proj_r = std::min({raise_smem(k_proj<T, 1, true>), raise_smem(k_proj<T, 2, true>),
+                             raise_smem(k_proj<T, 4, true>), raise_smem(k_proj<T, 8, true>)});
         x.gather = raise_smem(k_aug_gather<T>);
         x.trsm_u = raise_smem(k_trsm_u<T>);
         x.trsm_l = raise_smem(k_trsm_l<T>);
@@ -341,10 +353,9 @@ void FactorImpl<T>::run_level(size_t a) {
             W.ylead.push_back(yrows);
             ysum += yrows * n;
             W.wbase.push_back(wsum);
-            wsum += (int64_t)n * n;
+            wsum += (int64_t)n * (n + 1);
             gsm = std::max(gsm, (int)((n + L.k[i]) * 16 * sizeof(T)));
-            const int CH = n <= 192 ? 64 : 32;
-            csz = std::max(csz, CH * n);
+            csz = std::max(csz, basis_chunk_elems(n));
             // projection pairs (near blocks + fill blocks already holding fill)
             for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
                 const bool live = S.bkind[b] == 0 || S.first_touch[b] < c;
@@ -388,10 +399,11 @@ void FactorImpl<T>::run_level(size_t a) {
         }
         W.tile_cptr.push_back((int)W.tile_tgt.size());
         const size_t base = (size_t)(csz + 2 * nmax + 33) * sizeof(T) + 16;
-        const size_t wsm = (size_t)nmax * nmax * sizeof(T);
+        const size_t wsm = (size_t)nmax * (nmax + 1) * sizeof(T);
         const auto& lim = smem_limits<T>();
         H2_REQUIRE(base <= (size_t)lim.basis && (size_t)gsm <= (size_t)lim.gather &&
-                       (size_t)nmax * 32 * sizeof(T) <= (size_t)std::min(lim.proj_l, lim.proj_r),
+                       (size_t)2 * 32 * ((nmax + 31) / 32 * 32 + 1) * sizeof(T) <= (size_t)std::min(lim.proj_l, lim.proj_r) &&
+                       nmax <= 256,
                    H2_ERR_ARG, "box size too large for the shared-memory kernels");
         const int in_sm = base + wsm <= (size_t)lim.basis;
         W.w_in_smem.push_back(in_sm);
@@ -477,18 +489,19 @@ void FactorImpl<T>::run_level(size_t a) {
         // ---- projection + fill truncation
         const int pl0 = W.pl_cptr[c], npl = W.pl_cptr[c + 1] - pl0;
         const int pr0 = W.pr_cptr[c], npr = W.pr_cptr[c + 1] - pr0;
-        const int smp = W.nmax[c] * PW * (int)sizeof(T);
+        const int smp = 2 * PW * ((W.nmax[c] + 31) / 32 * 32 + 1) * (int)sizeof(T);
+        const int rpt = (W.nmax[c] + 31) / 32;
         if (npl) {
             kbegin(H2_K_PROJ);
-            k_proj_left<T><<<npl, 256, smp, s>>>(ar, d_pl_box.as<int>() + pl0, d_pl_blk.as<int>() + pl0,
-                                                          d_pl_pan.as<int>() + pl0);
+            launch_proj<T, false>(rpt, npl, smp, s, ar, d_pl_box.as<int>() + pl0, d_pl_blk.as<int>() + pl0,
+                                  d_pl_pan.as<int>() + pl0);
             kend();
         }
         H2_LAUNCHED();
         if (npr) {
             kbegin(H2_K_PROJ);
-            k_proj_right<T><<<npr, 256, smp, s>>>(ar, d_pr_box.as<int>() + pr0, d_pr_blk.as<int>() + pr0,
-                                                           d_pr_pan.as<int>() + pr0);
+            launch_proj<T, true>(rpt, npr, smp, s, ar, d_pr_box.as<int>() + pr0, d_pr_blk.as<int>() + pr0,
+                                 d_pr_pan.as<int>() + pr0);
             kend();
         }
         H2_LAUNCHED();

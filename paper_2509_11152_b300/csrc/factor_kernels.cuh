@@ -125,6 +125,89 @@ __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* 
     }
 }
 
+// R-factor of the live rows of Y^T (streamed in chunks of 64 rows) accumulated in W
+// (row-major n x n, row stride ldw).  Each thread keeps RPT = 64 / tpc rows of one
+// column of the chunk in registers (tpc threads per column); per Householder step only
+// the reflector column and its partial norms go through shared memory (double
+// buffered, one barrier per step).  Requires n * tpc <= 256.
+// elements of the chunk buffer of k_basis (also holds rfactor_stream's broadcasts)
+__host__ __device__ inline int basis_chunk_elems(int n) {
+    const int ch = n <= 192 ? 64 : 32;
+    const int e = (ch + 1) * n;
+    return e > 160 ? e : 160;
+}
+
+template <class T, int RPT>
+__device__ void rfactor_stream(const LevelArgs<T>& a, const ColourLists& L, int slot, int cur, int n,
+                               const T* __restrict__ Yt, int64_t ld, T* W, int ldw, T* vb) {
+    constexpr int CH = 64;
+    constexpr int TPC = CH / RPT;
+    const int tid = threadIdx.x;
+    const int part = tid % TPC, col = tid / TPC;
+    const bool own = col < n;
+    // vb layout: 2 buffers of [CH reflector values | TPC partial norms | x0]
+    const int bufsz = CH + TPC + 1;
+    const int s0 = L.seg_ptr[slot], s1 = L.seg_ptr[slot + 1];
+    T x[RPT];
+    for (int s = s0; s < s1; ++s) {
+        const int j = L.seg_j[s];
+        const int nj = a.n[j];
+        const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
+        const int64_t yoff = L.seg_yoff[s];
+        for (int r0 = skip; r0 < nj; r0 += CH) {
+            const int rows = min(CH, nj - r0);
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int rr = part * RPT + q;
+                x[q] = (own && rr < rows) ? Yt[(yoff + r0 + rr) + (int64_t)col * ld] : T(0);
+            }
+            for (int jj = 0; jj < n; ++jj) {
+                T* buf = vb + (jj & 1) * bufsz;
+                if (col == jj) {
+                    T p2 = 0;
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) {
+                        buf[part * RPT + q] = x[q];
+                        p2 += x[q] * x[q];
+                    }
+                    buf[CH + part] = p2;
+                    if (part == 0) buf[CH + TPC] = W[(int64_t)jj * ldw + jj];
+                }
+                __syncthreads();
+                T ss = 0;
+#pragma unroll
+                for (int p = 0; p < TPC; ++p) ss += buf[CH + p];
+                if (ss == T(0)) continue;                         // uniform; buffers alternate
+                const T x0 = buf[CH + TPC];
+                const T nrm = sqrt(x0 * x0 + ss);
+                const T beta = x0 > T(0) ? -nrm : nrm;
+                const T v0 = x0 - beta;
+                const T tw = -v0 / beta;
+                const T inv = T(1) / v0;
+                const bool act = own && col > jj;
+                T d = 0;
+                if (act) {
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) d += buf[part * RPT + q] * x[q];
+                }
+#pragma unroll
+                for (int o = 1; o < TPC; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (act) {
+                    const T w = W[(int64_t)jj * ldw + col] + d * inv;
+                    const T tww = tw * w;
+                    const T f = tww * inv;
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) x[q] -= f * buf[part * RPT + q];
+                    if (part == 0) W[(int64_t)jj * ldw + col] -= tww;
+                } else if (col == jj && part == 0) {
+                    W[(int64_t)jj * ldw + jj] = beta;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Basis augmentation + completion of one box (Alg. 2, truncSVD option 2):
 //   R  = R-factor of Y^T (Householder, streamed over row chunks, R kept row-major)
 //   one-sided Jacobi on M = R^T: its converged columns are sigma_p w_p with w_p the
@@ -142,9 +225,11 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nwarp = blockDim.x >> 5;
     const int CH = (n <= 192) ? 64 : 32;
+    const int ldc = CH + 1;                         // padded: no bank conflicts across columns
+    const int ldw = n + 1;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* C = reinterpret_cast<T*>(sm_raw);            // CH x n chunk (col-major, ld CH)
-    T* tau = C + (size_t)CH * n;                    // n
+    T* C = reinterpret_cast<T*>(sm_raw);            // CH x n chunk (col-major, ld ldc)
+    T* tau = C + basis_chunk_elems(n);              // n
     T* sig = tau + n;                               // n
     T* red = sig + n;                               // 33
     int* ired = reinterpret_cast<int*>(red + 33);   // 4
@@ -164,92 +249,127 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
     }
     int keep = 0;
     if (live > 0 && k < n) {
-        // ---------------- R-factor of Y^T
-        for (int x = tid; x < n * n; x += blockDim.x) W[x] = T(0);
+        // ---------------- R-factor of Y^T (R row-major in W, row stride ldw)
+        for (int x = tid; x < n * ldw; x += blockDim.x) W[x] = T(0);
         __syncthreads();
-        for (int s = s0; s < s1; ++s) {
-            const int j = L.seg_j[s];
-            const int nj = a.n[j];
-            const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
-            const int64_t yoff = L.seg_yoff[s];
-            for (int r0 = skip; r0 < nj; r0 += CH) {
-                const int rows = min(CH, nj - r0);
-                for (int x = tid; x < CH * n; x += blockDim.x) {
-                    const int rr = x % CH, col = x / CH;
-                    C[x] = rr < rows ? Yt[(yoff + r0 + rr) + (int64_t)col * ld] : T(0);
-                }
-                __syncthreads();
-                for (int jj = 0; jj < n; ++jj) {
-                    const T c0v = C[lane + jj * CH];
-                    const T c1v = (CH == 64) ? C[lane + 32 + jj * CH] : T(0);
-                    const T ss = warp_sum(c0v * c0v + c1v * c1v);
-                    if (ss == T(0)) continue;                       // uniform
-                    const T x0 = W[(int64_t)jj * n + jj];
-                    const T nrm = sqrt(x0 * x0 + ss);
-                    const T beta = x0 > T(0) ? -nrm : nrm;
-                    const T v0 = x0 - beta;
-                    const T tw = -v0 / beta;
-                    const T vr0 = c0v / v0, vr1 = c1v / v0;
-                    for (int col = jj + 1 + wid; col < n; col += nwarp) {
-                        const T e0 = C[lane + col * CH];
-                        const T e1 = (CH == 64) ? C[lane + 32 + col * CH] : T(0);
-                        const T w = W[(int64_t)jj * n + col] + warp_sum(vr0 * e0 + vr1 * e1);
-                        const T tww = tw * w;
-                        C[lane + col * CH] = e0 - tww * vr0;
-                        if (CH == 64) C[lane + 32 + col * CH] = e1 - tww * vr1;
-                        if (lane == 0) W[(int64_t)jj * n + col] -= tww;
+        if (n <= 32) rfactor_stream<T, 8>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
+        else if (n <= 64) rfactor_stream<T, 16>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
+        else if (n <= 128) rfactor_stream<T, 32>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
+        else if (n <= 256) rfactor_stream<T, 64>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
+        else {
+            // Every step's trailing update gives tpc threads to a column (a power of two,
+            // rows interleaved), so a column's dot product needs log2(tpc) shuffles only.
+            int tpc = 1;
+            while (tpc * 2 <= 16 && tpc * 2 * n <= 256) tpc *= 2;
+            const int cstep = 256 / tpc, part = tid % tpc, cofs = tid / tpc;
+            for (int s = s0; s < s1; ++s) {
+                const int j = L.seg_j[s];
+                const int nj = a.n[j];
+                const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
+                const int64_t yoff = L.seg_yoff[s];
+                for (int r0 = skip; r0 < nj; r0 += CH) {
+                    const int rows = min(CH, nj - r0);
+                    for (int x = tid; x < CH * n; x += blockDim.x) {
+                        const int rr = x % CH, col = x / CH;
+                        C[rr + col * ldc] = rr < rows ? Yt[(yoff + r0 + rr) + (int64_t)col * ld] : T(0);
                     }
                     __syncthreads();
-                    if (tid == 0) W[(int64_t)jj * n + jj] = beta;
+                    for (int jj = 0; jj < n; ++jj) {
+                        const T* cj = C + jj * ldc;
+                        T ss = 0;
+                        for (int r = 0; r < rows; ++r) ss += cj[r] * cj[r];
+                        if (ss == T(0)) continue;                       // uniform
+                        const T x0 = W[(int64_t)jj * ldw + jj];
+                        const T nrm = sqrt(x0 * x0 + ss);
+                        const T beta = x0 > T(0) ? -nrm : nrm;
+                        const T v0 = x0 - beta;
+                        const T tw = -v0 / beta;
+                        const T inv = T(1) / v0;
+                        for (int cb = jj + 1; cb < n; cb += cstep) {    // uniform trip count
+                            const int col = cb + cofs;
+                            const bool act = col < n;
+                            T* cc = C + (act ? col : jj) * ldc;
+                            T d = 0;
+                            for (int r = part; r < rows; r += tpc) d += cj[r] * cc[r];
+                            for (int o = 1; o < tpc; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                            if (act) {
+                                const T w = W[(int64_t)jj * ldw + col] + d * inv;
+                                const T tww = tw * w;
+                                const T f = tww * inv;
+                                for (int r = part; r < rows; r += tpc) cc[r] -= f * cj[r];
+                                if (part == 0) W[(int64_t)jj * ldw + col] -= tww;
+                            }
+                        }
+                        __syncthreads();
+                        if (tid == 0) W[(int64_t)jj * ldw + jj] = beta;
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
         __syncthreads();
         // ---------------- one-sided Jacobi on M = R^T (column p of M = row p of R)
+        // Round-robin pairs; tpp threads per pair (rows interleaved), so the three
+        // dot products of a pair need log2(tpp) shuffles each.
         const int meff = (int)(live < (int64_t)n ? live : (int64_t)n);
         const int m = meff + (meff & 1);
-        const T tol = T(4) * Eps<T>::v;
-        for (int sweep = 0; sweep < 60; ++sweep) {
+        const int npair = m / 2;
+        int tpp = 1;
+        while (tpp * 2 <= 32 && tpp * 2 * npair <= 256) tpp *= 2;
+        const int pstep = 256 / tpp, ppart = tid % tpp, pofs = tid / tpp;
+        // rotate only while the columns' cosine exceeds the rounding noise of a
+        // length-n dot product (a smaller threshold never converges in float32)
+        const T tol = T(n) * Eps<T>::v;
+        for (int sweep = 0; sweep < 40 && npair > 0; ++sweep) {
             if (tid == 0) ired[0] = 0;
             __syncthreads();
+            int rot = 0;
             for (int round = 0; round < m - 1; ++round) {
-                for (int pr = wid; pr < m / 2; pr += nwarp) {
+                for (int pb = 0; pb < npair; pb += pstep) {          // uniform trip count
+                    const int pr = pb + pofs;
                     const int x1 = pr, x2 = m - 1 - pr;
                     const int p = x1 == 0 ? 0 : ((x1 - 1 + round) % (m - 1)) + 1;
                     const int q = x2 == 0 ? 0 : ((x2 - 1 + round) % (m - 1)) + 1;
-                    if (p >= meff || q >= meff) continue;
-                    T* Mp = W + (int64_t)p * n;
-                    T* Mq = W + (int64_t)q * n;
+                    const bool act = pr < npair && p < meff && q < meff;
+                    T* Mp = W + (int64_t)(act ? p : 0) * ldw;
+                    T* Mq = W + (int64_t)(act ? q : 0) * ldw;
                     T al = 0, be = 0, ga = 0;
-                    for (int r = lane; r < n; r += 32) {
-                        const T u = Mp[r], v = Mq[r];
-                        al += u * u; be += v * v; ga += u * v;
+                    if (act)
+                        for (int r = ppart; r < n; r += tpp) {
+                            const T u = Mp[r], v = Mq[r];
+                            al += u * u; be += v * v; ga += u * v;
+                        }
+                    for (int o = 1; o < tpp; o <<= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
                     }
-                    al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                    if (al > T(0) && be > T(0) && t_abs(ga) > tol * sqrt(al * be)) {
+                    if (act && al > T(0) && be > T(0) && t_abs(ga) > tol * sqrt(al * be)) {
                         const T zeta = (be - al) / (T(2) * ga);
                         const T t = (zeta >= T(0) ? T(1) : T(-1)) /
                                     (t_abs(zeta) + sqrt(T(1) + zeta * zeta));
                         const T c = T(1) / sqrt(T(1) + t * t);
                         const T sn = c * t;
-                        for (int r = lane; r < n; r += 32) {
+                        for (int r = ppart; r < n; r += tpp) {
                             const T u = Mp[r], v = Mq[r];
                             Mp[r] = c * u - sn * v;
                             Mq[r] = sn * u + c * v;
                         }
-                        if (lane == 0) atomicAdd(&ired[0], 1);
+                        rot = 1;
                     }
                 }
                 __syncthreads();
             }
+            if (rot) atomicOr(&ired[0], 1);
+            __syncthreads();
             if (ired[0] == 0) break;
             __syncthreads();
         }
         // ---------------- singular values, selection (largest first)
         for (int p = wid; p < meff; p += nwarp) {
             T s2 = 0;
-            for (int r = lane; r < n; r += 32) s2 += W[(int64_t)p * n + r] * W[(int64_t)p * n + r];
+            for (int r = lane; r < n; r += 32) s2 += W[(int64_t)p * ldw + r] * W[(int64_t)p * ldw + r];
             s2 = warp_sum(s2);
             if (lane == 0) sig[p] = sqrt(s2);
         }
@@ -269,7 +389,7 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
             if (rank < keep) {
                 T* dst = Qs + (int64_t)(n - keep + rank) * n;
                 const T inv = T(1) / sp;
-                for (int r = lane; r < n; r += 32) dst[r] = W[(int64_t)p * n + r] * inv;
+                for (int r = lane; r < n; r += 32) dst[r] = W[(int64_t)p * ldw + r] * inv;
             }
         }
         __syncthreads();
@@ -352,59 +472,84 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
 }
 
 // ================================================================== projection
-// Left: B <- Q~_i^T B for a block in row i, by column panels of 32 (in place).
-template <class T>
-__global__ void k_proj_left(LevelArgs<T> a, const int* __restrict__ wl_box,
-                            const int* __restrict__ wl_blk, const int* __restrict__ wl_panel) {
-    constexpr int PW = 32;
+// In-place projection of one 32-wide panel of a block with the box's Q~ (Alg. 2:
+// D <- Q~^T D Q~, F <- Q~^T F Q~), as a register-tiled GEMM:
+//   left  (block in row i):    B[:, c0:c0+32]  <- Q~^T B[:, c0:c0+32]
+//   right (block in column i): B[r0:r0+32, :]  <- B[r0:r0+32, :] Q~
+// Each thread owns RPT coordinates of the box (a = ty + 32u) times 4 panel lines
+// (c = 4 tx + v); Q~ is staged in chunks of 32 rows (coalesced) and the panel is read
+// completely into shared memory before anything is written back.
+template <class T, int RPT, bool RIGHT>
+__global__ void __launch_bounds__(256)
+k_proj(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_blk,
+       const int* __restrict__ w_panel) {
+    constexpr int PW = 32, KC = 32;
     const int w = blockIdx.x;
-    const int i = wl_box[w], b = wl_blk[w], c0 = wl_panel[w] * PW;
+    const int i = w_box[w], b = w_blk[w], p0 = w_panel[w] * PW;
     const int n = a.n[i];
-    const int nj = a.n[a.bcol[b]];
-    const int pc = min(PW, nj - c0);
-    const T* Q = a.Q + a.Q_off[i];
+    const int nj = RIGHT ? a.n[a.brow[b]] : a.n[a.bcol[b]];   // the block's other dimension
+    const int pw = min(PW, nj - p0);
+    const T* __restrict__ Q = a.Q + a.Q_off[i];
     T* B = a.blk + a.blk_off[b];
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* P = reinterpret_cast<T*>(sm_raw);            // n x PW
-    for (int x = threadIdx.x; x < n * pc; x += blockDim.x) {
-        const int r = x % n, c = x / n;
-        P[r + c * n] = B[r + (int64_t)(c0 + c) * n];
+    const int nr = (n + KC - 1) / KC * KC;         // n rounded up to whole chunks
+    const int lp = nr + 1;                         // padded lines
+    T* Ps = reinterpret_cast<T*>(sm_raw);          // panel: PW x lp, Ps[c * lp + q]
+    T* Qs = Ps + PW * lp;                          // chunk: KC x lp, Qs[kk * lp + a]
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    // every entry the products read is written (zeros beyond n and beyond the panel)
+    if (!RIGHT) {
+        for (int x = tid; x < nr * PW; x += 256) {
+            const int q = x % nr, c = x / nr;
+            Ps[c * lp + q] = (c < pw && q < n) ? B[q + (int64_t)(p0 + c) * n] : T(0);
+        }
+    } else {
+        for (int x = tid; x < nr * PW; x += 256) {
+            const int c = x % PW, q = x / PW;
+            Ps[c * lp + q] = (c < pw && q < n) ? B[(p0 + c) + (int64_t)q * nj] : T(0);
+        }
     }
-    __syncthreads();
-    for (int x = threadIdx.x; x < n * pc; x += blockDim.x) {
-        const int r = x % n, c = x / n;
-        const T* qr = Q + (int64_t)r * n;
-        T acc = 0;
-        for (int q = 0; q < n; ++q) acc += qr[q] * P[q + c * n];
-        B[r + (int64_t)(c0 + c) * n] = acc;
+    T acc[RPT][4];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int k0 = 0; k0 < n; k0 += KC) {
+        const int kc = min(KC, n - k0);
+        __syncthreads();
+        for (int x = tid; x < KC * nr; x += 256) {
+            const int kk = x % KC, col = x / KC;
+            Qs[kk * lp + col] = (kk < kc && col < n) ? Q[(k0 + kk) + (int64_t)col * n] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KC; ++kk) {
+            T qv[RPT], pv[4];
+            // left: out[a][c] += Q~[q][a] P[q][c];  right: out[c][a] += P[c][q] Q~[q][a]
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int aa = ty + 32 * u;
+                qv[u] = aa < n ? Qs[kk * lp + aa] : T(0);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) pv[v] = Ps[(4 * tx + v) * lp + k0 + kk];
+#pragma unroll
+            for (int u = 0; u < RPT; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += qv[u] * pv[v];
+        }
     }
-}
-
-// Right: B <- B Q~_i for a block in column i, by row panels of 32 (in place).
-template <class T>
-__global__ void k_proj_right(LevelArgs<T> a, const int* __restrict__ wr_box,
-                             const int* __restrict__ wr_blk, const int* __restrict__ wr_panel) {
-    constexpr int PW = 32;
-    const int w = blockIdx.x;
-    const int i = wr_box[w], b = wr_blk[w], r0 = wr_panel[w] * PW;
-    const int n = a.n[i];
-    const int nj = a.n[a.brow[b]];
-    const int pr = min(PW, nj - r0);
-    const T* Q = a.Q + a.Q_off[i];
-    T* B = a.blk + a.blk_off[b];
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* P = reinterpret_cast<T*>(sm_raw);            // PW x n, P[r + c*PW]
-    for (int x = threadIdx.x; x < pr * n; x += blockDim.x) {
-        const int r = x % pr, c = x / pr;
-        P[r + c * PW] = B[(r0 + r) + (int64_t)c * nj];
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < pr * n; x += blockDim.x) {
-        const int r = x % pr, c = x / pr;
-        const T* qc = Q + (int64_t)c * n;
-        T acc = 0;
-        for (int q = 0; q < n; ++q) acc += P[r + q * PW] * qc[q];
-        B[(r0 + r) + (int64_t)c * nj] = acc;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int aa = ty + 32 * u;
+        if (aa >= n) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int c = 4 * tx + v;
+            if (c >= pw) continue;
+            if (!RIGHT) B[aa + (int64_t)(p0 + c) * n] = acc[u][v];
+            else B[(p0 + c) + (int64_t)aa * nj] = acc[u][v];
+        }
     }
 }
 
