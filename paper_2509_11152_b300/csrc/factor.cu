@@ -33,6 +33,7 @@ static LevelArgs<T> args_of(LevelRT& L, DevStatus* st) {
     a.Q = L.Q.as<T>();
     a.LU_off = L.d_LU_off.as<int64_t>();
     a.LU = L.LU.as<T>();
+    a.DI = L.DI.as<T>();
     a.piv_off = L.d_piv_off.as<int64_t>();
     a.piv = L.piv.as<int>();
     a.WU_off = L.d_WU_off.as<int64_t>();
@@ -77,7 +78,7 @@ static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<
 
 template <class T>
 struct SmemLimits {
-    int basis, lu, proj_l, proj_r, gather, trsm_u, trsm_l;
+    int basis, lu, proj_l, proj_r, gather;
 };
 
 template <class T>
@@ -91,8 +92,7 @@ static const SmemLimits<T>& smem_limits() {
         x.proj_r = std::min({raise_smem(k_proj<T, 1, true>), raise_smem(k_proj<T, 2, true>),
                              raise_smem(k_proj<T, 4, true>), raise_smem(k_proj<T, 8, true>)});
         x.gather = raise_smem(k_aug_gather<T>);
-        x.trsm_u = raise_smem(k_trsm_u<T>);
-        x.trsm_l = raise_smem(k_trsm_l<T>);
+
         return x;
     }();
     return lim;
@@ -264,6 +264,7 @@ void FactorImpl<T>::setup_level(size_t a) {
     upload(L.d_fl_cpos, S.fl_cpos, s);
     track(this, L.Q, std::max<int64_t>(1, L.Q_off[S.cnt]) * sizeof(T), s);
     track(this, L.LU, std::max<int64_t>(1, L.LU_off[S.cnt]) * sizeof(T), s);
+    track(this, L.DI, std::max<int64_t>(1, L.Q_off[S.cnt]) * sizeof(T), s);
     track(this, L.piv, std::max<int64_t>(1, L.piv_off[S.cnt]) * sizeof(int), s);
     track(this, L.WU, std::max<int64_t>(1, L.WU_off[S.cnt]) * sizeof(T), s);
     track(this, L.WL, std::max<int64_t>(1, L.WL_off[S.cnt]) * sizeof(T), s);
@@ -282,8 +283,8 @@ struct ColourWork {
     std::vector<int> pr_box, pr_blk, pr_pan, pr_cptr;
     std::vector<int> zf_box, zf_blk, zf_col, zf_cptr;
     std::vector<int> zn_box, zn_blk, zn_col, zn_cptr;
-    // trsm
-    std::vector<int> tu_box, tu_c0, tu_cptr;
+    // W_U / W_L GEMM tiles
+    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;
     // schur tiles
     std::vector<int> tile_tgt, tile_mn, tile_cptr;
 };
@@ -326,7 +327,8 @@ void FactorImpl<T>::run_level(size_t a) {
     W.pr_cptr.push_back(0);
     W.zf_cptr.push_back(0);
     W.zn_cptr.push_back(0);
-    W.tu_cptr.push_back(0);
+    W.wu_cptr.push_back(0);
+    W.wl_cptr.push_back(0);
     W.tile_cptr.push_back(0);
     W.seg_ptr.push_back(0);
     const int PW = 32;
@@ -374,10 +376,14 @@ void FactorImpl<T>::run_level(size_t a) {
                     W.zn_box.push_back(i); W.zn_blk.push_back(bt); W.zn_col.push_back(1);
                 }
             }
-            for (int c0 = 0; c0 < L.Nsum[i] + n; c0 += 8) {
-                W.tu_box.push_back(i);
-                W.tu_c0.push_back(c0);
-            }
+            const int wide = L.Nsum[i] + n;
+            for (int tm = 0; tm * 64 < n; ++tm)
+                for (int tn = 0; tn * 64 < wide; ++tn) {
+                    W.wu_box.push_back(i);
+                    W.wu_mn.push_back((tm << 16) | tn);
+                    W.wl_box.push_back(i);
+                    W.wl_mn.push_back((tn << 16) | tm);
+                }
         }
         for (size_t q = wfirst; q < W.wbase.size(); ++q) W.wbase[q] += ysum;   // after the Y^T rows
         W.box_cptr.push_back((int)W.boxes.size());
@@ -386,7 +392,8 @@ void FactorImpl<T>::run_level(size_t a) {
         W.pr_cptr.push_back((int)W.pr_box.size());
         W.zf_cptr.push_back((int)W.zf_box.size());
         W.zn_cptr.push_back((int)W.zn_box.size());
-        W.tu_cptr.push_back((int)W.tu_box.size());
+        W.wu_cptr.push_back((int)W.wu_box.size());
+        W.wl_cptr.push_back((int)W.wl_box.size());
         // schur tiles
         for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
             const int tb = S.sch_tblk[t];
@@ -419,7 +426,7 @@ void FactorImpl<T>::run_level(size_t a) {
     // seg_ptr is per box (global over colours): make it per-colour local
     DevBuf d_boxes, d_seg_ptr, d_seg_blk, d_seg_j, d_seg_slot, d_seg_yoff, d_ybase, d_ylead, d_wbase;
     DevBuf d_pl_box, d_pl_blk, d_pl_pan, d_pr_box, d_pr_blk, d_pr_pan;
-    DevBuf d_zf_box, d_zf_blk, d_zf_col, d_zn_box, d_zn_blk, d_zn_col, d_tu_box, d_tu_c0;
+    DevBuf d_zf_box, d_zf_blk, d_zf_col, d_zn_box, d_zn_blk, d_zn_col, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
     DevBuf d_tile_tgt, d_tile_mn, d_tgt_blk, d_tgt_ptr, d_c_box, d_c_ablk, d_c_kpos;
     upload(d_boxes, W.boxes, s);
     upload(d_seg_ptr, W.seg_ptr, s);
@@ -442,8 +449,10 @@ void FactorImpl<T>::run_level(size_t a) {
     upload(d_zn_box, W.zn_box, s);
     upload(d_zn_blk, W.zn_blk, s);
     upload(d_zn_col, W.zn_col, s);
-    upload(d_tu_box, W.tu_box, s);
-    upload(d_tu_c0, W.tu_c0, s);
+    upload(d_wu_box, W.wu_box, s);
+    upload(d_wu_mn, W.wu_mn, s);
+    upload(d_wl_box, W.wl_box, s);
+    upload(d_wl_mn, W.wl_mn, s);
     upload(d_tile_tgt, W.tile_tgt, s);
     upload(d_tile_mn, W.tile_mn, s);
     upload(d_tgt_blk, S.sch_tblk, s);
@@ -522,18 +531,20 @@ void FactorImpl<T>::run_level(size_t a) {
         k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, d_boxes.as<int>() + b0, lu_in);
         kend();
         H2_LAUNCHED();
-        const int tu0 = W.tu_cptr[c], ntu = W.tu_cptr[c + 1] - tu0;
-        const int tsm = 8 * W.nmax[c] * (int)sizeof(T);
-        if (ntu) {
+        const int wu0 = W.wu_cptr[c], nwu = W.wu_cptr[c + 1] - wu0;
+        if (nwu) {
             kbegin(H2_K_TRSM);
-            k_trsm_u<T><<<ntu, 256, tsm, s>>>(ar, d_tu_box.as<int>() + tu0, d_tu_c0.as<int>() + tu0);
+            k_wgemm<T, true><<<nwu, 256, 0, s>>>(ar, d_wu_box.as<int>() + wu0, d_wu_mn.as<int>() + wu0);
             kend();
-            H2_LAUNCHED();
-            kbegin(H2_K_TRSM);
-            k_trsm_l<T><<<ntu, 256, tsm, s>>>(ar, d_tu_box.as<int>() + tu0, d_tu_c0.as<int>() + tu0);
-            kend();
-            H2_LAUNCHED();
         }
+        H2_LAUNCHED();
+        const int wl0 = W.wl_cptr[c], nwl = W.wl_cptr[c + 1] - wl0;
+        if (nwl) {
+            kbegin(H2_K_TRSM);
+            k_wgemm<T, false><<<nwl, 256, 0, s>>>(ar, d_wl_box.as<int>() + wl0, d_wl_mn.as<int>() + wl0);
+            kend();
+        }
+        H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_LU);
         // ---- Schur update and zeroing of the eliminated rows / columns
@@ -758,7 +769,7 @@ void FactorImpl<T>::factorize() {
     stats.top_level = P.top;
     stats.top_size = nt;
     int64_t fb = 0;
-    for (auto& L : lv) fb += L.Q.bytes + L.LU.bytes + L.piv.bytes + L.WU.bytes + L.WL.bytes;
+    for (auto& L : lv) fb += L.Q.bytes + L.LU.bytes + L.DI.bytes + L.piv.bytes + L.WU.bytes + L.WL.bytes;
     fb += Dt.bytes + tpiv.bytes;
     stats.factor_bytes = fb;
     // layout export (levels 0 .. nlevels-1)

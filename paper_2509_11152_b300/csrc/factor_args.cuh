@@ -33,6 +33,7 @@ struct LevelArgs {
     T* Q;
     const int64_t* LU_off;
     T* LU;
+    T* DI;                 // D_RR^-1 per box (same offsets as Q)
     const int64_t* piv_off;
     int* piv;
     const int64_t* WU_off;

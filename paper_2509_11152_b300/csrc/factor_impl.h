@@ -22,7 +22,7 @@ struct LevelRT {
     DevBuf d_nb_ptr, d_nb_col, d_nbofs, d_Nsum, d_nb_blk, d_nb_blkT, d_diag_blk, d_voff;
     DevBuf d_fl_tbox, d_fl_tptr, d_fl_ci, d_fl_cpos;
     // device: factor data
-    DevBuf Q, LU, piv, WU, WL;
+    DevBuf Q, LU, DI, piv, WU, WL;
     // device: working data (freed after the level close)
     DevBuf blk, V;
 };

@@ -650,112 +650,142 @@ k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
     }
     if (in_smem)
         for (int x = tid; x < r * r; x += blockDim.x) G[x] = W[x];
+    // D_RR^-1 = U^-1 L^-1 P^T: the permuted identity, then the two triangular solves
+    // (column parallel; the inverse feeds W_U / W_L as GEMMs and the diagonal solves)
+    T* X = a.DI + a.Q_off[i];
+    if (tid == 0) {
+        // row a of P^T is e_{sigma(a)}; sigma from the interchanges in forward order
+        int* sg = reinterpret_cast<int*>(X + (int64_t)r * r - r);   // temporary: last column
+        for (int q = 0; q < r; ++q) sg[q] = q;
+        for (int j = 0; j < r; ++j) { const int p = pv[j]; const int t0 = sg[j]; sg[j] = sg[p]; sg[p] = t0; }
+    }
+    __syncthreads();
+    {
+        const int* sg = reinterpret_cast<const int*>(X + (int64_t)r * r - r);
+        int my[4];
+        for (int q = 0; q < 4; ++q) my[q] = (tid + q * 256 < r) ? sg[tid + q * 256] : 0;
+        __syncthreads();
+        for (int x = tid; x < r * r; x += blockDim.x) X[x] = T(0);
+        __syncthreads();
+        for (int q = 0; q < 4; ++q)
+            if (tid + q * 256 < r) X[(tid + q * 256) + (int64_t)my[q] * r] = T(1);
+    }
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {                      // L (unit lower)
+        const int m = r - j - 1;
+        for (int x = tid; x < m * r; x += blockDim.x) {
+            const int rr = j + 1 + x % m, c = x / m;
+            X[rr + (int64_t)c * r] -= W[rr + (int64_t)j * r] * X[j + (int64_t)c * r];
+        }
+        __syncthreads();
+    }
+    for (int j = r - 1; j >= 0; --j) {                 // U
+        const T d = W[j + (int64_t)j * r];
+        for (int c = tid; c < r; c += blockDim.x) X[j + (int64_t)c * r] /= d;
+        __syncthreads();
+        for (int x = tid; x < j * r; x += blockDim.x) {
+            const int rr = x % j, c = x / j;
+            X[rr + (int64_t)c * r] -= W[rr + (int64_t)j * r] * X[j + (int64_t)c * r];
+        }
+        __syncthreads();
+    }
 }
 
-// W_U^i = D_RR^-1 [D_{i_R, j} ..., D_{i_R, i_S}]: one warp per column (8 per block).
-template <class T>
-__global__ void k_trsm_u(LevelArgs<T> a, const int* __restrict__ w_box,
-                         const int* __restrict__ w_col0) {
+// W_U^i = D_RR^-1 [D_{i_R, j} ..., D_{i_R, i_S}]   (LEFT)  and
+// W_L^i = [D_{j, i_R}; ...; D_{i_S, i_R}] D_RR^-1  (!LEFT), as 64x64-tiled GEMMs with
+// K = r_i; the gathered operand's columns (rows) are located per tile from N(i).
+template <class T, bool LEFT>
+__global__ void __launch_bounds__(256)
+k_wgemm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_mn) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    __shared__ const T* gptr[64];
+    __shared__ int64_t gld[64];
     const int i = w_box[blockIdx.x];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col = w_col0[blockIdx.x] + wid;
-    const int n = a.n[i], kt = a.kt[i], r = n - kt;
-    const int ns = a.Nsum[i];
-    if (r <= 0 || col >= ns + kt) return;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* buf = reinterpret_cast<T*>(sm_raw) + (size_t)wid * n;
-    const T* src;
-    if (col >= ns) {
-        src = a.blk + a.blk_off[a.diag_blk[i]] + (int64_t)(r + col - ns) * n;
-    } else {
-        int pos = a.nb_ptr[i];
-        for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
-            const int j = a.nb_col[p];
-            if (j != i && a.nbofs[p] <= col && col < a.nbofs[p] + a.n[j]) { pos = p; break; }
+    const int mn = w_mn[blockIdx.x];
+    const int n = a.n[i], kt = a.kt[i], r = n - kt, ns = a.Nsum[i];
+    const int nt = ns + kt;                       // width of W_U / height of W_L
+    const int M = LEFT ? r : nt, N = LEFT ? nt : r;
+    const int m0 = (mn >> 16) * BM, n0 = (mn & 0xffff) * BN;
+    if (r <= 0 || m0 >= M || n0 >= N) return;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const T* DI = a.DI + a.Q_off[i];
+    // locate the gathered lines: columns of D_{i_R,*} (LEFT) or rows of D_{*,i_R}
+    if (tid < 64) {
+        const int c = (LEFT ? n0 : m0) + tid;
+        const T* ptr = nullptr;
+        int64_t ldl = 0;
+        if (c < nt) {
+            if (c >= ns) {
+                const T* Dii = a.blk + a.blk_off[a.diag_blk[i]];
+                if (LEFT) { ptr = Dii + (int64_t)(r + c - ns) * n; ldl = 1; }
+                else { ptr = Dii + (r + c - ns); ldl = n; }
+            } else {
+                for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
+                    const int j = a.nb_col[p];
+                    if (j != i && a.nbofs[p] <= c && c < a.nbofs[p] + a.n[j]) {
+                        if (LEFT) { ptr = a.blk + a.blk_off[a.nb_blk[p]] + (int64_t)(c - a.nbofs[p]) * n; ldl = 1; }
+                        else { ptr = a.blk + a.blk_off[a.nb_blkT[p]] + (c - a.nbofs[p]); ldl = a.n[j]; }
+                        break;
+                    }
+                }
+            }
         }
-        src = a.blk + a.blk_off[a.nb_blk[pos]] + (int64_t)(col - a.nbofs[pos]) * n;
+        gptr[tid] = ptr;
+        gld[tid] = ldl;
     }
-    for (int x = lane; x < r; x += 32) buf[x] = src[x];
-    __syncwarp();
-    const T* LU = a.LU + a.LU_off[i];
-    const int* pv = a.piv + a.piv_off[i];
-    if (lane == 0)
-        for (int j = 0; j < r; ++j) {
-            const int p = pv[j];
-            if (p < j || p >= r) { dev_fail(a.status, H2_ERR_SINGULAR, a.level, i); break; }
-            if (p != j) { const T t0 = buf[j]; buf[j] = buf[p]; buf[p] = t0; }
+    __syncthreads();
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int k0 = 0; k0 < r; k0 += BK) {
+        for (int x = tid; x < BK * BM; x += 256) {
+            const int kk = x / BM, rr = x % BM;
+            const int gr = m0 + rr, gk = k0 + kk;
+            T v = T(0);
+            if (gr < M && gk < r) {
+                if (LEFT) v = DI[gr + (int64_t)gk * r];
+                else if (gptr[rr]) v = gptr[rr][(int64_t)gk * gld[rr]];
+            }
+            As[kk][rr] = v;
         }
-    __syncwarp();
-    for (int j = 0; j < r; ++j) {
-        const T xj = buf[j];
-        for (int x = j + 1 + lane; x < r; x += 32) buf[x] -= LU[x + (int64_t)j * r] * xj;
-        __syncwarp();
-    }
-    for (int j = r - 1; j >= 0; --j) {
-        if (lane == 0) buf[j] /= LU[j + (int64_t)j * r];
-        __syncwarp();
-        const T xj = buf[j];
-        for (int x = lane; x < j; x += 32) buf[x] -= LU[x + (int64_t)j * r] * xj;
-        __syncwarp();
-    }
-    T* out = a.WU + a.WU_off[i] + (int64_t)col * r;
-    for (int x = lane; x < r; x += 32) out[x] = buf[x];
-}
-
-// W_L^i = [D_{j, i_R}; D_{i_S, i_R}] D_RR^-1: one warp per row (8 per block).
-template <class T>
-__global__ void k_trsm_l(LevelArgs<T> a, const int* __restrict__ w_box,
-                         const int* __restrict__ w_row0) {
-    const int i = w_box[blockIdx.x];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = w_row0[blockIdx.x] + wid;
-    const int n = a.n[i], kt = a.kt[i], r = n - kt;
-    const int ns = a.Nsum[i];
-    if (r <= 0 || row >= ns + kt) return;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* buf = reinterpret_cast<T*>(sm_raw) + (size_t)wid * n;
-    const T* src;
-    int64_t stride;
-    if (row >= ns) {
-        src = a.blk + a.blk_off[a.diag_blk[i]] + (r + row - ns);
-        stride = n;
-    } else {
-        int pos = a.nb_ptr[i];
-        for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
-            const int j = a.nb_col[p];
-            if (j != i && a.nbofs[p] <= row && row < a.nbofs[p] + a.n[j]) { pos = p; break; }
+        for (int x = tid; x < BK * BN; x += 256) {
+            const int kk = x % BK, cc = x / BK;
+            const int gc = n0 + cc, gk = k0 + kk;
+            T v = T(0);
+            if (gc < N && gk < r) {
+                if (LEFT) { if (gptr[cc]) v = gptr[cc][gk]; }
+                else v = DI[gk + (int64_t)gc * r];
+            }
+            Bs[kk][cc] = v;
         }
-        stride = a.n[a.nb_col[pos]];
-        src = a.blk + a.blk_off[a.nb_blkT[pos]] + (row - a.nbofs[pos]);
-    }
-    for (int x = lane; x < r; x += 32) buf[x] = src[(int64_t)x * stride];
-    __syncwarp();
-    const T* LU = a.LU + a.LU_off[i];
-    const int* pv = a.piv + a.piv_off[i];
-    // x U = y
-    for (int j = 0; j < r; ++j) {
-        if (lane == 0) buf[j] /= LU[j + (int64_t)j * r];
-        __syncwarp();
-        const T xj = buf[j];
-        for (int b = j + 1 + lane; b < r; b += 32) buf[b] -= xj * LU[j + (int64_t)b * r];
-        __syncwarp();
-    }
-    // z L = x (unit lower)
-    for (int j = r - 1; j >= 0; --j) {
-        const T zj = buf[j];
-        for (int b = lane; b < j; b += 32) buf[b] -= zj * LU[j + (int64_t)b * r];
-        __syncwarp();
-    }
-    if (lane == 0)
-        for (int j = r - 1; j >= 0; --j) {
-            const int p = pv[j];
-            if (p < j || p >= r) { dev_fail(a.status, H2_ERR_SINGULAR, a.level, i); break; }
-            if (p != j) { const T t0 = buf[j]; buf[j] = buf[p]; buf[p] = t0; }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = As[kk][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][ty + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
         }
-    __syncwarp();
-    T* out = a.WL + a.WL_off[i] + row;
-    const int64_t ldw = a.WLld[i];
-    for (int x = lane; x < r; x += 32) out[(int64_t)x * ldw] = buf[x];
+        __syncthreads();
+    }
+    T* out = LEFT ? a.WU + a.WU_off[i] : a.WL + a.WL_off[i];
+    const int64_t ldo = LEFT ? r : a.WLld[i];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int gr = m0 + tx + 16 * u, gc = n0 + ty + 16 * v;
+            if (gr < M && gc < N) out[gr + (int64_t)gc * ldo] = acc[u][v];
+        }
 }
 
 // ================================================================== Schur update

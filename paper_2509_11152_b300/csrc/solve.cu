@@ -121,43 +121,26 @@ __global__ void s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n
     }
 }
 
-// diagonal solves with the redundant blocks: lower (P, L) or upper (U); one warp per
-// (box, right-hand side)
+// diagonal solve with the redundant block: x_{i_R} <- D_RR^-1 x_{i_R} (the explicit
+// inverse formed by the factorisation), one block per box
 template <class T>
-__global__ void s_diag(const int* __restrict__ n, const int* __restrict__ kt, const T* __restrict__ LU,
-                       const int64_t* __restrict__ LU_off, const int* __restrict__ piv,
-                       const int64_t* __restrict__ piv_off, const int64_t* __restrict__ voff,
-                       T* __restrict__ x, int nrhs, int cnt, int upper) {
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= cnt * nrhs) return;
-    const int i = w / nrhs, c = w % nrhs;
+__global__ void s_diag(const int* __restrict__ n, const int* __restrict__ kt, const T* __restrict__ DI,
+                       const int64_t* __restrict__ DI_off, const int64_t* __restrict__ voff,
+                       T* __restrict__ x, int nrhs) {
+    const int i = blockIdx.x;
     const int ni = n[i], r = ni - kt[i];
     if (r <= 0) return;
-    T* xr = x + voff[i] * nrhs + (int64_t)c * ni;
-    const T* F = LU + LU_off[i];
-    if (!upper) {
-        const int* pv = piv + piv_off[i];
-        if (lane == 0)
-            for (int j = 0; j < r; ++j) {
-                const int p = pv[j];
-                if (p < j || p >= r) break;        // never produced by the LU kernel
-                if (p != j) { const T t0 = xr[j]; xr[j] = xr[p]; xr[p] = t0; }
-            }
-        __syncwarp();
-        for (int j = 0; j < r; ++j) {
-            const T xj = xr[j];
-            for (int a = j + 1 + lane; a < r; a += 32) xr[a] -= F[a + (int64_t)j * r] * xj;
-            __syncwarp();
-        }
-    } else {
-        for (int j = r - 1; j >= 0; --j) {
-            if (lane == 0) xr[j] /= F[j + (int64_t)j * r];
-            __syncwarp();
-            const T xj = xr[j];
-            for (int a = lane; a < j; a += 32) xr[a] -= F[a + (int64_t)j * r] * xj;
-            __syncwarp();
-        }
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* xs = reinterpret_cast<T*>(sm_raw);
+    T* xi = x + voff[i] * nrhs;
+    const T* D = DI + DI_off[i];
+    for (int e = threadIdx.x; e < r * nrhs; e += blockDim.x) xs[e] = xi[(e % r) + (int64_t)(e / r) * ni];
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * nrhs; e += blockDim.x) {
+        const int a = e % r, c = e / r;
+        T acc = 0;
+        for (int q = 0; q < r; ++q) acc += D[a + (int64_t)q * r] * xs[q + c * r];
+        xi[a + (int64_t)c * ni] = acc;
     }
 }
 
@@ -224,9 +207,26 @@ __global__ void s_top_solve(const double* __restrict__ LU, const int* __restrict
 }
 
 // ------------------------------------------------------------------ driver
+template <class K>
+static void allow_smem(K kern) {
+    int dev = 0, optin = 0;
+    H2_CUDA_CHECK(cudaGetDevice(&dev));
+    H2_CUDA_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    H2_CUDA_CHECK(cudaFuncGetAttributes(&fa, kern));
+    H2_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       optin - (int)fa.sharedSizeBytes));
+}
+
 template <class T>
 void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
     cudaStream_t s = stream;
+    static bool smem_ready = false;
+    if (!smem_ready) {
+        allow_smem(s_apply_q<T>);
+        allow_smem(s_diag<T>);
+        smem_ready = true;
+    }
     const Plan& P = A->plan;
     const size_t nl = P.levels.size();
     std::vector<DevBuf> vec(nl + 1);
@@ -280,11 +280,9 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
                 count_launch();
             }
         }
-        const int nw = L.cnt * nrhs;
-        s_diag<T><<<(nw + 7) / 8, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.LU.as<T>(),
-                                               L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
-                                               L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(),
-                                               vec[a].as<T>(), nrhs, L.cnt, 0);
+        s_diag<T><<<L.cnt, 256, nmax * nrhs * (int)sizeof(T), s>>>(L.d_n.as<int>(), L.d_kt.as<int>(),
+                                                                 L.DI.as<T>(), L.d_Q_off.as<int64_t>(),
+                                                                 L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
         count_launch();
         LevelRT& Pn = lv[a + 1];
         s_sweep<T><<<Pn.cnt, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.d_voff.as<int64_t>(),
@@ -315,12 +313,7 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
                                           vec[a].as<T>(), Pn.d_voff.as<int64_t>(), vec[a + 1].as<T>(),
                                           nrhs, 0);
         count_launch();
-        const int nw = L.cnt * nrhs;
-        s_diag<T><<<(nw + 7) / 8, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.LU.as<T>(),
-                                               L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
-                                               L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(),
-                                               vec[a].as<T>(), nrhs, L.cnt, 1);
-        count_launch();
+
         int nmax = 1;
         for (int v : L.n) nmax = std::max(nmax, v);
         const int qsm = nmax * nrhs * (int)sizeof(T);
