@@ -310,32 +310,72 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
         }
         __syncthreads();
         // ---------------- one-sided Jacobi on M = R^T (column p of M = row p of R)
-        // Round-robin pairs; tpp threads per pair (rows interleaved), so the three
-        // dot products of a pair need log2(tpp) shuffles each.
+        // Round-robin pairs over the active columns, tpp threads per pair (rows
+        // interleaved).  Each sweep first drops columns whose squared norm is below
+        // defl^2: even all of them together stay under 1e-3 eps_fill (1e-6 in float64),
+        // so they cannot change which singular values exceed eps_fill; the remaining
+        // columns are ordered by decreasing norm (faster convergence).
         const int meff = (int)(live < (int64_t)n ? live : (int64_t)n);
-        const int m = meff + (meff & 1);
-        const int npair = m / 2;
-        int tpp = 1;
-        while (tpp * 2 <= 32 && tpp * 2 * npair <= 256) tpp *= 2;
-        const int pstep = 256 / tpp, ppart = tid % tpp, pofs = tid / tpp;
-        // rotate only while the columns' cosine exceeds the rounding noise of a
-        // length-n dot product (a smaller threshold never converges in float32)
+        int* act = reinterpret_cast<int*>(tau);          // active columns
+        int* nact = reinterpret_cast<int*>(C);           // next sweep's active columns
         const T tol = T(n) * Eps<T>::v;
-        for (int sweep = 0; sweep < 40 && npair > 0; ++sweep) {
-            if (tid == 0) ired[0] = 0;
+        const T defl = (sizeof(T) == 4 ? T(1e-3) : T(1e-6)) * eps_fill / sqrt(T(n));
+        const T defl2 = defl * defl;
+        if (tid == 0) ired[2] = meff;
+        for (int p = tid; p < meff; p += blockDim.x) act[p] = p;
+        __syncthreads();
+        for (int sweep = 0; sweep < 40; ++sweep) {
+            const int mcur = ired[2];
+            for (int q = wid; q < mcur; q += nwarp) {
+                const int p = act[q];
+                T s2 = 0;
+                for (int r = lane; r < n; r += 32) s2 += W[(int64_t)p * ldw + r] * W[(int64_t)p * ldw + r];
+                s2 = warp_sum(s2);
+                if (lane == 0) sig[p] = s2;
+            }
             __syncthreads();
+            for (int q = tid; q < mcur; q += blockDim.x) {
+                const int p = act[q];
+                const T sp = sig[p];
+                if (sp >= defl2) {
+                    int rank = 0;
+                    for (int q2 = 0; q2 < mcur; ++q2) {
+                        const int p2 = act[q2];
+                        const T s2 = sig[p2];
+                        rank += (s2 >= defl2) && (s2 > sp || (s2 == sp && p2 < p));
+                    }
+                    nact[rank] = p;
+                }
+            }
+            if (tid == 0) {
+                int c = 0;
+                for (int q = 0; q < mcur; ++q) c += sig[act[q]] >= defl2;
+                ired[3] = c;
+                ired[0] = 0;
+            }
+            __syncthreads();
+            const int ma = ired[3];
+            for (int q = tid; q < ma; q += blockDim.x) act[q] = nact[q];
+            if (tid == 0) ired[2] = ma;
+            __syncthreads();
+            const int m = ma + (ma & 1);
+            const int npair = m / 2;
+            if (npair == 0) break;
+            int tpp = 1;
+            while (tpp * 2 <= 32 && tpp * 2 * npair <= 256) tpp *= 2;
+            const int pstep = 256 / tpp, ppart = tid % tpp, pofs = tid / tpp;
             int rot = 0;
             for (int round = 0; round < m - 1; ++round) {
                 for (int pb = 0; pb < npair; pb += pstep) {          // uniform trip count
                     const int pr = pb + pofs;
                     const int x1 = pr, x2 = m - 1 - pr;
-                    const int p = x1 == 0 ? 0 : ((x1 - 1 + round) % (m - 1)) + 1;
-                    const int q = x2 == 0 ? 0 : ((x2 - 1 + round) % (m - 1)) + 1;
-                    const bool act = pr < npair && p < meff && q < meff;
-                    T* Mp = W + (int64_t)(act ? p : 0) * ldw;
-                    T* Mq = W + (int64_t)(act ? q : 0) * ldw;
+                    const int px = x1 == 0 ? 0 : ((x1 - 1 + round) % (m - 1)) + 1;
+                    const int qx = x2 == 0 ? 0 : ((x2 - 1 + round) % (m - 1)) + 1;
+                    const bool on = pr < npair && px < ma && qx < ma;
+                    T* Mp = W + (int64_t)(on ? act[px] : 0) * ldw;
+                    T* Mq = W + (int64_t)(on ? act[qx] : 0) * ldw;
                     T al = 0, be = 0, ga = 0;
-                    if (act)
+                    if (on)
                         for (int r = ppart; r < n; r += tpp) {
                             const T u = Mp[r], v = Mq[r];
                             al += u * u; be += v * v; ga += u * v;
@@ -345,7 +385,7 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
                         be += __shfl_xor_sync(0xffffffffu, be, o);
                         ga += __shfl_xor_sync(0xffffffffu, ga, o);
                     }
-                    if (act && al > T(0) && be > T(0) && t_abs(ga) > tol * sqrt(al * be)) {
+                    if (on && al > T(0) && be > T(0) && t_abs(ga) > tol * sqrt(al * be)) {
                         const T zeta = (be - al) / (T(2) * ga);
                         const T t = (zeta >= T(0) ? T(1) : T(-1)) /
                                     (t_abs(zeta) + sqrt(T(1) + zeta * zeta));
