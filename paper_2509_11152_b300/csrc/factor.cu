@@ -76,6 +76,16 @@ static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
 }
 
+// Schur tile edge
+template <class T> constexpr int schur_tile() { return 64; }
+
+template <class T>
+static void launch_schur(int ntile, cudaStream_t s, const LevelArgs<T>& ar, int c, const int* tb,
+                         const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
+                         const int* tmn) {
+    k_schur<T><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+}
+
 template <class T>
 struct SmemLimits {
     int basis, lu, proj_l, proj_r, gather;
@@ -398,8 +408,9 @@ void FactorImpl<T>::run_level(size_t a) {
         for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
             const int tb = S.sch_tblk[t];
             const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
-            for (int tm = 0; tm * 64 < m; ++tm)
-                for (int tn = 0; tn * 64 < nn; ++tn) {
+            const int ts = schur_tile<T>();
+            for (int tm = 0; tm * ts < m; ++tm)
+                for (int tn = 0; tn * ts < nn; ++tn) {
                     W.tile_tgt.push_back(t);
                     W.tile_mn.push_back((tm << 16) | tn);
                 }
@@ -549,13 +560,14 @@ void FactorImpl<T>::run_level(size_t a) {
         mark(PH_LU);
         // ---- Schur update and zeroing of the eliminated rows / columns
         const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
-        if (ntile)
+        if (ntile) {
             kbegin(H2_K_SCHUR);
-            k_schur<T><<<ntile, 256, 0, s>>>(ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(),
-                                             d_c_box.as<int>(), d_c_ablk.as<int>(), d_c_kpos.as<int>(),
-                                             d_tile_tgt.as<int>() + t0, d_tile_mn.as<int>() + t0);
+            launch_schur<T>(ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
+                            d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
+                            d_tile_mn.as<int>() + t0);
             kend();
-            H2_LAUNCHED();
+        }
+        H2_LAUNCHED();
         const int zn0 = W.zn_cptr[c], nzn = W.zn_cptr[c + 1] - zn0;
         if (nzn) {
             kbegin(H2_K_ZERO);
@@ -630,21 +642,23 @@ void FactorImpl<T>::close_level(size_t a) {
     upload(d_cf, S.cl_fblk, s);
     upload(d_ca, S.cl_adm, s);
     const int nbp = Pn.S->nblocks();
-    if (nbp)
+    if (nbp) {
         kbegin(H2_K_CLOSE);
         k_close_blocks<T><<<nbp, 256, 0, s>>>(ar, Pn.blk.as<T>(), Pn.d_blk_off.as<int64_t>(),
                                               Pn.d_brow.as<int>(), Pn.d_bcol.as<int>(), d_cd.as<int>(),
                                               d_cf.as<int>(), d_ca.as<int64_t>(), M.S.as<double>(),
                                               M.d_S_off.as<int64_t>());
         kend();
-        H2_LAUNCHED();
-    if (a + 1 < lv.size() - 1)
+    }
+    H2_LAUNCHED();
+    if (a + 1 < lv.size() - 1) {          // the top level keeps no basis
         kbegin(H2_K_CLOSE);
         k_close_basis<T><<<Pn.cnt, 256, 0, s>>>(ar, Pn.V.as<T>(), Pn.d_V_off.as<int64_t>(),
                                                 Pn.d_k.as<int>(), M.E.as<double>(),
                                                 M.d_E_off.as<int64_t>(), L.S->first);
         kend();
-        H2_LAUNCHED();
+    }
+    H2_LAUNCHED();
     H2_CUDA_CHECK(cudaGetLastError());
     mark(PH_CLOSE);
     account(PH_CLOSE, 0, 2.0 * sizeof(T) * (double)Pn.blk_off.back());
