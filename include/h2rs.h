@@ -122,6 +122,22 @@ H2_API void h2_matrix_destroy(h2_matrix* A);
 H2_API int h2_matvec(const h2_matrix* A, int32_t nrhs, const double* x, int64_t ldx,
               double* y, int64_t ldy, int32_t on_device);
 
+/* The same product with no device allocation, for callers that may not allocate
+ * device memory while it runs (an application that owns all of the GPU's memory and
+ * forbids cudaMalloc/cudaFree, or a tight solver loop that cannot pay for an allocator
+ * call or the synchronisation of a free).  No counterpart in the paper.
+ * The coefficient vectors live in one static device array of H2_MATVEC_STATIC_WORDS
+ * doubles (32 MiB) that every GPU loading the library keeps until the process exits.
+ * x and y are device pointers (n x nrhs, ldx/ldy >= n).  Calls needing more than the
+ * array (2 * sum(rank) * nrhs doubles) return H2_ERR_ARG with a message.  The first
+ * call on a device looks up the array's device address, so make that first call
+ * before any stream capture.  All calls share the array and it keeps the last call's
+ * contents (every value read is written first within a call); calls that overlap on
+ * the GPU race, so serialise them.  Errors: H2_ERR_ARG, H2_ERR_CUDA. */
+#define H2_MATVEC_STATIC_WORDS (1 << 22)
+H2_API int h2_matvec_static(const h2_matrix* A, int32_t nrhs, const double* x, int64_t ldx,
+                            double* y, int64_t ldy);
+
 /* ------------------------------------------------------------- factorisation */
 typedef struct {
     double eps_lu;              /* truncation threshold of the fill (Alg. 1)           */

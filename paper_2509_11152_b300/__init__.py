@@ -5,8 +5,9 @@ The compute path is the CUDA library ``libh2rs.so`` (sources in ``csrc/``, C-ABI
 """
 from .binding import (H2_PREC_FP32, H2_PREC_FP64, H2Error, colmajor, h2_factor_create,
                       h2_factor_stats_get, h2_layout_get, h2_matrix_create, h2_matvec,
+                      h2_matvec_static,
                       h2_plan_query, h2_refine_solve, h2_solve, h2_version, lib)
 
 __all__ = ["H2_PREC_FP32", "H2_PREC_FP64", "H2Error", "colmajor", "h2_factor_create",
-           "h2_factor_stats_get", "h2_layout_get", "h2_matrix_create", "h2_matvec", "h2_plan_query",
+           "h2_factor_stats_get", "h2_layout_get", "h2_matrix_create", "h2_matvec", "h2_matvec_static", "h2_plan_query",
            "h2_refine_solve", "h2_solve", "h2_version", "lib"]

@@ -62,6 +62,8 @@ _SIGS = [
     ("h2_matrix_destroy", None, [ctypes.c_void_p]),
     ("h2_matvec", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    ("h2_matvec_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int64]),
     ("h2_factor_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(h2_factor_opts),
                                         ctypes.POINTER(ctypes.c_void_p)]),
     ("h2_factor_destroy", None, [ctypes.c_void_p]),
@@ -229,6 +231,16 @@ def h2_matvec(M: Matrix, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
     if nrhs != nrhs_y or dev != dev_y:
         raise ValueError("x and y must match in shape and device")
     _check(lib().h2_matvec(M.handle, nrhs, ctypes.c_void_p(px), ldx, ctypes.c_void_p(py), ldy, dev))
+    return y
+
+
+def h2_matvec_static(M: Matrix, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """``h2_matvec`` without device allocation (x, y on the GPU; see the header)."""
+    px, nrhs, ldx, dev = _vec(x)
+    py, nrhs_y, ldy, dev_y = _vec(y)
+    if nrhs != nrhs_y or not dev or not dev_y:
+        raise ValueError("x and y must be GPU tensors of the same shape")
+    _check(lib().h2_matvec_static(M.handle, nrhs, ctypes.c_void_p(px), ldx, ctypes.c_void_p(py), ldy))
     return y
 
 

@@ -173,42 +173,49 @@ void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out
 
 // ------------------------------------------------------------------ driver
 void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
-                cudaStream_t s) {
+                cudaStream_t s, double* scratch) {
     const HostStructure& H = M.H;
     const int d = H.d;
     const int64_t ncoef = M.coef_off.back();
-    DevBuf xh, yh;
-    xh.alloc(std::max<int64_t>(1, ncoef * nrhs) * sizeof(double), s);
-    yh.alloc(std::max<int64_t>(1, ncoef * nrhs) * sizeof(double), s);
+    DevBuf xh_buf, yh_buf;
+    double* xh_p = scratch;
+    double* yh_p = scratch ? scratch + ncoef * nrhs : nullptr;
+    if (!scratch) {
+        xh_buf.alloc(std::max<int64_t>(1, ncoef * nrhs) * sizeof(double), s);
+        yh_buf.alloc(std::max<int64_t>(1, ncoef * nrhs) * sizeof(double), s);
+        xh_p = xh_buf.as<double>();
+        yh_p = yh_buf.as<double>();
+    }
+    struct { double* p; } xh{xh_p}, yh{yh_p};
     const int64_t first_leaf = (int64_t(1) << d) - 1;
     const int nleaf = 1 << d;
     const int64_t* rank = M.d_rank.as<int64_t>();
     const int64_t* coef = M.d_coef_off.as<int64_t>();
     mv_leaf_up<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
                                      M.d_node_size.as<int64_t>(), rank, coef, first_leaf, x, ldx,
-                                     xh.as<double>(), nrhs);
+                                     xh.p, nrhs);
     count_launch();
     for (int l = d; l >= 1; --l) {
         const int64_t pf = (int64_t(1) << (l - 1)) - 1;
         mv_up<<<1 << (l - 1), 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, pf,
-                                           xh.as<double>(), nrhs);
+                                           xh.p, nrhs);
         count_launch();
     }
     mv_couple<<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
                                                   M.d_adm_ptr.as<int64_t>(), M.d_adm_col.as<int64_t>(), rank,
-                                                  coef, xh.as<double>(), yh.as<double>(), nrhs);
+                                                  coef, xh.p, yh.p, nrhs);
     count_launch();
     for (int l = 1; l <= d; ++l) {
         const int64_t f = (int64_t(1) << l) - 1;
         mv_down<<<1 << l, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, f,
-                                       yh.as<double>(), nrhs);
+                                       yh.p, nrhs);
         count_launch();
     }
     mv_leaf_down<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),
                                        M.d_D_off.as<int64_t>(), M.d_inad_ptr.as<int64_t>(),
                                        M.d_inad_col.as<int64_t>(), M.d_node_start.as<int64_t>(),
                                        M.d_node_size.as<int64_t>(), rank, coef, first_leaf,
-                                       yh.as<double>(), x, ldx, y, ldy, nrhs);
+                                       yh.p, x, ldx, y, ldy, nrhs);
     count_launch();
     H2_CUDA_CHECK(cudaGetLastError());
 }

@@ -5,8 +5,10 @@
 
 namespace h2rs {
 
+// y = A x on the device.  The coefficient vectors (2 * sum(rank) * nrhs doubles) are
+// allocated stream-ordered, or taken from `scratch` when it is not null.
 void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
-                cudaStream_t s);
+                cudaStream_t s, double* scratch = nullptr);
 
 // r = b - y;  x += d;  out[c] = ||v_c||^2  (all n x nrhs column-major, device)
 void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, double* r, int64_t ldr,
