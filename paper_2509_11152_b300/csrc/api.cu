@@ -20,6 +20,16 @@ void DevBuf::alloc(size_t nbytes, cudaStream_t s) {
     stream = s;
     if (nbytes == 0) nbytes = 1;
     cudaError_t e = cudaMallocAsync(&ptr, nbytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        // the pool keeps freed memory reserved; give it back and try once more
+        (void)cudaGetLastError();
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaStreamSynchronize(s) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocAsync(&ptr, nbytes, s);
+    }
     if (e != cudaSuccess) {
         ptr = nullptr;
         (void)cudaGetLastError();
