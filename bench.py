@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--fp64-arm", type=int, default=1, help="also time the float64 factor arm once")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
+    p.add_argument("--matrix-cache", default="", help="load the H^2 matrix from this .npz if it exists, "
+                   "else build and save it there (lets a profiler run skip the construction)")
     return p.parse_args()
 
 
@@ -143,8 +145,14 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
 
 def _problem(args, device):
     from h2gen import make_problem
+    from h2gen.problems import load_problem, save_problem
     over = {} if not args.n else {"n": args.n}
-    return make_problem(args.workload, device=device, **over)
+    if args.matrix_cache and os.path.exists(args.matrix_cache):
+        return load_problem(args.matrix_cache, device)
+    pb = make_problem(args.workload, device=device, **over)
+    if args.matrix_cache:
+        save_problem(pb, args.matrix_cache)
+    return pb
 
 
 def _rhs(n, nrhs, device):

@@ -147,7 +147,8 @@ class H2Matrix:
     def save(self, path: str) -> None:
         arrs = {k: getattr(self, k) for k in self.__dataclass_fields__ if k != "meta"}
         arrs = {k: (v.cpu().numpy() if torch.is_tensor(v) else np.asarray(v)) for k, v in arrs.items()}
-        np.savez(path, **arrs)
+        with open(path, "wb") as f:
+            np.savez(f, **arrs)
 
     @classmethod
     def load(cls, path: str) -> "H2Matrix":

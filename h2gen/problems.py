@@ -115,3 +115,22 @@ def make_problem(name: str, device="cpu", **over) -> Problem:
 def rhs(n: int, nrhs: int, seed: int = 0) -> np.ndarray:
     """Right-hand sides: N(0,1) entries, seeded (tree order = generation order)."""
     return P.standard_normal((n, nrhs), seed)
+
+
+def save_problem(pb: Problem, path: str) -> None:
+    """Write a built problem (matrix arrays + workload + norm) to an .npz file."""
+    import json
+    pb.A.save(path)
+    with open(path + ".json", "w") as f:
+        json.dump({"workload": pb.workload.__dict__, "norm_a": pb.norm_a, "stats": pb.stats}, f)
+
+
+def load_problem(path: str, device="cpu") -> Problem:
+    """Read a problem written by :func:`save_problem` (values moved to ``device``)."""
+    import json
+    with open(path + ".json") as f:
+        meta = json.load(f)
+    A = H2Matrix.load(path).to(device)
+    w = Workload(**meta["workload"])
+    A.meta = dict(workload=w.name, norm_a=meta["norm_a"])
+    return Problem(w, A, meta["norm_a"], 0.0, meta["stats"])
