@@ -180,11 +180,15 @@ H2_API void h2_factor_destroy(h2_factor* Z);
  * The solve runs in the factor's precision.  Errors: H2_ERR_ARG, H2_ERR_CUDA. */
 H2_API int h2_solve(const h2_factor* Z, int32_t nrhs, double* b, int64_t ldb, int32_t on_device);
 
-/* Iterative refinement in float64: x0 = solve(b); x_{k+1} = x_k + solve(b - A x_k)
- * until max over columns of ||b - A x|| / (norm_a ||x||) <= tol or maxit
- * corrections.  b, x: n x nrhs (device when on_device != 0).  *iters receives the
- * number of corrections, *berr the final backward error.  Returns
- * H2_ERR_NO_CONVERGENCE (x still written) if tol was not reached. */
+/* Iterative refinement in float64: x0 = solve(b), then corrections
+ * x_{k+1} = x_k + solve(b - A x_k); once a correction fails to halve the backward
+ * error (eps_lu * cond(A) near 1) the remaining corrections are restarted GMRES(30)
+ * cycles on A d = b - A x_k right-preconditioned by the factor (GMRES-based
+ * refinement).  Stops when max over columns of ||b - A x|| / (norm_a ||x||) <= tol or
+ * after maxit corrections (plain steps plus GMRES iterations).  b, x: n x nrhs (device
+ * when on_device != 0).  *iters receives the number of corrections, *berr the final
+ * backward error.  Returns H2_ERR_NO_CONVERGENCE (x still written) if tol was not
+ * reached. */
 H2_API int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs,
                     const double* b, int64_t ldb, double* x, int64_t ldx,
                     double tol, int32_t maxit, int32_t on_device,

@@ -296,43 +296,143 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
         const double* bd = b;
         double* xd = x;
         int64_t lb = ldb, lx = ldx;
+        const size_t vbytes = (size_t)n * nrhs * sizeof(double);
         if (!on_device) {
-            db.alloc(n * nrhs * sizeof(double), s);
-            dx.alloc(n * nrhs * sizeof(double), s);
+            db.alloc(vbytes, s);
+            dx.alloc(vbytes, s);
             H2_CUDA_CHECK(cudaMemcpy2DAsync(db.ptr, n * sizeof(double), b, ldb * sizeof(double),
                                             n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
             bd = db.as<double>();
             xd = dx.as<double>();
             lb = lx = n;
         }
-        dy.alloc(n * nrhs * sizeof(double), s);
-        dr.alloc(n * nrhs * sizeof(double), s);
+        dy.alloc(vbytes, s);
+        dr.alloc(vbytes, s);
         dn.alloc(2 * nrhs * sizeof(double), s);
         H2_CUDA_CHECK(cudaMemcpy2DAsync(xd, lx * sizeof(double), bd, lb * sizeof(double), n * sizeof(double),
                                         nrhs, cudaMemcpyDeviceToDevice, s));
         F.solve_dev(xd, nrhs, lx);
         const double nA = F.norm_a_;
-        std::vector<double> h(2 * nrhs);
-        int it = 0;
-        double be = INFINITY;
-        for (;;) {
+        std::vector<double> h(2 * nrhs), xnorm(nrhs);
+        // backward error of x; r = b - A x is left in dr
+        auto residual = [&]() -> double {
             matvec_dev(A->m, nrhs, xd, lx, dy.as<double>(), n, s);
             residual_dev(bd, lb, dy.as<double>(), n, dr.as<double>(), n, n, nrhs, s);
             colnorm2_dev(dr.as<double>(), n, n, nrhs, dn.as<double>(), s);
             colnorm2_dev(xd, lx, n, nrhs, dn.as<double>() + nrhs, s);
             H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
             H2_CUDA_CHECK(cudaStreamSynchronize(s));
-            be = 0;
+            double be = 0;
             for (int c = 0; c < nrhs; ++c) {
-                const double xn = std::sqrt(h[nrhs + c]);
-                const double e = xn > 0 ? std::sqrt(h[c]) / (nA * xn) : (h[c] > 0 ? INFINITY : 0.0);
+                xnorm[c] = std::sqrt(h[nrhs + c]);
+                const double e = xnorm[c] > 0 ? std::sqrt(h[c]) / (nA * xnorm[c]) : (h[c] > 0 ? INFINITY : 0.0);
                 be = std::max(be, e);
             }
             H2_REQUIRE(std::isfinite(be), H2_ERR_NONFINITE, "non-finite residual in refinement");
-            if (be <= tol || it >= maxit) break;
+            return be;
+        };
+        // One restarted-GMRES cycle on A d = r, right-preconditioned by the factor
+        // (A M^-1 u = r, d = M^-1 u), classical Gram-Schmidt applied twice; float64.
+        // Used once plain correction steps stop contracting (eps_lu * cond(A) near 1).
+        DevBuf Vb, hb, tb;
+        auto gmres_cycle = [&](int m, double target_rel) -> int {
+            Vb.alloc((size_t)(m + 1) * vbytes, s);
+            hb.alloc((size_t)(m + 1) * nrhs * sizeof(double), s);
+            tb.alloc(vbytes, s);
+            double* V = Vb.as<double>();
+            double* hd = hb.as<double>();
+            std::vector<double> beta(nrhs), sc(nrhs);
+            colnorm2_dev(dr.as<double>(), n, n, nrhs, dn.as<double>(), s);
+            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+            H2_CUDA_CHECK(cudaStreamSynchronize(s));
+            for (int c = 0; c < nrhs; ++c) {
+                beta[c] = std::sqrt(h[c]);
+                sc[c] = beta[c] > 0 ? 1.0 / beta[c] : 0.0;
+            }
+            H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+            scale_dev(dr.as<double>(), dn.as<double>(), n, nrhs, V, s);
+            std::vector<double> H((size_t)(m + 1) * m * nrhs, 0.0), g((size_t)(m + 1) * nrhs, 0.0),
+                cs((size_t)m * nrhs), sn((size_t)m * nrhs), hh((size_t)(m + 1) * nrhs), h2((size_t)(m + 1) * nrhs);
+            for (int c = 0; c < nrhs; ++c) g[c] = beta[c];
+            auto Hc = [&](int row, int col, int c) -> double& { return H[((size_t)col * (m + 1) + row) * nrhs + c]; };
+            int k = 0;
+            for (int j = 0; j < m; ++j) {
+                double* vj = V + (size_t)j * n * nrhs;
+                double* w = V + (size_t)(j + 1) * n * nrhs;
+                H2_CUDA_CHECK(cudaMemcpyAsync(tb.ptr, vj, vbytes, cudaMemcpyDeviceToDevice, s));
+                F.solve_dev(tb.as<double>(), nrhs, n);                       // M^-1 v_j
+                matvec_dev(A->m, nrhs, tb.as<double>(), n, w, n, s);          // A M^-1 v_j
+                for (int pass = 0; pass < 2; ++pass) {
+                    multidot_dev(V, w, j + 1, n, nrhs, hd, s);
+                    H2_CUDA_CHECK(cudaMemcpyAsync(h2.data(), hd, (size_t)(j + 1) * nrhs * sizeof(double),
+                                                  cudaMemcpyDeviceToHost, s));
+                    H2_CUDA_CHECK(cudaStreamSynchronize(s));
+                    for (size_t q = 0; q < (size_t)(j + 1) * nrhs; ++q) {
+                        if (pass == 0) hh[q] = h2[q]; else hh[q] += h2[q];
+                        h2[q] = -h2[q];
+                    }
+                    H2_CUDA_CHECK(cudaMemcpyAsync(hd, h2.data(), (size_t)(j + 1) * nrhs * sizeof(double),
+                                                  cudaMemcpyHostToDevice, s));
+                    combine_dev(V, hd, j + 1, n, nrhs, w, s);
+                }
+                colnorm2_dev(w, n, n, nrhs, dn.as<double>(), s);
+                H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+                H2_CUDA_CHECK(cudaStreamSynchronize(s));
+                bool done = true;
+                for (int c = 0; c < nrhs; ++c) {
+                    const double hn = std::sqrt(h[c]);
+                    sc[c] = hn > 0 ? 1.0 / hn : 0.0;
+                    for (int i = 0; i <= j; ++i) Hc(i, j, c) = hh[(size_t)i * nrhs + c];
+                    Hc(j + 1, j, c) = hn;
+                    for (int i = 0; i < j; ++i) {                            // previous rotations
+                        const double a0 = Hc(i, j, c), a1 = Hc(i + 1, j, c);
+                        Hc(i, j, c) = cs[(size_t)i * nrhs + c] * a0 + sn[(size_t)i * nrhs + c] * a1;
+                        Hc(i + 1, j, c) = -sn[(size_t)i * nrhs + c] * a0 + cs[(size_t)i * nrhs + c] * a1;
+                    }
+                    const double a0 = Hc(j, j, c), a1 = Hc(j + 1, j, c);
+                    const double rr = std::hypot(a0, a1);
+                    const double cj = rr > 0 ? a0 / rr : 1.0, sj = rr > 0 ? a1 / rr : 0.0;
+                    cs[(size_t)j * nrhs + c] = cj;
+                    sn[(size_t)j * nrhs + c] = sj;
+                    Hc(j, j, c) = rr;
+                    Hc(j + 1, j, c) = 0.0;
+                    g[(size_t)(j + 1) * nrhs + c] = -sj * g[(size_t)j * nrhs + c];
+                    g[(size_t)j * nrhs + c] = cj * g[(size_t)j * nrhs + c];
+                    if (std::fabs(g[(size_t)(j + 1) * nrhs + c]) > target_rel * nA * xnorm[c]) done = false;
+                }
+                H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+                scale_dev(w, dn.as<double>(), n, nrhs, w, s);
+                k = j + 1;
+                if (done) break;
+            }
+            // y = R^-1 g per column; u = V y; d = M^-1 u (left in dr)
+            std::vector<double> y((size_t)k * nrhs, 0.0);
+            for (int c = 0; c < nrhs; ++c)
+                for (int i = k - 1; i >= 0; --i) {
+                    double t = g[(size_t)i * nrhs + c];
+                    for (int q = i + 1; q < k; ++q) t -= Hc(i, q, c) * y[(size_t)q * nrhs + c];
+                    y[(size_t)i * nrhs + c] = Hc(i, i, c) != 0 ? t / Hc(i, i, c) : 0.0;
+                }
+            H2_CUDA_CHECK(cudaMemcpyAsync(hd, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            H2_CUDA_CHECK(cudaMemsetAsync(dr.ptr, 0, vbytes, s));
+            combine_dev(V, hd, k, n, nrhs, dr.as<double>(), s);
             F.solve_dev(dr.as<double>(), nrhs, n);
+            return k;
+        };
+        int it = 0;
+        double be = residual(), prev = INFINITY;
+        bool krylov = false;
+        while (be > tol && it < maxit) {
+            if (!krylov && be > 0.5 * prev) krylov = true;      // plain corrections stalled
+            prev = be;
+            if (!krylov) {
+                F.solve_dev(dr.as<double>(), nrhs, n);
+                ++it;
+            } else {
+                it += gmres_cycle(std::max(1, std::min(30, maxit - it)), 0.5 * tol);
+            }
             add_dev(xd, lx, dr.as<double>(), n, n, nrhs, s);
-            ++it;
+            be = residual();
         }
         if (!on_device)
             H2_CUDA_CHECK(cudaMemcpy2DAsync(x, ldx * sizeof(double), xd, n * sizeof(double), n * sizeof(double),

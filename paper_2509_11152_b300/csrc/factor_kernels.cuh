@@ -838,8 +838,8 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
         const int* __restrict__ c_box, const int* __restrict__ c_ablk, const int* __restrict__ c_kpos,
         const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn) {
     constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ T As[BK][BM + 1];
-    __shared__ T Bs[BK][BN + 1];
+    __shared__ T As[2][BK][BM + 1];
+    __shared__ T Bs[2][BK][BN + 1];
     const int tt = tile_tgt[blockIdx.x];
     const int mn = tile_mn[blockIdx.x];
     const int tb = tgt_blk[tt];
@@ -851,45 +851,74 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
     const int m0 = (mn >> 16) * BM, n0 = (mn & 0xffff) * BN;
     if (m0 >= m || n0 >= nn) return;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // this thread's load slots: A rows 4*(tid%16)+q of k-column tid/16; B k-rows 4*(tid%4)+q of column tid/4
+    const int la_k = tid >> 4, la_r = 4 * (tid & 15);
+    const int lb_c = tid >> 2, lb_k = 4 * (tid & 3);
     T acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    for (int c = tgt_ptr[tt]; c < tgt_ptr[tt + 1]; ++c) {
-        const int i = c_box[c];
-        const int ri = a.n[i] - a.kt[i];
-        if (ri <= 0) continue;
-        const T* A = a.blk + a.blk_off[c_ablk[c]] + row_lo;           // m x ri, ld nj
-        const int pos = a.nb_ptr[i] + c_kpos[c];
-        const T* B = a.WU + a.WU_off[i] + (int64_t)a.nbofs[pos] * ri;  // ri x nn, ld ri
-        for (int k0 = 0; k0 < ri; k0 += BK) {
-            for (int x = tid; x < BK * BM; x += 256) {
-                const int kk = x / BM, rr = x % BM;
-                const int gr = m0 + rr, gk = k0 + kk;
-                As[kk][rr] = (gr < m && gk < ri) ? A[gr + (int64_t)gk * nj] : T(0);
-            }
-            for (int x = tid; x < BK * BN; x += 256) {
-                const int kk = x % BK, cc = x / BK;
-                const int gc = n0 + cc, gk = k0 + kk;
-                Bs[kk][cc] = (gc < nn && gk < ri) ? B[gk + (int64_t)gc * ri] : T(0);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                T av[4], bv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) av[u] = As[kk][tx + 16 * u];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][ty + 16 * v];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
-            }
-            __syncthreads();
+    // K-steps run over (contributor, 16-wide slice); the next step's operands are
+    // fetched into registers while the current step computes from shared memory
+    int c = tgt_ptr[tt];
+    const int cend = tgt_ptr[tt + 1];
+    int k0 = 0, ri = 0;
+    const T* A = nullptr;
+    const T* B = nullptr;
+    auto advance = [&](bool first) -> bool {        // move (c, k0) to the next valid step
+        if (!first) {
+            k0 += BK;
+            if (k0 < ri) return true;
+            ++c;
         }
-    }
+        for (; c < cend; ++c) {
+            const int i = c_box[c];
+            ri = a.n[i] - a.kt[i];
+            if (ri <= 0) continue;
+            A = a.blk + a.blk_off[c_ablk[c]] + row_lo;                        // m x ri, ld nj
+            B = a.WU + a.WU_off[i] + (int64_t)a.nbofs[a.nb_ptr[i] + c_kpos[c]] * ri;   // ri x nn, ld ri
+            k0 = 0;
+            return true;
+        }
+        return false;
+    };
+    T ra[4], rb[4];
+    auto fetch = [&]() {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gr = m0 + la_r + q, gk = k0 + la_k;
+            ra[q] = (gr < m && gk < ri) ? A[gr + (int64_t)gk * nj] : T(0);
+            const int gc = n0 + lb_c, gk2 = k0 + lb_k + q;
+            rb[q] = (gc < nn && gk2 < ri) ? B[gk2 + (int64_t)gc * ri] : T(0);
+        }
+    };
+    bool have = advance(true);
+    if (have) fetch();
+    int buf = 0;
+    while (have) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            As[buf][la_k][la_r + q] = ra[q];
+            Bs[buf][lb_k + q][lb_c] = rb[q];
+        }
+        __syncthreads();
+        have = advance(false);
+        if (have) fetch();                           // overlaps with the products below
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = As[buf][kk][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) bv[v] = Bs[buf][kk][ty + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+        }
+        buf ^= 1;                                    // the other buffer is free: its last
+    }                                                // readers passed this step's barrier
     T* Cm = a.blk + a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
 #pragma unroll
     for (int u = 0; u < 4; ++u)

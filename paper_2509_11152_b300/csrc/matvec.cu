@@ -153,6 +153,61 @@ __global__ void v_colnorm2(const double* __restrict__ v, int64_t ldv, int64_t n,
     }
 }
 
+// h[i*nrhs + c] = <V_i[:, c], w[:, c]> for i < m (V_i = V + i * n * nrhs, ld n); one block
+// per (i, c)
+__global__ void v_multidot(const double* __restrict__ V, const double* __restrict__ w, int64_t n, int nrhs,
+                           double* __restrict__ h) {
+    __shared__ double red[32];
+    const int i = blockIdx.x, c = blockIdx.y;
+    const double* vi = V + ((int64_t)i * nrhs + c) * n;
+    const double* wc = w + (int64_t)c * n;
+    double acc = 0;
+    for (int64_t a = threadIdx.x; a < n; a += blockDim.x) acc += vi[a] * wc[a];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        h[(int64_t)i * nrhs + c] = t;
+    }
+}
+
+// w[:, c] += sum_{i < m} coef[i*nrhs + c] V_i[:, c]
+__global__ void v_combine(const double* __restrict__ V, const double* __restrict__ coef, int m, int64_t n,
+                          int nrhs, double* __restrict__ w) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nrhs) return;
+    const int64_t a = e % n;
+    const int c = (int)(e / n);
+    double acc = w[e];
+    for (int i = 0; i < m; ++i) acc += coef[(int64_t)i * nrhs + c] * V[((int64_t)i * nrhs + c) * n + a];
+    w[e] = acc;
+}
+
+// y[:, c] = s[c] * x[:, c]
+__global__ void v_scale(const double* __restrict__ x, const double* __restrict__ sc, int64_t n, int nrhs,
+                        double* __restrict__ y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nrhs) return;
+    y[e] = sc[e / n] * x[e];
+}
+
+void multidot_dev(const double* V, const double* w, int m, int64_t n, int nrhs, double* h, cudaStream_t s) {
+    v_multidot<<<dim3(m, nrhs), 256, 0, s>>>(V, w, n, nrhs, h);
+    count_launch();
+}
+
+void combine_dev(const double* V, const double* coef, int m, int64_t n, int nrhs, double* w, cudaStream_t s) {
+    v_combine<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(V, coef, m, n, nrhs, w);
+    count_launch();
+}
+
+void scale_dev(const double* x, const double* sc, int64_t n, int nrhs, double* y, cudaStream_t s) {
+    v_scale<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(x, sc, n, nrhs, y);
+    count_launch();
+}
+
 void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, double* r, int64_t ldr,
                   int64_t n, int nrhs, cudaStream_t s) {
     const unsigned g = (unsigned)((n * nrhs + 255) / 256);

@@ -16,4 +16,10 @@ void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, do
 void add_dev(double* x, int64_t ldx, const double* d, int64_t ldd, int64_t n, int nrhs, cudaStream_t s);
 void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s);
 
+// GMRES helpers on n x nrhs column blocks stored contiguously (ld n):
+// h[i*nrhs+c] = <V_i[:,c], w[:,c]>;  w[:,c] += sum_i coef[i*nrhs+c] V_i[:,c];  y = diag(sc) x
+void multidot_dev(const double* V, const double* w, int m, int64_t n, int nrhs, double* h, cudaStream_t s);
+void combine_dev(const double* V, const double* coef, int m, int64_t n, int nrhs, double* w, cudaStream_t s);
+void scale_dev(const double* x, const double* sc, int64_t n, int nrhs, double* y, cudaStream_t s);
+
 }  // namespace h2rs

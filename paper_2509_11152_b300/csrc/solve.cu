@@ -92,32 +92,58 @@ __global__ void s_fwd_l(const int* __restrict__ tbox, const int* __restrict__ tp
     }
 }
 
-// backward U update of a colour: x_{i_R} -= sum_k W_U^i[k] x_k (box owned)
-template <class T>
-__global__ void s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n, const int* __restrict__ kt,
-                        const int* __restrict__ nb_ptr, const int* __restrict__ nb_col,
-                        const int* __restrict__ nbofs, const T* __restrict__ WU,
-                        const int64_t* __restrict__ WU_off, const int64_t* __restrict__ voff,
-                        T* __restrict__ x, int nrhs) {
+// backward U update of a colour: x_{i_R} -= sum_k W_U^i[k] x_k (box owned).  One block
+// per box; warp w takes every 8th column of each neighbour segment of W_U^i, lane l
+// accumulates rows l + 32u in registers (RU per lane), then the 8 warps are summed.
+template <class T, int RU>
+__global__ void __launch_bounds__(256)
+s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n, const int* __restrict__ kt,
+        const int* __restrict__ nb_ptr, const int* __restrict__ nb_col,
+        const int* __restrict__ nbofs, const T* __restrict__ WU,
+        const int64_t* __restrict__ WU_off, const int64_t* __restrict__ voff,
+        T* __restrict__ x, int nrhs) {
     const int i = boxes[blockIdx.x];
     const int ni = n[i], ri = ni - kt[i];
     if (ri <= 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* red = reinterpret_cast<T*>(sm_raw);                 // 8 x ri
     T* xi = x + voff[i] * nrhs;
     const T* Wi = WU + WU_off[i];
-    for (int e = threadIdx.x; e < ri * nrhs; e += blockDim.x) {
-        const int a = e % ri, c = e / ri;
-        T acc = 0;
+    for (int c = 0; c < nrhs; ++c) {
+        T acc[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) acc[u] = T(0);
         for (int p = nb_ptr[i]; p < nb_ptr[i + 1]; ++p) {
-            const int j = nb_col[p];
+            const int jb = nb_col[p];
             const int o = nbofs[p];
             const T* xs;
-            int w;
-            if (j == i) { xs = xi + (int64_t)c * ni + ri; w = kt[i]; }
-            else { xs = x + voff[j] * nrhs + (int64_t)c * n[j]; w = n[j]; }
-            const T* Wc = Wi + a + (int64_t)o * ri;
-            for (int b = 0; b < w; ++b) acc += Wc[(int64_t)b * ri] * xs[b];
+            int wdt;
+            if (jb == i) { xs = xi + (int64_t)c * ni + ri; wdt = kt[i]; }
+            else { xs = x + voff[jb] * nrhs + (int64_t)c * n[jb]; wdt = n[jb]; }
+            for (int b = w; b < wdt; b += 8) {
+                const T xb = xs[b];
+                const T* col = Wi + (int64_t)(o + b) * ri;
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int aa = lane + 32 * u;
+                    if (aa < ri) acc[u] += col[aa] * xb;
+                }
+            }
         }
-        xi[a + (int64_t)c * ni] -= acc;
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int aa = lane + 32 * u;
+            if (aa < ri) red[w * ri + aa] = acc[u];
+        }
+        __syncthreads();
+        for (int aa = threadIdx.x; aa < ri; aa += blockDim.x) {
+            T sacc = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sacc += red[q * ri + aa];
+            xi[aa + (int64_t)c * ni] -= sacc;
+        }
+        __syncthreads();
     }
 }
 
@@ -216,6 +242,18 @@ static void allow_smem(K kern) {
     H2_CUDA_CHECK(cudaFuncGetAttributes(&fa, kern));
     H2_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        optin - (int)fa.sharedSizeBytes));
+}
+
+template <class T>
+static void launch_bwd_u(int nmax, int nb, cudaStream_t s, const int* boxes, const int* n, const int* kt,
+                         const int* nb_ptr, const int* nb_col, const int* nbofs, const T* WU,
+                         const int64_t* WU_off, const int64_t* voff, T* x, int nrhs) {
+    const int smem = 8 * nmax * (int)sizeof(T);
+    if (nmax <= 32) s_bwd_u<T, 1><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else if (nmax <= 64) s_bwd_u<T, 2><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else if (nmax <= 128) s_bwd_u<T, 4><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else if (nmax <= 256) s_bwd_u<T, 8><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the solve"};
 }
 
 template <class T>
@@ -319,10 +357,10 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         const int qsm = nmax * nrhs * (int)sizeof(T);
         for (int c = S.ncolour - 1; c >= 0; --c) {
             const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;
-            s_bwd_u<T><<<nb, 256, 0, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.d_kt.as<int>(),
-                                          L.d_nb_ptr.as<int>(), L.d_nb_col.as<int>(), L.d_nbofs.as<int>(),
-                                          L.WU.as<T>(), L.d_WU_off.as<int64_t>(), L.d_voff.as<int64_t>(),
-                                          vec[a].as<T>(), nrhs);
+            launch_bwd_u<T>(nmax, nb, s, d_boxes.as<int>() + b0, L.d_n.as<int>(), L.d_kt.as<int>(),
+                            L.d_nb_ptr.as<int>(), L.d_nb_col.as<int>(), L.d_nbofs.as<int>(),
+                            L.WU.as<T>(), L.d_WU_off.as<int64_t>(), L.d_voff.as<int64_t>(),
+                            vec[a].as<T>(), nrhs);
             count_launch();
             s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
                                               L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),

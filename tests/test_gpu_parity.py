@@ -181,3 +181,20 @@ def test_singular_matrix_reports_error_and_context_survives(h):
     b = rhs(pb.A.n, 1, seed=8)
     _, _, x = _gpu_solve(h, pb, b, 1e-8, h.H2_PREC_FP64)
     assert np.isfinite(x).all()
+
+
+def test_gmres_refinement_when_plain_corrections_stall(h):
+    """A loose eps_lu on an ill-conditioned Gaussian-kernel matrix: plain corrections
+    stop contracting and the refinement continues with preconditioned GMRES cycles;
+    the backward error is checked with the oracle's own matvec."""
+    pb = problem("gauss3d", n=4096, leaf=32)
+    A = pb.A.numpy()
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, 1e-2, pb.norm_a, h.H2_PREC_FP32)
+    b = rhs(A.n, 2, seed=9)
+    bt = h.colmajor(torch.from_numpy(b).cuda())
+    xt = h.colmajor(torch.zeros_like(bt))
+    it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 60)
+    assert ok and berr <= BERR_TOL and it > 3
+    nw, _ = dense.backward_error(A, xt.cpu().numpy(), b, pb.norm_a)
+    assert nw <= BERR_TOL
