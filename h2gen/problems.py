@@ -112,6 +112,23 @@ def make_problem(name: str, device="cpu", **over) -> Problem:
     return Problem(w, A, norm_a, t1 - t0, stats)
 
 
+def uneven_sizes(nsys: int = 64, nmin: int = 2048, nmax: int = 131072) -> list[int]:
+    """System sizes of the uneven batch: N_s = round(exp(U(ln nmin, ln nmax))), the
+    uniform draw seeded by s."""
+    out = []
+    for s in range(nsys):
+        u = np.random.default_rng(s).uniform(math.log(nmin), math.log(nmax))
+        out.append(int(round(math.exp(u))))
+    return out
+
+
+def make_batch(name: str = "gauss3d", nsys: int = 64, nmin: int = 2048, nmax: int = 131072,
+               device="cpu", **over) -> list[Problem]:
+    """The uneven batch: system s is workload ``name`` with N_s points drawn with seed s."""
+    return [make_problem(name, device=device, n=n, seed=s, **over)
+            for s, n in enumerate(uneven_sizes(nsys, nmin, nmax))]
+
+
 def rhs(n: int, nrhs: int, seed: int = 0) -> np.ndarray:
     """Right-hand sides: N(0,1) entries, seeded (tree order = generation order)."""
     return P.standard_normal((n, nrhs), seed)

@@ -17,6 +17,8 @@
  *  - Dense blocks are column-major float64.
  *  - Nodes of the complete binary cluster tree use heap numbering: level l holds
  *    the ids 2^l-1 .. 2^(l+1)-2, node g has children 2g+1 and 2g+2.
+ *  - A batch of independent matrices (h2_matrix_create_batch) is one h2_matrix whose
+ *    vectors are the systems' vectors stacked in the caller's order.
  *  - "device" pointers are CUDA device pointers of the current device; the
  *    library runs every kernel on the stream given in the options / descriptor
  *    (NULL = the legacy default stream).
@@ -115,6 +117,20 @@ typedef struct h2_factor h2_factor;   /* opaque: owns all device memory of Z    
 H2_API int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out);
 H2_API void h2_matrix_destroy(h2_matrix* A);
 
+/* A batch of nsys independent symmetric H^2 matrices (descs[0..nsys-1], each as for
+ * h2_matrix_create, of any sizes and depths) as one block-diagonal h2_matrix.  The
+ * trees are aligned by height above the leaves, so every level of the factorisation
+ * and of the solve treats the boxes of all systems in the same kernel launches
+ * (Sec. 2.2 applied to a forest; the paper treats one matrix).  Vectors are the
+ * systems' tree-order vectors stacked in the order of descs (system s starts at row
+ * sum_{q<s} descs[q].n).  The values are copied with descs[s].values_on_device; every
+ * copy runs on descs[0].stream.  Errors as h2_matrix_create. */
+H2_API int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_matrix** out);
+
+/* Number of systems of A and their row offsets (sys_offset: nsys+1 entries, last = n);
+ * either output may be NULL.  Errors: H2_ERR_ARG. */
+H2_API int h2_matrix_batch_info(const h2_matrix* A, int32_t* nsys, int64_t* sys_offset);
+
 /* y = A x in float64 (the H^2 matrix-vector product: upsweep, couplings, downsweep,
  * near field).  x: n x nrhs (ldx >= n), y: n x nrhs (ldy >= n); both device pointers
  * when on_device != 0, else host pointers (copied in and out).  Errors: H2_ERR_ARG,
@@ -145,6 +161,9 @@ typedef struct {
     int32_t precision;          /* H2_PREC_*                                           */
     int32_t flags;              /* H2_FLAG_* bits, 0 by default                        */
     void* stream;               /* cudaStream_t for every kernel of this factor        */
+    const double* sys_norm_a;   /* batch: ||A_s||_2 of every system (host, nsys values,
+                                   copied); NULL = norm_a for all.  Each system's
+                                   eps_fill and backward error use its own norm       */
 } h2_factor_opts;
 
 /* h2_factor_opts.flags: time every factorisation kernel launch with CUDA events
@@ -184,8 +203,9 @@ H2_API int h2_solve(const h2_factor* Z, int32_t nrhs, double* b, int64_t ldb, in
  * x_{k+1} = x_k + solve(b - A x_k); once a correction fails to halve the backward
  * error (eps_lu * cond(A) near 1) the remaining corrections are restarted GMRES(30)
  * cycles on A d = b - A x_k right-preconditioned by the factor (GMRES-based
- * refinement).  Stops when max over columns of ||b - A x|| / (norm_a ||x||) <= tol or
- * after maxit corrections (plain steps plus GMRES iterations).  b, x: n x nrhs (device
+ * refinement).  Stops when the max over columns (and, for a batch, over systems s) of
+ * ||b_s - A_s x_s|| / (||A_s|| ||x_s||) <= tol or after maxit corrections (plain steps
+ * plus GMRES iterations).  b, x: n x nrhs (device
  * when on_device != 0).  *iters receives the number of corrections, *berr the final
  * backward error.  Returns H2_ERR_NO_CONVERGENCE (x still written) if tol was not
  * reached. */
@@ -230,9 +250,18 @@ H2_API int h2_layout_get(const h2_factor* Z, int32_t level, int64_t* sizes, int6
  * `level` (0 = leaves), the number of boxes and of merged blocks, the greedy colour
  * of every box and the merged block CSR with kinds, exactly as h2_factor_create
  * will use them.  Only the index arrays of the descriptor are read.  Arrays may be
- * NULL (counts only).  Errors: H2_ERR_ARG. */
+ * NULL (counts only).  Errors: H2_ERR_ARG (also for a level that is not skeletonised). */
 H2_API int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
                   int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind);
+
+/* The same for a batch (as h2_matrix_create_batch): forest level `level` counted from
+ * the leaves, up to and including the last level, which holds dense top matrices only.
+ * Per box additionally: state (0 above its system's top, 1 skeletonised at this level,
+ * 2 part of its system's dense top matrix; colour is -1 unless 1) and system (index
+ * into descs).  Boxes of one system are contiguous and in their tree's order. */
+H2_API int h2_plan_query_batch(int32_t nsys, const h2_matrix_desc* descs, int32_t level, int64_t* nbox,
+                               int64_t* nblk, int32_t* colour, int64_t* row_ptr, int64_t* col,
+                               int32_t* kind, int32_t* state, int32_t* system);
 
 /* Number of CUDA kernels this library has launched in the process so far (all
  * entry points; for counting launches inside a timed region). */

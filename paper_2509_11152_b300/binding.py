@@ -40,7 +40,7 @@ class h2_matrix_desc(ctypes.Structure):
 
 class h2_factor_opts(ctypes.Structure):
     _fields_ = [("eps_lu", ctypes.c_double), ("norm_a", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p), ("sys_norm_a", _dp)]
 
 
 class h2_factor_stats(ctypes.Structure):
@@ -60,6 +60,9 @@ H2_FLAG_TIME_KERNELS = 1
 _SIGS = [
     ("h2_matrix_create", ctypes.c_int, [ctypes.POINTER(h2_matrix_desc), ctypes.POINTER(ctypes.c_void_p)]),
     ("h2_matrix_destroy", None, [ctypes.c_void_p]),
+    ("h2_matrix_create_batch", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(h2_matrix_desc),
+                                              ctypes.POINTER(ctypes.c_void_p)]),
+    ("h2_matrix_batch_info", ctypes.c_int, [ctypes.c_void_p, _i32p, _i64p]),
     ("h2_matvec", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
     ("h2_matvec_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
@@ -78,6 +81,8 @@ _SIGS = [
                                      _i32p, _i64p]),
     ("h2_plan_query", ctypes.c_int, [ctypes.POINTER(h2_matrix_desc), ctypes.c_int32, _i64p, _i64p, _i32p,
                                      _i64p, _i64p, _i32p]),
+    ("h2_plan_query_batch", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(h2_matrix_desc), ctypes.c_int32,
+                                           _i64p, _i64p, _i32p, _i64p, _i64p, _i32p, _i32p, _i32p]),
     ("h2_kernel_launch_count", ctypes.c_int64, []),
     ("h2_last_error", ctypes.c_char_p, []),
     ("h2_version", ctypes.c_char_p, []),
@@ -205,11 +210,38 @@ def h2_matrix_create(A, stream=None) -> Matrix:
     return Matrix(h, int(A.n))
 
 
-def h2_factor_create(M: Matrix, eps_lu: float, norm_a: float, precision: int = H2_PREC_FP64,
+def h2_matrix_create_batch(As, stream=None) -> Matrix:
+    """One block-diagonal matrix of the independent H^2 matrices ``As`` (vectors are
+    the systems' vectors stacked in this order)."""
+    descs, keeps = zip(*[make_desc(A, stream) for A in As])
+    arr = (h2_matrix_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(lib().h2_matrix_create_batch(len(descs), arr, ctypes.byref(h)))
+    del keeps
+    return Matrix(h, int(sum(int(A.n) for A in As)))
+
+
+def h2_matrix_batch_info(M: Matrix) -> np.ndarray:
+    """Row offsets of the systems of ``M`` (nsys + 1 entries)."""
+    ns = ctypes.c_int32()
+    _check(lib().h2_matrix_batch_info(M.handle, ctypes.byref(ns), None))
+    off = np.zeros(ns.value + 1, np.int64)
+    _check(lib().h2_matrix_batch_info(M.handle, None, _ptr(off, ctypes.c_int64)))
+    return off
+
+
+def h2_factor_create(M: Matrix, eps_lu: float, norm_a, precision: int = H2_PREC_FP64,
                      stream=None, flags: int = 0) -> Factor:
+    """``norm_a``: ||A||_2, or for a batch one norm per system (a sequence)."""
     o = h2_factor_opts()
     o.eps_lu = float(eps_lu)
-    o.norm_a = float(norm_a)
+    keep = None
+    if np.ndim(norm_a) == 0:
+        o.norm_a = float(norm_a)
+    else:
+        keep = np.ascontiguousarray(np.asarray(norm_a, dtype=np.float64))
+        o.norm_a = float(keep.max())
+        o.sys_norm_a = _ptr(keep, ctypes.c_double)
     o.precision = int(precision)
     o.flags = int(flags)
     o.stream = ctypes.c_void_p(stream) if stream else None
@@ -302,6 +334,26 @@ def h2_plan_query(A, level: int) -> dict:
                                _ptr(out["row_ptr"], ctypes.c_int64), _ptr(out["col"], ctypes.c_int64),
                                _ptr(out["kind"], ctypes.c_int32)))
     del keep
+    return out
+
+
+def h2_plan_query_batch(As, level: int) -> dict:
+    """Host-only: forest level ``level`` (0 = leaves) of the batch ``As`` as planned by
+    the library, with each box's state and system."""
+    descs, keeps = zip(*[make_desc(A) for A in As])
+    arr = (h2_matrix_desc * len(descs))(*descs)
+    nbox = ctypes.c_int64()
+    nblk = ctypes.c_int64()
+    _check(lib().h2_plan_query_batch(len(descs), arr, level, ctypes.byref(nbox), ctypes.byref(nblk),
+                                     None, None, None, None, None, None))
+    nb, nk = nbox.value, nblk.value
+    out = dict(colour=np.zeros(nb, np.int32), row_ptr=np.zeros(nb + 1, np.int64), col=np.zeros(nk, np.int64),
+               kind=np.zeros(nk, np.int32), state=np.zeros(nb, np.int32), system=np.zeros(nb, np.int32))
+    _check(lib().h2_plan_query_batch(len(descs), arr, level, None, None, _ptr(out["colour"], ctypes.c_int32),
+                                     _ptr(out["row_ptr"], ctypes.c_int64), _ptr(out["col"], ctypes.c_int64),
+                                     _ptr(out["kind"], ctypes.c_int32), _ptr(out["state"], ctypes.c_int32),
+                                     _ptr(out["system"], ctypes.c_int32)))
+    del keeps
     return out
 
 

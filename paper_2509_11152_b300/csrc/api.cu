@@ -80,74 +80,6 @@ static int guard(F&& f) {
 }
 
 template <class T>
-static std::vector<T> host_copy(const T* p, int64_t n, const char* what) {
-    H2_REQUIRE(n >= 0, H2_ERR_ARG, std::string("negative length for ") + what);
-    H2_REQUIRE(n == 0 || p != nullptr, H2_ERR_ARG, std::string("null array ") + what);
-    return std::vector<T>(p, p + n);
-}
-
-// index arrays -> host structure, with consistency checks
-static void read_structure(const h2_matrix_desc* d, HostStructure& H) {
-    H2_REQUIRE(d != nullptr, H2_ERR_ARG, "null descriptor");
-    H2_REQUIRE(d->n > 0 && d->depth >= 0 && d->depth < 30, H2_ERR_ARG, "bad n or depth");
-    H.n = d->n;
-    H.d = d->depth;
-    H.nnodes = (int64_t(1) << (H.d + 1)) - 1;
-    const int64_t nn = H.nnodes, nleaf = int64_t(1) << H.d, first_leaf = nleaf - 1;
-    H.node_start = host_copy(d->node_start, nn, "node_start");
-    H.node_size = host_copy(d->node_size, nn, "node_size");
-    H.rank = host_copy(d->rank, nn, "rank");
-    H.U_off = host_copy(d->U_off, nleaf + 1, "U_off");
-    H.E_off = host_copy(d->E_off, nn + 1, "E_off");
-    H.adm_ptr = host_copy(d->adm_ptr, nn + 1, "adm_ptr");
-    H.inad_ptr = host_copy(d->inad_ptr, nn + 1, "inad_ptr");
-    H2_REQUIRE(H.adm_ptr[0] == 0 && H.inad_ptr[0] == 0, H2_ERR_ARG, "CSR must start at 0");
-    H.adm_col = host_copy(d->adm_col, H.adm_ptr[nn], "adm_col");
-    H.S_off = host_copy(d->S_off, H.adm_ptr[nn] + 1, "S_off");
-    H.inad_col = host_copy(d->inad_col, H.inad_ptr[nn], "inad_col");
-    const int64_t nnear = H.inad_ptr[nn] - H.inad_ptr[first_leaf];
-    H.D_off = host_copy(d->D_off, nnear + 1, "D_off");
-    H2_REQUIRE(H.node_size[0] == H.n && H.node_start[0] == 0, H2_ERR_ARG, "root must cover 0..n");
-    for (int64_t g = 0; g < nn - nleaf; ++g) {
-        const int64_t c1 = 2 * g + 1, c2 = 2 * g + 2;
-        H2_REQUIRE(H.node_size[c1] + H.node_size[c2] == H.node_size[g] &&
-                       H.node_start[c1] == H.node_start[g] &&
-                       H.node_start[c2] == H.node_start[g] + H.node_size[c1],
-                   H2_ERR_ARG, "children must partition their parent");
-    }
-    for (int64_t i = 0; i < nleaf; ++i) {
-        const int64_t g = first_leaf + i;
-        H2_REQUIRE(H.rank[g] >= 0 && H.rank[g] <= H.node_size[g], H2_ERR_ARG, "leaf rank > size");
-        H2_REQUIRE(H.U_off[i + 1] - H.U_off[i] == H.node_size[g] * H.rank[g], H2_ERR_ARG, "U_off size");
-    }
-    for (int64_t g = 1; g < nn; ++g)
-        H2_REQUIRE(H.E_off[g + 1] - H.E_off[g] == H.rank[g] * H.rank[(g - 1) / 2], H2_ERR_ARG,
-                   "E_off size");
-    for (int64_t g = 0; g < nn; ++g) {
-        const int l = 63 - __builtin_clzll((unsigned long long)(g + 1));
-        const int64_t lf = (int64_t(1) << l) - 1, ll = (int64_t(1) << (l + 1)) - 1;
-        for (int64_t e = H.adm_ptr[g]; e < H.adm_ptr[g + 1]; ++e) {
-            const int64_t t = H.adm_col[e];
-            H2_REQUIRE(t >= lf && t < ll, H2_ERR_ARG, "admissible pair across levels");
-            H2_REQUIRE(H.S_off[e + 1] - H.S_off[e] == H.rank[g] * H.rank[t], H2_ERR_ARG, "S_off size");
-        }
-        bool self = false;
-        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
-            const int64_t t = H.inad_col[e];
-            H2_REQUIRE(t >= lf && t < ll, H2_ERR_ARG, "inadmissible pair across levels");
-            self |= t == g;
-            if (e > H.inad_ptr[g]) H2_REQUIRE(t > H.inad_col[e - 1], H2_ERR_ARG, "inad_col not sorted");
-            if (g >= first_leaf) {
-                const int64_t j = e - H.inad_ptr[first_leaf];
-                H2_REQUIRE(H.D_off[j + 1] - H.D_off[j] == H.node_size[g] * H.node_size[t], H2_ERR_ARG,
-                           "D_off size");
-            }
-        }
-        H2_REQUIRE(self, H2_ERR_ARG, "every node must be in its own near field");
-    }
-}
-
-template <class T>
 static void upload_values(DevBuf& b, const T* p, int64_t n, bool on_dev, cudaStream_t s) {
     b.alloc(std::max<int64_t>(1, n) * sizeof(T), s);
     if (n > 0)
@@ -165,27 +97,46 @@ const char* h2_last_error(void) { return g_err.c_str(); }
 int64_t h2_kernel_launch_count(void) { return g_launches.load(); }
 const char* h2_version(void) { return "h2rs 0.1 (sm_103a)"; }
 
-int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out) {
+int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_matrix** out) {
     if (!out) { set_error("null output pointer"); return H2_ERR_ARG; }
     *out = nullptr;
     h2_matrix* A = nullptr;
     int rc = guard([&] {
+        H2_REQUIRE(nsys >= 1 && descs != nullptr, H2_ERR_ARG, "need at least one descriptor");
         keep_pool_memory();
         A = new h2_matrix();
         MatrixObj& M = A->m;
-        read_structure(desc, M.H);
-        M.stream = static_cast<cudaStream_t>(desc->stream);
+        std::vector<HostStructure> parts(nsys);
+        for (int z = 0; z < nsys; ++z) {
+            read_structure(&descs[z], parts[z]);
+            const HostStructure& p = parts[z];
+            const h2_matrix_desc& d = descs[z];
+            H2_REQUIRE((d.U || p.U_off.back() == 0) && (d.E || p.E_off.back() == 0) &&
+                           (d.S || p.S_off.back() == 0) && (d.D || p.D_off.back() == 0),
+                       H2_ERR_ARG, "null value array");
+        }
+        std::vector<int> order;
+        ForestValues fv;
+        merge_forest(parts, M.H, order, fv);
+        parts.clear();
+        M.stream = static_cast<cudaStream_t>(descs[0].stream);
         cudaStream_t s = M.stream;
         const HostStructure& H = M.H;
-        const int64_t nn = H.nnodes, nleaf = int64_t(1) << H.d;
-        const bool od = desc->values_on_device != 0;
-        H2_REQUIRE((desc->U || H.U_off[nleaf] == 0) && (desc->E || H.E_off[nn] == 0) &&
-                       (desc->S || H.S_off.back() == 0) && (desc->D || H.D_off.back() == 0),
-                   H2_ERR_ARG, "null value array");
-        upload_values(M.U, desc->U, H.U_off[nleaf], od, s);
-        upload_values(M.E, desc->E, H.E_off[nn], od, s);
-        upload_values(M.S, desc->S, H.S_off.back(), od, s);
-        upload_values(M.D, desc->D, H.D_off.back(), od, s);
+        const int64_t nn = H.nnodes, nleaf = H.lev_cnt[H.d];
+        auto place = [&](DevBuf& b, int64_t total, const std::vector<ValueChunk>& ch, auto member) {
+            b.alloc(std::max<int64_t>(1, total) * sizeof(double), s);
+            for (const ValueChunk& c : ch) {
+                const h2_matrix_desc& d = descs[c.sys];
+                const double* src = d.*member;
+                H2_CUDA_CHECK(cudaMemcpyAsync(b.as<double>() + c.dst, src + c.src, c.cnt * sizeof(double),
+                                              d.values_on_device ? cudaMemcpyDeviceToDevice
+                                                                 : cudaMemcpyHostToDevice, s));
+            }
+        };
+        place(M.U, H.U_off[nleaf], fv.U, &h2_matrix_desc::U);
+        place(M.E, H.E_off[nn], fv.E, &h2_matrix_desc::E);
+        place(M.S, H.S_off.back(), fv.S, &h2_matrix_desc::S);
+        place(M.D, H.D_off.back(), fv.D, &h2_matrix_desc::D);
         upload(M.d_node_start, H.node_start, s);
         upload(M.d_node_size, H.node_size, s);
         upload(M.d_rank, H.rank, s);
@@ -197,6 +148,12 @@ int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out) {
         upload(M.d_adm_col, H.adm_col, s);
         upload(M.d_inad_ptr, H.inad_ptr, s);
         upload(M.d_inad_col, H.inad_col, s);
+        upload(M.d_parent, H.parent, s);
+        std::vector<int64_t> child0(nn, -1);
+        for (int l = 0; l < H.d; ++l)
+            for (int64_t i = 0; i < H.lev_cnt[l]; ++i) child0[H.lev_first[l] + i] = H.lev_first[l + 1] + 2 * i;
+        upload(M.d_child0, child0, s);
+        upload(M.d_sys_voff, H.sys_voff, s);
         M.coef_off.assign(nn + 1, 0);
         for (int64_t g = 0; g < nn; ++g) M.coef_off[g + 1] = M.coef_off[g] + H.rank[g];
         upload(M.d_coef_off, M.coef_off, s);
@@ -205,6 +162,23 @@ int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out) {
     });
     if (rc != H2_OK) { delete A; return rc; }
     *out = A;
+    return H2_OK;
+}
+
+int h2_matrix_create(const h2_matrix_desc* desc, h2_matrix** out) {
+    if (!desc) {
+        if (out) *out = nullptr;
+        set_error("null descriptor");
+        return H2_ERR_ARG;
+    }
+    return h2_matrix_create_batch(1, desc, out);
+}
+
+int h2_matrix_batch_info(const h2_matrix* A, int32_t* nsys, int64_t* sys_offset) {
+    if (!A) { set_error("null matrix"); return H2_ERR_ARG; }
+    const HostStructure& H = A->m.H;
+    if (nsys) *nsys = H.nsys;
+    if (sys_offset) for (int z = 0; z <= H.nsys; ++z) sys_offset[z] = H.sys_voff[z];
     return H2_OK;
 }
 
@@ -241,7 +215,8 @@ int h2_factor_create(const h2_matrix* A, const h2_factor_opts* o, h2_factor** ou
     int rc = guard([&] {
         H2_REQUIRE(A && o, H2_ERR_ARG, "null matrix or options");
         H2_REQUIRE(o->eps_lu >= 0 && std::isfinite(o->eps_lu), H2_ERR_ARG, "eps_lu must be >= 0");
-        H2_REQUIRE(o->norm_a > 0 && std::isfinite(o->norm_a), H2_ERR_ARG, "norm_a must be > 0");
+        H2_REQUIRE((o->norm_a > 0 && std::isfinite(o->norm_a)) || o->sys_norm_a, H2_ERR_ARG,
+                   "norm_a must be > 0");
         H2_REQUIRE(o->precision == H2_PREC_FP64 || o->precision == H2_PREC_FP32, H2_ERR_ARG,
                    "unknown precision");
         Z = new h2_factor();
@@ -308,25 +283,35 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
         }
         dy.alloc(vbytes, s);
         dr.alloc(vbytes, s);
-        dn.alloc(2 * nrhs * sizeof(double), s);
+        const HostStructure& HS = A->m.H;
+        const int nseg = HS.nsys;
+        dn.alloc(std::max(2 * nseg, 1) * nrhs * sizeof(double), s);
+        const int64_t* seg = A->m.d_sys_voff.as<int64_t>();
         H2_CUDA_CHECK(cudaMemcpy2DAsync(xd, lx * sizeof(double), bd, lb * sizeof(double), n * sizeof(double),
                                         nrhs, cudaMemcpyDeviceToDevice, s));
         F.solve_dev(xd, nrhs, lx);
-        const double nA = F.norm_a_;
-        std::vector<double> h(2 * nrhs), xnorm(nrhs);
-        // backward error of x; r = b - A x is left in dr
+        const std::vector<double>& nA = F.norm_sys;
+        std::vector<double> h(std::max(2 * nseg, 1) * nrhs), xscale(nrhs);
+        // backward error of x (max over systems and columns of ||r|| / (||A_s|| ||x||));
+        // r = b - A x is left in dr.  xscale[c] = min over systems of ||A_s|| ||x_s,c||.
         auto residual = [&]() -> double {
             matvec_dev(A->m, nrhs, xd, lx, dy.as<double>(), n, s);
             residual_dev(bd, lb, dy.as<double>(), n, dr.as<double>(), n, n, nrhs, s);
-            colnorm2_dev(dr.as<double>(), n, n, nrhs, dn.as<double>(), s);
-            colnorm2_dev(xd, lx, n, nrhs, dn.as<double>() + nrhs, s);
-            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+            segnorm2_dev(dr.as<double>(), n, seg, nseg, nrhs, dn.as<double>(), s);
+            segnorm2_dev(xd, lx, seg, nseg, nrhs, dn.as<double>() + (size_t)nseg * nrhs, s);
+            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, 2 * (size_t)nseg * nrhs * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
             H2_CUDA_CHECK(cudaStreamSynchronize(s));
             double be = 0;
             for (int c = 0; c < nrhs; ++c) {
-                xnorm[c] = std::sqrt(h[nrhs + c]);
-                const double e = xnorm[c] > 0 ? std::sqrt(h[c]) / (nA * xnorm[c]) : (h[c] > 0 ? INFINITY : 0.0);
-                be = std::max(be, e);
+                xscale[c] = INFINITY;
+                for (int z = 0; z < nseg; ++z) {
+                    const double r2 = h[(size_t)c * nseg + z], x2 = h[(size_t)nseg * nrhs + (size_t)c * nseg + z];
+                    const double xs = nA[z] * std::sqrt(x2);
+                    const double e = xs > 0 ? std::sqrt(r2) / xs : (r2 > 0 ? INFINITY : 0.0);
+                    be = std::max(be, e);
+                    xscale[c] = std::min(xscale[c], xs);
+                }
             }
             H2_REQUIRE(std::isfinite(be), H2_ERR_NONFINITE, "non-finite residual in refinement");
             return be;
@@ -398,7 +383,7 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
                     Hc(j + 1, j, c) = 0.0;
                     g[(size_t)(j + 1) * nrhs + c] = -sj * g[(size_t)j * nrhs + c];
                     g[(size_t)j * nrhs + c] = cj * g[(size_t)j * nrhs + c];
-                    if (std::fabs(g[(size_t)(j + 1) * nrhs + c]) > target_rel * nA * xnorm[c]) done = false;
+                    if (std::fabs(g[(size_t)(j + 1) * nrhs + c]) > target_rel * xscale[c]) done = false;
                 }
                 H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
                 scale_dev(w, dn.as<double>(), n, nrhs, w, s);
@@ -480,22 +465,46 @@ int h2_layout_get(const h2_factor* Z, int32_t level, int64_t* sizes, int64_t* ra
     return H2_OK;
 }
 
-int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
-                  int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind) {
+int h2_plan_query_batch(int32_t nsys, const h2_matrix_desc* descs, int32_t level, int64_t* nbox,
+                        int64_t* nblk, int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind,
+                        int32_t* state, int32_t* system) {
     return guard([&] {
+        H2_REQUIRE(nsys >= 1 && descs != nullptr, H2_ERR_ARG, "need at least one descriptor");
+        std::vector<HostStructure> parts(nsys);
+        for (int z = 0; z < nsys; ++z) read_structure(&descs[z], parts[z]);
         HostStructure H;
-        read_structure(desc, H);
+        std::vector<int> order;
+        ForestValues fv;
+        merge_forest(parts, H, order, fv);
         Plan P;
         build_plan(H, P);
-        H2_REQUIRE(level >= 0 && level < (int)P.levels.size(), H2_ERR_ARG, "bad level");
-        const LevelStruct& S = P.levels[level];
+        H2_REQUIRE(level >= 0 && level <= (int)P.levels.size(), H2_ERR_ARG, "bad level");
+        const LevelStruct& S = level < (int)P.levels.size() ? P.levels[level] : P.toplev;
         if (nbox) *nbox = S.cnt;
         if (nblk) *nblk = S.nblocks();
         if (colour) for (int i = 0; i < S.cnt; ++i) colour[i] = S.colour[i];
         if (row_ptr) for (int i = 0; i <= S.cnt; ++i) row_ptr[i] = S.bptr[i];
         if (col) for (int b = 0; b < S.nblocks(); ++b) col[b] = S.bcol[b];
         if (kind) for (int b = 0; b < S.nblocks(); ++b) kind[b] = S.bkind[b];
+        if (state) for (int i = 0; i < S.cnt; ++i) state[i] = S.state[i];
+        if (system) for (int i = 0; i < S.cnt; ++i) system[i] = H.sys[S.first + i];
     });
+}
+
+int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
+                  int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind) {
+    if (!desc) { set_error("null descriptor"); return H2_ERR_ARG; }
+    // the skeletonised levels only (the batch query also reaches the top-only level)
+    int64_t nb = 0;
+    int rc = h2_plan_query_batch(1, desc, level, &nb, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr);
+    if (rc != H2_OK) return rc;
+    std::vector<int32_t> st(nb);
+    rc = h2_plan_query_batch(1, desc, level, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             st.data(), nullptr);
+    if (rc != H2_OK) return rc;
+    if (nb == 0 || st[0] != 1) { set_error("bad level"); return H2_ERR_ARG; }
+    return h2_plan_query_batch(1, desc, level, nbox, nblk, colour, row_ptr, col, kind, nullptr, nullptr);
 }
 
 }  // extern "C"

@@ -48,6 +48,7 @@ static LevelArgs<T> args_of(LevelRT& L, DevStatus* st) {
     a.nb_blk = L.d_nb_blk.as<int>();
     a.nb_blkT = L.d_nb_blkT.as<int>();
     a.diag_blk = L.d_diag_blk.as<int>();
+    a.eps_fill = L.d_eps.as<T>();
     a.status = st;
     return a;
 }
@@ -117,8 +118,14 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
     A = A_;
     eps_lu = o.eps_lu;
     norm_a = o.norm_a;
-    norm_a_ = o.norm_a;
     precision = o.precision;
+    norm_sys.assign(A->H.nsys, o.norm_a);
+    if (o.sys_norm_a)
+        for (int z = 0; z < A->H.nsys; ++z) {
+            H2_REQUIRE(o.sys_norm_a[z] > 0 && std::isfinite(o.sys_norm_a[z]), H2_ERR_ARG,
+                       "sys_norm_a entries must be > 0");
+            norm_sys[z] = o.sys_norm_a[z];
+        }
     time_kernels = (o.flags & H2_FLAG_TIME_KERNELS) != 0;
     stream = static_cast<cudaStream_t>(o.stream);
     status.alloc(sizeof(DevStatus), stream);
@@ -207,6 +214,17 @@ void FactorImpl<T>::setup_level(size_t a) {
         else L.n[i] = lv[a - 1].kt[2 * i] + lv[a - 1].kt[2 * i + 1];
         L.k[i] = (int)H.rank[S.first + i];
     }
+    // boxes of dense top matrices: offsets inside their system's matrix
+    L.ttoff.assign(S.cnt, 0);
+    L.tsys.assign(S.cnt, 0);
+    for (int i : S.top_boxes) {
+        const int z = H.sys[S.first + i];
+        L.tsys[i] = z;
+        L.ttoff[i] = sys_nt[z];
+        sys_nt[z] += L.n[i];
+    }
+    std::vector<T> eps(S.cnt);
+    for (int i = 0; i < S.cnt; ++i) eps[i] = (T)(eps_lu * norm_sys[H.sys[S.first + i]]);
     const int nb = S.nblocks();
     L.brow.resize(nb);
     L.blk_off.assign(nb + 1, 0);
@@ -231,14 +249,21 @@ void FactorImpl<T>::setup_level(size_t a) {
     upload(L.d_bcol, S.bcol, s);
     upload(L.d_V_off, L.V_off, s);
     upload(L.d_voff, L.voff, s);
+    upload(L.d_ttoff, L.ttoff, s);
+    upload(L.d_tsys, L.tsys, s);
+    upload(L.d_top_boxes, S.top_boxes, s);
+    upload(L.d_skel_boxes, S.skel_boxes, s);
+    upload(L.d_eps, eps, s);
     L.kt.assign(S.cnt, 0);
     upload(L.d_kt, L.kt, s);
     track(this, L.blk, std::max<int64_t>(1, L.blk_off[nb]) * sizeof(T), s);
     if (is_top) return;
     track(this, L.V, std::max<int64_t>(1, L.V_off[S.cnt]) * sizeof(T), s);
-    prefix(L.Q_off, [&](int i) { return (int64_t)L.n[i] * L.n[i]; });
+    // factor data only for the boxes skeletonised here
+    auto sk = [&](int i) { return S.state[i] == 1; };
+    prefix(L.Q_off, [&](int i) { return sk(i) ? (int64_t)L.n[i] * L.n[i] : 0; });
     L.LU_off = L.Q_off;
-    prefix(L.piv_off, [&](int i) { return (int64_t)L.n[i]; });
+    prefix(L.piv_off, [&](int i) { return sk(i) ? (int64_t)L.n[i] : 0; });
     L.Nsum.assign(S.cnt, 0);
     L.nbofs.assign(S.nb_col.size(), 0);
     L.diag_blk.assign(S.cnt, -1);
@@ -253,7 +278,7 @@ void FactorImpl<T>::setup_level(size_t a) {
     }
     L.WLld.resize(S.cnt);
     for (int i = 0; i < S.cnt; ++i) L.WLld[i] = L.Nsum[i] + L.n[i];
-    prefix(L.WU_off, [&](int i) { return (int64_t)L.n[i] * L.WLld[i]; });
+    prefix(L.WU_off, [&](int i) { return sk(i) ? (int64_t)L.n[i] * L.WLld[i] : 0; });
     L.WL_off = L.WU_off;
     upload(L.d_Q_off, L.Q_off, s);
     upload(L.d_LU_off, L.LU_off, s);
@@ -471,9 +496,6 @@ void FactorImpl<T>::run_level(size_t a) {
     upload(d_c_box, S.sch_ci, s);
     upload(d_c_ablk, S.sch_cA, s);
     upload(d_c_kpos, S.sch_ckpos, s);
-    int nmax_level = 1;
-    for (int v : L.n) nmax_level = std::max(nmax_level, v);
-    const T eps_fill = (T)(eps_lu * norm_a);
     for (int c = 0; c < nc; ++c) {
         const int b0 = W.box_cptr[c], nbx = W.box_cptr[c + 1] - b0;
         if (nbx == 0) continue;
@@ -501,7 +523,7 @@ void FactorImpl<T>::run_level(size_t a) {
         }
         kbegin(H2_K_BASIS);
         k_basis<T><<<nbx, 256, W.smem_basis[c], s>>>(ar, CL, c, scratch.as<T>(), scratch.as<T>(),
-                                                     eps_fill, W.w_in_smem[c]);
+                                                     W.w_in_smem[c]);
         kend();
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
@@ -667,73 +689,94 @@ void FactorImpl<T>::close_level(size_t a) {
 }
 
 // ------------------------------------------------------------------ top level
+// Dense float64 top matrices of the systems whose skeletonisation ends below level a:
+// allocated here (their orders are now known) and assembled from the level's blocks,
+// before the level close releases them.
+template <class T>
+void FactorImpl<T>::assemble_tops(size_t a) {
+    LevelRT& L = lv[a];
+    const LevelStruct& S = *L.S;
+    if (S.top_boxes.empty()) return;
+    const MatrixObj& M = *A;
+    const Plan& P = M.plan;
+    cudaStream_t s = stream;
+    for (int z = 0; z < M.H.nsys; ++z) {
+        if (P.sys_toplev[z] != S.l) continue;
+        const int64_t n2 = sys_nt[z] * sys_nt[z];
+        track(this, sys_Dt[z], std::max<int64_t>(1, n2) * sizeof(double), s);
+        track(this, sys_piv[z], std::max<int64_t>(1, sys_nt[z]) * sizeof(int), s);
+        H2_CUDA_CHECK(cudaMemsetAsync(sys_Dt[z].ptr, 0, std::max<int64_t>(1, n2) * sizeof(double), s));
+        tops[z] = TopSys{sys_Dt[z].as<double>(), sys_piv[z].as<int>(), sys_nt[z]};
+    }
+    upload(d_tops, tops, s);
+    std::vector<int> blist;
+    for (int i : S.top_boxes)
+        for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) blist.push_back(b);
+    if (blist.empty()) return;
+    DevBuf d_blist, d_near;
+    upload(d_blist, blist, s);
+    const bool leaf = S.l == M.H.d;                  // float64 blocks straight from A
+    if (leaf) upload(d_near, S.near_entry, s);
+    kbegin(H2_K_TOP);
+    k_top_assemble<T><<<(unsigned)blist.size(), 256, 0, s>>>(
+        d_blist.as<int>(), L.blk.as<T>(), L.d_blk_off.as<int64_t>(), leaf ? M.D.as<double>() : nullptr,
+        M.d_D_off.as<int64_t>(), leaf ? d_near.as<int64_t>() : nullptr, L.d_brow.as<int>(), L.d_bcol.as<int>(),
+        L.d_n.as<int>(), L.d_ttoff.as<int64_t>(), L.d_tsys.as<int>(), d_tops.as<TopSys>());
+    kend();
+    H2_LAUNCHED();
+}
+
+// Blocked LU with partial pivoting of every system's top matrix: one launch per
+// kernel and panel for the whole batch.
 template <class T>
 void FactorImpl<T>::top_factor() {
-    const Plan& P = A->plan;
-    const MatrixObj& M = *A;
     cudaStream_t s = stream;
     LevelRT& Tl = lv.back();
-    const LevelStruct& S = *Tl.S;
-    tn = Tl.n;
-    toff.assign(S.cnt + 1, 0);
-    for (int i = 0; i < S.cnt; ++i) toff[i + 1] = toff[i] + tn[i];
-    nt = toff[S.cnt];
-    upload(d_toff, toff, s);
-    track(this, Dt, std::max<int64_t>(1, nt * nt) * sizeof(double), s);
-    track(this, tpiv, std::max<int64_t>(1, nt) * sizeof(int), s);
-    H2_CUDA_CHECK(cudaMemsetAsync(Dt.ptr, 0, std::max<int64_t>(1, nt * nt) * sizeof(double), s));
-    if (nt > 0) {
-        if (P.top < 0) {
-            std::vector<int64_t> off(S.nblocks());
-            for (int b = 0; b < S.nblocks(); ++b) off[b] = M.H.D_off[S.near_entry[b]];
-            DevBuf d_off;
-            upload(d_off, off, s);
-            kbegin(H2_K_TOP);
-            k_top_assemble<double><<<S.nblocks(), 256, 0, s>>>(M.D.as<double>(), d_off.as<int64_t>(),
-                                                               Tl.d_brow.as<int>(), Tl.d_bcol.as<int>(),
-                                                               Tl.d_n.as<int>(), d_toff.as<int64_t>(),
-                                                               Dt.as<double>(), nt);
-            kend();
-            H2_LAUNCHED();
-        } else {
-            kbegin(H2_K_TOP);
-            k_top_assemble<T><<<S.nblocks(), 256, 0, s>>>(Tl.blk.as<T>(), Tl.d_blk_off.as<int64_t>(),
-                                                          Tl.d_brow.as<int>(), Tl.d_bcol.as<int>(),
-                                                          Tl.d_n.as<int>(), d_toff.as<int64_t>(),
-                                                          Dt.as<double>(), nt);
-            kend();
-            H2_LAUNCHED();
-        }
-        H2_CUDA_CHECK(cudaGetLastError());
-        const int NB = 64;
-        for (int64_t j0 = 0; j0 < nt; j0 += NB) {
-            const int jb = (int)std::min<int64_t>(NB, nt - j0);
-            kbegin(H2_K_TOP);
-            k_top_panel<<<1, 1024, 0, s>>>(Dt.as<double>(), nt, j0, jb, tpiv.as<int>(), status.as<DevStatus>());
-            kend();
-            H2_LAUNCHED();
-            kbegin(H2_K_TOP);
-            k_top_swap<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(Dt.as<double>(), nt, j0, jb, tpiv.as<int>());
-            kend();
-            H2_LAUNCHED();
-            const int64_t rest = nt - j0 - jb;
-            if (rest > 0) {
-                kbegin(H2_K_TOP);
-                k_top_trsm<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(Dt.as<double>(), nt, j0, jb);
-                kend();
-                H2_LAUNCHED();
-                dim3 g((unsigned)((rest + 63) / 64), (unsigned)((rest + 63) / 64));
-                kbegin(H2_K_TOP);
-                k_top_gemm<<<g, 256, 0, s>>>(Dt.as<double>(), nt, j0, jb);
-                kend();
-                H2_LAUNCHED();
-            }
-        }
-        H2_CUDA_CHECK(cudaGetLastError());
+    assemble_tops(lv.size() - 1);
+    const int nsys = (int)tops.size();
+    nt = 0;
+    int64_t ntmax = 0;
+    sys_xt.assign(nsys + 1, 0);
+    double flops = 0;
+    for (int z = 0; z < nsys; ++z) {
+        nt += sys_nt[z];
+        ntmax = std::max(ntmax, sys_nt[z]);
+        sys_xt[z + 1] = sys_xt[z] + sys_nt[z];
+        flops += 2.0 / 3.0 * (double)sys_nt[z] * sys_nt[z] * sys_nt[z];
     }
+    upload(d_tops, tops, s);
+    upload(d_sys_nt, sys_nt, s);
+    upload(d_sys_xt, sys_xt, s);
+    const int NB = 64;
+    for (int64_t j0 = 0; j0 < ntmax; j0 += NB) {
+        const int jb = (int)std::min<int64_t>(NB, ntmax - j0);
+        kbegin(H2_K_TOP);
+        k_top_panel<<<nsys, 1024, 0, s>>>(d_tops.as<TopSys>(), j0, NB, status.as<DevStatus>());
+        kend();
+        H2_LAUNCHED();
+        kbegin(H2_K_TOP);
+        k_top_swap<<<dim3((unsigned)((ntmax + 255) / 256), nsys), 256, 0, s>>>(d_tops.as<TopSys>(), j0, NB);
+        kend();
+        H2_LAUNCHED();
+        const int64_t rest = ntmax - j0 - jb;
+        if (rest > 0) {
+            kbegin(H2_K_TOP);
+            k_top_trsm<<<dim3((unsigned)((rest + 127) / 128), nsys), 128, 0, s>>>(d_tops.as<TopSys>(), j0, NB);
+            kend();
+            H2_LAUNCHED();
+            const unsigned g = (unsigned)((rest + 63) / 64);
+            kbegin(H2_K_TOP);
+            k_top_gemm<<<dim3(g, g, nsys), 256, 0, s>>>(d_tops.as<TopSys>(), j0, NB);
+            kend();
+            H2_LAUNCHED();
+        }
+    }
+    H2_CUDA_CHECK(cudaGetLastError());
     untrack(this, Tl.blk);
     mark(PH_TOP);
-    account(PH_TOP, 2.0 / 3.0 * (double)nt * nt * nt, 16.0 * (double)nt * nt);
+    double tb = 0;
+    for (int z = 0; z < nsys; ++z) tb += 16.0 * (double)sys_nt[z] * sys_nt[z];
+    account(PH_TOP, flops, tb);
     check_status("top-level LU");
 }
 
@@ -748,12 +791,20 @@ void FactorImpl<T>::factorize() {
     H2_CUDA_CHECK(cudaMemsetAsync(status.ptr, 0, sizeof(DevStatus), stream));
     lv.clear();
     lv.resize(P.levels.size() + 1);
+    const int nsys = A->H.nsys;
+    sys_nt.assign(nsys, 0);
+    sys_Dt.clear();
+    sys_Dt.resize(nsys);
+    sys_piv.clear();
+    sys_piv.resize(nsys);
+    tops.assign(nsys, TopSys{nullptr, nullptr, 0});
     bytes_now = 0;
     stats.peak_bytes = 0;
     mark(-1);
     setup_level(0);
     for (size_t a = 0; a < P.levels.size(); ++a) {
         run_level(a);
+        assemble_tops(a);
         setup_level(a + 1);
         close_level(a);
     }
@@ -784,7 +835,7 @@ void FactorImpl<T>::factorize() {
     stats.top_size = nt;
     int64_t fb = 0;
     for (auto& L : lv) fb += L.Q.bytes + L.LU.bytes + L.DI.bytes + L.piv.bytes + L.WU.bytes + L.WL.bytes;
-    fb += Dt.bytes + tpiv.bytes;
+    for (int z = 0; z < nsys; ++z) fb += sys_Dt[z].bytes + sys_piv[z].bytes;
     stats.factor_bytes = fb;
     // layout export (levels 0 .. nlevels-1)
     lay_sizes.clear(); lay_ranks.clear(); lay_rowptr.clear(); lay_col.clear(); lay_offset.clear();

@@ -48,7 +48,15 @@ struct LevelArgs {
     const int* nb_blk;     // block id of (i, j) per N(i) position
     const int* nb_blkT;    // block id of (j, i) per N(i) position
     const int* diag_blk;   // block id of (i, i)
+    const T* eps_fill;     // truncation threshold eps_lu * ||A_s|| of every box
     DevStatus* status;
+};
+
+// One dense top matrix of the batch (float64, column-major nt x nt) and its pivots.
+struct TopSys {
+    double* A;
+    int* piv;
+    int64_t nt;
 };
 
 // Per-colour work lists of the basis kernels (device pointers).

@@ -16,6 +16,10 @@ struct LevelRT {
     std::vector<int64_t> blk_off, V_off, Q_off, LU_off, piv_off, WU_off, WL_off, voff;
     std::vector<int> WLld, Nsum, nbofs, diag_blk, brow;
     int64_t vtot = 0;
+    // boxes of dense top matrices at this level: offset inside their system's matrix
+    std::vector<int64_t> ttoff;
+    std::vector<int> tsys;
+    DevBuf d_ttoff, d_tsys, d_top_boxes, d_skel_boxes, d_eps;
     // device: structure and offsets
     DevBuf d_n, d_k, d_kt, d_colour, d_blk_off, d_brow, d_bcol;
     DevBuf d_V_off, d_Q_off, d_LU_off, d_piv_off, d_WU_off, d_WL_off, d_WLld;
@@ -35,7 +39,7 @@ struct FactorBase {
     h2_factor_stats stats{};
     int64_t bytes_now = 0;
     int precision = H2_PREC_FP64;
-    double norm_a_ = 0;
+    std::vector<double> norm_sys;             // ||A_s|| of every system (caller order)
     cudaStream_t stream = nullptr;
     const MatrixObj* A = nullptr;
     std::vector<std::vector<int64_t>> lay_sizes, lay_ranks, lay_rowptr, lay_col, lay_offset;
@@ -48,11 +52,12 @@ template <class T>
 struct FactorImpl : FactorBase {
     double eps_lu = 0, norm_a = 0;
     std::vector<LevelRT> lv;
-    // top level (float64)
-    int64_t nt = 0;
-    std::vector<int64_t> toff;
-    std::vector<int> tn;
-    DevBuf Dt, tpiv, d_toff;
+    // dense top matrices (float64), one per system
+    int64_t nt = 0;                           // sum of their orders
+    std::vector<int64_t> sys_nt, sys_xt;      // order, prefix of orders
+    std::vector<DevBuf> sys_Dt, sys_piv;
+    std::vector<TopSys> tops;
+    DevBuf d_tops, d_sys_nt, d_sys_xt;
     DevBuf status;
     // events for phase timing
     std::vector<cudaEvent_t> ev;
@@ -73,6 +78,7 @@ struct FactorImpl : FactorBase {
     void setup_level(size_t a);
     void run_level(size_t a);
     void close_level(size_t a);
+    void assemble_tops(size_t a);
     void top_factor();
     void mark(int phase);
     void check_status(const char* where);

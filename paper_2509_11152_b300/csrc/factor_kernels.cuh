@@ -218,10 +218,11 @@ __device__ void rfactor_stream(const LevelArgs<T>& a, const ColourLists& L, int 
 template <class T>
 __global__ void __launch_bounds__(256)
 k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
-        T* __restrict__ gwork, T eps_fill, int w_in_smem) {
+        T* __restrict__ gwork, int w_in_smem) {
     const int slot = blockIdx.x;
     const int i = L.boxes[slot];
     const int n = a.n[i], k = a.k[i];
+    const T eps_fill = a.eps_fill[i];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nwarp = blockDim.x >> 5;
     const int CH = (n <= 192) ? 64 : 32;
@@ -988,31 +989,49 @@ __global__ void k_close_basis(LevelArgs<T> a, T* __restrict__ pV, const int64_t*
 }
 
 // ================================================================== top level
-// Dense float64 matrix of the top level from its blocks.
+// Dense float64 top matrices of the systems whose top level this is, from the level's
+// blocks (blk, working precision) or, at the leaf level, from A's float64 near-field
+// blocks (D != nullptr: entry near_entry[b] of D_off).  One thread block per block.
 template <class T>
-__global__ void k_top_assemble(const T* __restrict__ blk, const int64_t* __restrict__ blk_off,
+__global__ void k_top_assemble(const int* __restrict__ blist, const T* __restrict__ blk,
+                               const int64_t* __restrict__ blk_off, const double* __restrict__ D,
+                               const int64_t* __restrict__ D_off, const int64_t* __restrict__ near_entry,
                                const int* __restrict__ brow, const int* __restrict__ bcol,
-                               const int* __restrict__ n, const int64_t* __restrict__ toff,
-                               double* __restrict__ Dt, int64_t nt) {
-    const int b = blockIdx.x;
+                               const int* __restrict__ n, const int64_t* __restrict__ ttoff,
+                               const int* __restrict__ tsys, const TopSys* __restrict__ tops) {
+    const int b = blist[blockIdx.x];
     const int p = brow[b], q = bcol[b];
     const int np = n[p], nq = n[q];
-    const T* src = blk + blk_off[b];
-    double* dst = Dt + toff[p] + toff[q] * nt;
-    for (int64_t x = threadIdx.x; x < (int64_t)np * nq; x += blockDim.x) {
-        const int rr = (int)(x % np), c = (int)(x / np);
-        dst[rr + (int64_t)c * nt] = (double)src[x];
+    const TopSys ts = tops[tsys[p]];
+    double* dst = ts.A + ttoff[p] + ttoff[q] * ts.nt;
+    if (D) {
+        const double* src = D + D_off[near_entry[b]];
+        for (int64_t x = threadIdx.x; x < (int64_t)np * nq; x += blockDim.x)
+            dst[x % np + (x / np) * ts.nt] = src[x];
+    } else {
+        const T* src = blk + blk_off[b];
+        for (int64_t x = threadIdx.x; x < (int64_t)np * nq; x += blockDim.x)
+            dst[x % np + (x / np) * ts.nt] = (double)src[x];
     }
 }
 
-// Panel factorisation (columns j0..j0+jb of rows j0..nt) with partial pivoting.
+// The top LU runs over all systems at once: panel j0 of every top matrix whose order
+// exceeds j0 (blockIdx.x / y / z selects the system, see each kernel).
+
+// Panel factorisation (columns j0..j0+jb of rows j0..nt) with partial pivoting; one
+// thread block per system.
 __global__ void __launch_bounds__(1024)
-k_top_panel(double* __restrict__ A, int64_t nt, int64_t j0, int jb, int* __restrict__ piv,
-            DevStatus* st) {
+k_top_panel(const TopSys* __restrict__ tops, int64_t j0, int nb, DevStatus* st) {
     __shared__ double rv[32];
     __shared__ int64_t ri[32];
     __shared__ int64_t psel;
     __shared__ double pval;
+    const TopSys ts = tops[blockIdx.x];
+    const int64_t nt = ts.nt;
+    if (j0 >= nt) return;
+    const int jb = (int)(nt - j0 < nb ? nt - j0 : nb);
+    double* A = ts.A;
+    int* piv = ts.piv;
     const int tid = threadIdx.x;
     for (int jj = 0; jj < jb; ++jj) {
         const int64_t j = j0 + jj;
@@ -1065,13 +1084,18 @@ k_top_panel(double* __restrict__ A, int64_t nt, int64_t j0, int jb, int* __restr
     }
 }
 
-// Apply the panel's row interchanges to the columns outside the panel.
-__global__ void k_top_swap(double* __restrict__ A, int64_t nt, int64_t j0, int jb,
-                           const int* __restrict__ piv) {
+// Apply the panel's row interchanges to the columns outside the panel (blockIdx.y =
+// system).
+__global__ void k_top_swap(const TopSys* __restrict__ tops, int64_t j0, int nb) {
+    const TopSys ts = tops[blockIdx.y];
+    const int64_t nt = ts.nt;
+    if (j0 >= nt) return;
+    const int jb = (int)(nt - j0 < nb ? nt - j0 : nb);
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nt || (c >= j0 && c < j0 + jb)) return;
+    double* A = ts.A;
     for (int jj = 0; jj < jb; ++jj) {
-        const int64_t j = j0 + jj, p = piv[j];
+        const int64_t j = j0 + jj, p = ts.piv[j];
         if (p < j || p >= nt) return;   // panel stopped at a singular pivot (status set)
         if (p != j) {
             const double t0 = A[j + c * nt];
@@ -1081,25 +1105,37 @@ __global__ void k_top_swap(double* __restrict__ A, int64_t nt, int64_t j0, int j
     }
 }
 
-// U12 = L11^-1 A12 (unit lower L11 of the panel), one thread per column.
-__global__ void k_top_trsm(double* __restrict__ A, int64_t nt, int64_t j0, int jb) {
+// U12 = L11^-1 A12 (unit lower L11 of the panel), one thread per column (blockIdx.y =
+// system).
+__global__ void k_top_trsm(const TopSys* __restrict__ tops, int64_t j0, int nb) {
+    const TopSys ts = tops[blockIdx.y];
+    const int64_t nt = ts.nt;
+    if (j0 >= nt) return;
+    const int jb = (int)(nt - j0 < nb ? nt - j0 : nb);
     const int64_t c = j0 + jb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nt) return;
-    double* col = A + c * nt;
+    const double* A = ts.A;
+    double* col = ts.A + c * nt;
     for (int jj = 0; jj < jb; ++jj) {
         const double x = col[j0 + jj];
         for (int r = jj + 1; r < jb; ++r) col[j0 + r] -= A[(j0 + r) + (j0 + jj) * nt] * x;
     }
 }
 
-// A22 -= L21 U12 (64x64 tiles, float64).
+// A22 -= L21 U12 (64x64 tiles, float64; blockIdx.z = system).
 __global__ void __launch_bounds__(256)
-k_top_gemm(double* __restrict__ A, int64_t nt, int64_t j0, int jb) {
+k_top_gemm(const TopSys* __restrict__ tops, int64_t j0, int nb) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
+    const TopSys ts = tops[blockIdx.z];
+    const int64_t nt = ts.nt;
+    if (j0 >= nt) return;
+    const int jb = (int)(nt - j0 < nb ? nt - j0 : nb);
     const int64_t base = j0 + jb;
     const int64_t m0 = base + (int64_t)blockIdx.x * BM, n0 = base + (int64_t)blockIdx.y * BN;
+    if (m0 >= nt || n0 >= nt) return;
+    double* A = ts.A;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < jb; k0 += BK) {

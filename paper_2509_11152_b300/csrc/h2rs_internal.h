@@ -76,12 +76,26 @@ void upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ host copy of A
+// A forest of one or more complete binary cluster trees whose levels are aligned by
+// height above the leaves (a batch of independent systems).  Level l (0 = the roots
+// of the deepest trees, d = every leaf) holds the global node ids
+// lev_first[l] .. lev_first[l] + lev_cnt[l] - 1; trees are ordered by decreasing depth
+// so that the children of local box i at level l are the local boxes 2i and 2i+1 at
+// level l+1, and a tree of depth d_s has its root at level d - d_s.  For one tree this
+// is the heap numbering (lev_first[l] = 2^l - 1).
 struct HostStructure {
     int64_t n = 0;
     int d = 0;
     int64_t nnodes = 0;
     std::vector<int64_t> node_start, node_size, rank;
     std::vector<int64_t> U_off, E_off, adm_ptr, adm_col, S_off, inad_ptr, inad_col, D_off;
+    std::vector<int64_t> lev_first, lev_cnt;  // d+1 entries
+    std::vector<int64_t> parent;              // global parent id, -1 for a root
+    std::vector<int> sys;                     // system (tree) of every node
+    int nsys = 1;
+    std::vector<int> sys_root;                // level of each system's root
+    std::vector<int64_t> sys_voff;            // nsys+1: vector offsets (caller order)
+    int level_of(int64_t g) const;            // level of a global node id
 };
 
 // ------------------------------------------------------------------ plan
@@ -90,6 +104,11 @@ struct LevelStruct {
     int l = 0;
     int cnt = 0;               // boxes at the level
     int64_t first = 0;         // global id of the first box
+    // box state: 0 not reached (above its system's top), 1 skeletonised at this level,
+    // 2 part of its system's dense top matrix
+    std::vector<int8_t> state;
+    std::vector<int> top_boxes;               // boxes with state 2, ascending
+    std::vector<int> skel_boxes;              // boxes with state 1, ascending
     std::vector<int> nb_ptr, nb_col;          // near field N(i), sorted, includes i
     std::vector<int> colour;
     int ncolour = 0;
@@ -127,12 +146,31 @@ struct LevelStruct {
 
 struct Plan {
     int d = 0;
-    int top = -1;                             // t, or -1 when nothing is admissible
-    std::vector<LevelStruct> levels;          // index 0 = level d (leaves) ... level t
-    LevelStruct toplev;                       // the level holding the dense top matrix
+    int top = -1;                             // min over systems of t, -1 when no system
+                                              // has an admissible block
+    std::vector<int> sys_top;                 // per system: t_s (forest level), or -1
+    std::vector<int> sys_toplev;              // per system: level of its dense top matrix
+    std::vector<LevelStruct> levels;          // index 0 = level d (leaves) ... level top
+    LevelStruct toplev;                       // the last level: dense top matrices only
 };
 
 void build_plan(const HostStructure& H, Plan& P);
+
+// one tree (heap numbering) from a descriptor, with consistency checks
+void read_structure(const h2_matrix_desc* d, HostStructure& H);
+// Where each tree's value arrays (U, E, S, D) land in the forest's arrays: element
+// ranges copied unchanged (a tree's values of one level stay contiguous).
+struct ValueChunk {
+    int sys;                                  // caller index of the tree
+    int64_t src, dst, cnt;                    // element offsets and count
+};
+struct ForestValues {
+    std::vector<ValueChunk> U, E, S, D;
+};
+// forest of the trees in `parts` (caller order); order[r] = caller index of the tree at
+// merged rank r (trees sorted by decreasing depth, ties in caller order)
+void merge_forest(const std::vector<HostStructure>& parts, HostStructure& F, std::vector<int>& order,
+                  ForestValues& values);
 
 // ------------------------------------------------------------------ objects
 struct MatrixObj {
@@ -142,6 +180,9 @@ struct MatrixObj {
     DevBuf U, E, S, D;                        // float64 values on the device
     DevBuf d_node_start, d_node_size, d_rank, d_U_off, d_E_off, d_S_off, d_D_off;
     DevBuf d_adm_ptr, d_adm_col, d_inad_ptr, d_inad_col;
+    DevBuf d_parent;                          // forest parent of every node (-1: root)
+    DevBuf d_child0;                          // first child id (children c, c+1), -1: leaf
+    DevBuf d_sys_voff;                        // nsys+1 vector offsets of the systems
     // matvec helpers: per node offsets of the coefficient vectors (rank prefix)
     std::vector<int64_t> coef_off;
     DevBuf d_coef_off;

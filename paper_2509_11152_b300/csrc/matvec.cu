@@ -27,17 +27,19 @@ __global__ void mv_leaf_up(const double* __restrict__ U, const int64_t* __restri
     }
 }
 
-// xh_p = sum_c E_c^T xh_c for the nodes p of one level (first = first node id)
+// xh_p = sum_c E_c^T xh_c for the nodes p of one level (first = first node id; the
+// children of p are child0[p] and child0[p] + 1)
 __global__ void mv_up(const double* __restrict__ E, const int64_t* __restrict__ E_off,
                       const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off, int64_t first,
-                      double* __restrict__ xh, int nrhs) {
+                      const int64_t* __restrict__ child0, double* __restrict__ xh, int nrhs) {
     const int64_t p = first + blockIdx.x;
+    const int64_t c0 = child0[p];
     const int kp = (int)rank[p];
     double* out = xh + coef_off[p] * nrhs;
     for (int e = threadIdx.x; e < kp * nrhs; e += blockDim.x) {
         const int a = e % kp, c = e / kp;
         double acc = 0;
-        for (int64_t ch = 2 * p + 1; ch <= 2 * p + 2; ++ch) {
+        for (int64_t ch = c0; ch <= c0 + 1; ++ch) {
             const int kc = (int)rank[ch];
             const double* Ec = E + E_off[ch] + (int64_t)a * kc;   // column a of E_c
             const double* xc = xh + coef_off[ch] * nrhs + (int64_t)c * kc;
@@ -69,12 +71,13 @@ __global__ void mv_couple(const double* __restrict__ S, const int64_t* __restric
     }
 }
 
-// yh_c += E_c yh_parent for the nodes c of one level
+// yh_c += E_c yh_parent for the nodes c of one level (roots of a forest have none)
 __global__ void mv_down(const double* __restrict__ E, const int64_t* __restrict__ E_off,
                         const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off, int64_t first,
-                        double* __restrict__ yh, int nrhs) {
+                        const int64_t* __restrict__ parent, double* __restrict__ yh, int nrhs) {
     const int64_t g = first + blockIdx.x;
-    const int64_t p = (g - 1) / 2;
+    const int64_t p = parent[g];
+    if (p < 0) return;
     const int kc = (int)rank[g], kp = (int)rank[p];
     double* out = yh + coef_off[g] * nrhs;
     const double* yp = yh + coef_off[p] * nrhs;
@@ -221,6 +224,32 @@ void add_dev(double* x, int64_t ldx, const double* d, int64_t ldd, int64_t n, in
     count_launch();
 }
 
+// out[c * nseg + z] = squared 2-norm of rows seg[z] .. seg[z+1]-1 of column c
+__global__ void v_segnorm2(const double* __restrict__ v, int64_t ldv, const int64_t* __restrict__ seg, int nseg,
+                           double* __restrict__ out) {
+    __shared__ double red[32];
+    const int z = blockIdx.x, c = blockIdx.y;
+    double acc = 0;
+    for (int64_t a = seg[z] + threadIdx.x; a < seg[z + 1]; a += blockDim.x) {
+        const double t = v[a + c * ldv];
+        acc += t * t;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        out[(int64_t)c * nseg + z] = s;
+    }
+}
+
+void segnorm2_dev(const double* v, int64_t ldv, const int64_t* seg, int nseg, int nrhs, double* out,
+                  cudaStream_t s) {
+    v_segnorm2<<<dim3(nseg, nrhs), 256, 0, s>>>(v, ldv, seg, nseg, out);
+    count_launch();
+}
+
 void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s) {
     v_colnorm2<<<nrhs, 256, 0, s>>>(v, ldv, n, out);
     count_launch();
@@ -242,8 +271,8 @@ void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, doub
         yh_p = yh_buf.as<double>();
     }
     struct { double* p; } xh{xh_p}, yh{yh_p};
-    const int64_t first_leaf = (int64_t(1) << d) - 1;
-    const int nleaf = 1 << d;
+    const int64_t first_leaf = H.lev_first[d];
+    const int nleaf = (int)H.lev_cnt[d];
     const int64_t* rank = M.d_rank.as<int64_t>();
     const int64_t* coef = M.d_coef_off.as<int64_t>();
     mv_leaf_up<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
@@ -251,9 +280,8 @@ void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, doub
                                      xh.p, nrhs);
     count_launch();
     for (int l = d; l >= 1; --l) {
-        const int64_t pf = (int64_t(1) << (l - 1)) - 1;
-        mv_up<<<1 << (l - 1), 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, pf,
-                                           xh.p, nrhs);
+        mv_up<<<(unsigned)H.lev_cnt[l - 1], 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef,
+                                                         H.lev_first[l - 1], M.d_child0.as<int64_t>(), xh.p, nrhs);
         count_launch();
     }
     mv_couple<<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
@@ -261,9 +289,8 @@ void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, doub
                                                   coef, xh.p, yh.p, nrhs);
     count_launch();
     for (int l = 1; l <= d; ++l) {
-        const int64_t f = (int64_t(1) << l) - 1;
-        mv_down<<<1 << l, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, f,
-                                       yh.p, nrhs);
+        mv_down<<<(unsigned)H.lev_cnt[l], 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef,
+                                                       H.lev_first[l], M.d_parent.as<int64_t>(), yh.p, nrhs);
         count_launch();
     }
     mv_leaf_down<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),

@@ -15,6 +15,9 @@ void residual_dev(const double* b, int64_t ldb, const double* y, int64_t ldy, do
                   int64_t n, int nrhs, cudaStream_t s);
 void add_dev(double* x, int64_t ldx, const double* d, int64_t ldd, int64_t n, int nrhs, cudaStream_t s);
 void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s);
+// out[c * nseg + z] = squared norm of rows seg[z] .. seg[z+1]-1 of column c (seg: device)
+void segnorm2_dev(const double* v, int64_t ldv, const int64_t* seg, int nseg, int nrhs, double* out,
+                  cudaStream_t s);
 
 // GMRES helpers on n x nrhs column blocks stored contiguously (ld n):
 // h[i*nrhs+c] = <V_i[:,c], w[:,c]>;  w[:,c] += sum_i coef[i*nrhs+c] V_i[:,c];  y = diag(sc) x

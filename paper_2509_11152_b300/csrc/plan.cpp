@@ -25,27 +25,34 @@ int LevelStruct::find(int i, int j) const {
 
 static inline uint64_t key(int a, int b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
 
-// near-field CSR of level l (local indices), from A's inadmissible CSR
+// near-field CSR of level l (local indices), from A's inadmissible CSR; boxes that are
+// not reached at this level (state 0) get empty rows
 static void near_graph(const HostStructure& H, int l, LevelStruct& L) {
     L.l = l;
-    L.first = (int64_t(1) << l) - 1;
-    L.cnt = 1 << l;
+    L.first = H.lev_first[l];
+    L.cnt = (int)H.lev_cnt[l];
     L.nb_ptr.assign(L.cnt + 1, 0);
     L.nb_col.clear();
+    L.top_boxes.clear();
+    L.skel_boxes.clear();
     for (int i = 0; i < L.cnt; ++i) {
         int64_t g = L.first + i;
-        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e)
-            L.nb_col.push_back((int)(H.inad_col[e] - L.first));
+        if (L.state[i] != 0)
+            for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e)
+                L.nb_col.push_back((int)(H.inad_col[e] - L.first));
         std::sort(L.nb_col.begin() + L.nb_ptr[i], L.nb_col.end());
         L.nb_ptr[i + 1] = (int)L.nb_col.size();
+        if (L.state[i] == 1) L.skel_boxes.push_back(i);
+        if (L.state[i] == 2) L.top_boxes.push_back(i);
     }
 }
 
-// first-fit colouring in ascending box index, self loops ignored
+// first-fit colouring in ascending box index, self loops ignored; only the boxes
+// skeletonised at this level are coloured (others keep -1)
 static void colour_level(LevelStruct& L) {
     L.colour.assign(L.cnt, -1);
     std::vector<int> mark;
-    for (int i = 0; i < L.cnt; ++i) {
+    for (int i : L.skel_boxes) {
         mark.assign(L.nb_ptr[i + 1] - L.nb_ptr[i] + 2, 0);
         for (int e = L.nb_ptr[i]; e < L.nb_ptr[i + 1]; ++e) {
             int j = L.nb_col[e];
@@ -59,7 +66,7 @@ static void colour_level(LevelStruct& L) {
     }
     L.ncolour = L.cnt ? *std::max_element(L.colour.begin(), L.colour.end()) + 1 : 0;
     L.cboxes.assign(L.ncolour, {});
-    for (int i = 0; i < L.cnt; ++i) L.cboxes[L.colour[i]].push_back(i);
+    for (int i : L.skel_boxes) L.cboxes[L.colour[i]].push_back(i);
 }
 
 static bool is_near(const LevelStruct& L, int i, int j) {
@@ -74,7 +81,7 @@ static void block_list(LevelStruct& L, const std::vector<std::pair<int, int>>& c
     for (int i = 0; i < L.cnt; ++i)
         for (int e = L.nb_ptr[i]; e < L.nb_ptr[i + 1]; ++e) rows[i].push_back(L.nb_col[e]);
     std::vector<std::vector<int>> fill(L.cnt);
-    for (int i = 0; i < L.cnt; ++i)
+    for (int i : L.skel_boxes)                    // only eliminated boxes create fill
         for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
             int j = L.nb_col[a];
             for (int b = L.nb_ptr[i]; b < L.nb_ptr[i + 1]; ++b) {
@@ -227,34 +234,59 @@ static void close_lists(const HostStructure& H, LevelStruct& C, const LevelStruc
         }
 }
 
+// leaf near blocks come from A's inadmissible leaf entries
+static void leaf_entries(const HostStructure& H, LevelStruct& L) {
+    L.near_entry.assign(L.nblocks(), -1);
+    for (int i = 0; i < L.cnt; ++i) {
+        if (L.state[i] == 0) continue;
+        int64_t g = L.first + i;
+        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
+            int j = (int)(H.inad_col[e] - L.first);
+            L.near_entry[L.find(i, j)] = e - H.inad_ptr[L.first];
+        }
+    }
+}
+
 void build_plan(const HostStructure& H, Plan& P) {
     P.d = H.d;
+    // per system: t_s = the coarsest level holding an admissible block (levels t_s ..
+    // leaves are skeletonised; the dense top matrix is formed at level t_s - 1), or -1
+    // when nothing is admissible (the top matrix is the leaf near field)
+    P.sys_top.assign(H.nsys, -1);
+    for (int64_t g = 0; g < H.nnodes; ++g)
+        if (H.adm_ptr[g + 1] > H.adm_ptr[g]) {
+            const int l = H.level_of(g);
+            int& t = P.sys_top[H.sys[g]];
+            t = t < 0 ? l : std::min(t, l);
+        }
+    P.sys_toplev.assign(H.nsys, H.d);
     P.top = -1;
-    for (int l = 0; l <= H.d && P.top < 0; ++l) {
-        int64_t first = (int64_t(1) << l) - 1, last = (int64_t(1) << (l + 1)) - 1;
-        if (H.adm_ptr[last] - H.adm_ptr[first] > 0) P.top = l;
-    }
+    for (int s = 0; s < H.nsys; ++s)
+        if (P.sys_top[s] >= 0) {
+            P.sys_toplev[s] = P.sys_top[s] - 1;
+            P.top = P.top < 0 ? P.sys_top[s] : std::min(P.top, P.sys_top[s]);
+        }
+    auto set_state = [&](LevelStruct& L, int l) {
+        L.state.assign(H.lev_cnt[l], 0);
+        for (int64_t i = 0; i < H.lev_cnt[l]; ++i) {
+            const int s = H.sys[H.lev_first[l] + i];
+            if (P.sys_top[s] >= 0 && l >= P.sys_top[s]) L.state[i] = 1;
+            else if (l == P.sys_toplev[s]) L.state[i] = 2;
+        }
+    };
     P.levels.clear();
     std::vector<std::pair<int, int>> carried;
-    int lowest = P.top < 0 ? H.d + 1 : P.top;       // skeletonised levels d .. t
+    int lowest = P.top < 0 ? H.d + 1 : P.top;       // forest levels with skeletonised boxes
     for (int l = H.d; l >= lowest; --l) {
         LevelStruct L;
+        set_state(L, l);
         near_graph(H, l, L);
         colour_level(L);
         block_list(L, carried);
         schur_lists(L);
         solve_lists(L);
-        for (int i = 0; i < L.cnt; ++i)
-            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) L.near_entry.push_back(-1);
-        if (l == H.d) {                              // leaf near blocks come from A
-            for (int i = 0; i < L.cnt; ++i) {
-                int64_t g = L.first + i;
-                for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
-                    int j = (int)(H.inad_col[e] - L.first);
-                    L.near_entry[L.find(i, j)] = e - H.inad_ptr[L.first];
-                }
-            }
-        }
+        if (l == H.d) leaf_entries(H, L);
+        else L.near_entry.assign(L.nblocks(), -1);
         // fill carried to the parent level: parents of fill pairs
         carried.clear();
         for (int i = 0; i < L.cnt; ++i)
@@ -264,26 +296,16 @@ void build_plan(const HostStructure& H, Plan& P) {
         carried.erase(std::unique(carried.begin(), carried.end()), carried.end());
         P.levels.push_back(std::move(L));
     }
-    // the level holding the dense top matrix: t-1 (or the leaves if nothing is
-    // admissible, in which case no level is skeletonised)
+    // the last level: dense top matrices only (t-1, or the leaves when no level is
+    // skeletonised)
     int lt = P.top < 0 ? H.d : P.top - 1;
     LevelStruct T;
+    set_state(T, lt);
     near_graph(H, lt, T);
     colour_level(T);
-    if (P.top < 0) {
-        block_list(T, {});
-        for (int i = 0; i < T.cnt; ++i)
-            for (int b = T.bptr[i]; b < T.bptr[i + 1]; ++b) T.near_entry.push_back(-1);
-        for (int i = 0; i < T.cnt; ++i) {
-            int64_t g = T.first + i;
-            for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
-                int j = (int)(H.inad_col[e] - T.first);
-                T.near_entry[T.find(i, j)] = e - H.inad_ptr[T.first];
-            }
-        }
-    } else {
-        block_list(T, carried);
-    }
+    block_list(T, P.top < 0 ? std::vector<std::pair<int, int>>{} : carried);
+    if (P.top < 0) leaf_entries(H, T);
+    else T.near_entry.assign(T.nblocks(), -1);
     P.toplev = std::move(T);
     // close lists: level l -> l-1 (parent of the last skeletonised level is toplev)
     for (size_t a = 0; a < P.levels.size(); ++a) {

@@ -148,12 +148,12 @@ s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n, const int* __r
 }
 
 // diagonal solve with the redundant block: x_{i_R} <- D_RR^-1 x_{i_R} (the explicit
-// inverse formed by the factorisation), one block per box
+// inverse formed by the factorisation), one block per skeletonised box
 template <class T>
-__global__ void s_diag(const int* __restrict__ n, const int* __restrict__ kt, const T* __restrict__ DI,
-                       const int64_t* __restrict__ DI_off, const int64_t* __restrict__ voff,
-                       T* __restrict__ x, int nrhs) {
-    const int i = blockIdx.x;
+__global__ void s_diag(const int* __restrict__ boxes, const int* __restrict__ n, const int* __restrict__ kt,
+                       const T* __restrict__ DI, const int64_t* __restrict__ DI_off,
+                       const int64_t* __restrict__ voff, T* __restrict__ x, int nrhs) {
+    const int i = boxes[blockIdx.x];
     const int ni = n[i], r = ni - kt[i];
     if (r <= 0) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -191,25 +191,37 @@ __global__ void s_sweep(const int* __restrict__ cn, const int* __restrict__ ckt,
     }
 }
 
-// top level: gather into a float64 dense vector, solve with L_t U_t, scatter back
+// top boxes of one level: gather into / scatter from their system's float64 dense
+// vector (system z at sys_xt[z]*nrhs, column-major nt_z x nrhs)
 template <class T>
-__global__ void s_top_io(const int* __restrict__ n, const int64_t* __restrict__ voff,
-                         const int64_t* __restrict__ toff, T* __restrict__ x, double* __restrict__ xt,
-                         int64_t nt, int nrhs, int to_dense) {
-    const int p = blockIdx.x;
+__global__ void s_top_io(const int* __restrict__ boxes, const int* __restrict__ n,
+                         const int64_t* __restrict__ voff, const int64_t* __restrict__ ttoff,
+                         const int* __restrict__ tsys, const TopSys* __restrict__ tops,
+                         const int64_t* __restrict__ sys_xt, T* __restrict__ x, double* __restrict__ xt,
+                         int nrhs, int to_dense) {
+    const int p = boxes[blockIdx.x];
     const int np = n[p];
+    const int z = tsys[p];
+    const int64_t nt = tops[z].nt;
     T* xp = x + voff[p] * nrhs;
+    double* xz = xt + sys_xt[z] * nrhs + ttoff[p];
     for (int e = threadIdx.x; e < np * nrhs; e += blockDim.x) {
         const int a = e % np, c = e / np;
-        double* d = xt + toff[p] + a + (int64_t)c * nt;
+        double* d = xz + a + (int64_t)c * nt;
         if (to_dense) *d = (double)xp[e];
         else xp[e] = (T)*d;
     }
 }
 
-__global__ void s_top_solve(const double* __restrict__ LU, const int* __restrict__ piv, int64_t nt,
-                            double* __restrict__ xt) {
-    double* x = xt + (int64_t)blockIdx.x * nt;
+// L_t U_t solve of every system's top matrix (blockIdx.x = column, blockIdx.y = system)
+__global__ void s_top_solve(const TopSys* __restrict__ tops, const int64_t* __restrict__ sys_xt,
+                            double* __restrict__ xt, int nrhs) {
+    const TopSys ts = tops[blockIdx.y];
+    const int64_t nt = ts.nt;
+    if (nt == 0) return;
+    const double* LU = ts.A;
+    const int* piv = ts.piv;
+    double* x = xt + sys_xt[blockIdx.y] * nrhs + (int64_t)blockIdx.x * nt;
     const int tid = threadIdx.x;
     if (tid == 0)
         for (int64_t j = 0; j < nt; ++j) {
@@ -299,7 +311,7 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         LevelRT& L = lv[a];
         const LevelStruct& S = *L.S;
         int nmax = 1;
-        for (int v : L.n) nmax = std::max(nmax, v);
+        for (int i : S.skel_boxes) nmax = std::max(nmax, L.n[i]);
         const int qsm = nmax * nrhs * (int)sizeof(T);
         for (int c = 0; c < S.ncolour; ++c) {
             const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;
@@ -318,29 +330,40 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
                 count_launch();
             }
         }
-        s_diag<T><<<L.cnt, 256, nmax * nrhs * (int)sizeof(T), s>>>(L.d_n.as<int>(), L.d_kt.as<int>(),
-                                                                 L.DI.as<T>(), L.d_Q_off.as<int64_t>(),
-                                                                 L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
-        count_launch();
+        if (!S.skel_boxes.empty()) {
+            s_diag<T><<<(unsigned)S.skel_boxes.size(), 256, nmax * nrhs * (int)sizeof(T), s>>>(
+                L.d_skel_boxes.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(), L.DI.as<T>(),
+                L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
+            count_launch();
+        }
         LevelRT& Pn = lv[a + 1];
         s_sweep<T><<<Pn.cnt, 256, 0, s>>>(L.d_n.as<int>(), L.d_kt.as<int>(), L.d_voff.as<int64_t>(),
                                           vec[a].as<T>(), Pn.d_voff.as<int64_t>(), vec[a + 1].as<T>(),
                                           nrhs, 1);
         count_launch();
     }
-    // top
-    LevelRT& Tl = lv[nl];
+    // dense top solves of every system (their boxes sit at the levels where each
+    // system's skeletonisation ended)
     if (nt > 0) {
         DevBuf xt;
         xt.alloc(nt * nrhs * sizeof(double), s);
-        s_top_io<T><<<Tl.cnt, 256, 0, s>>>(Tl.d_n.as<int>(), Tl.d_voff.as<int64_t>(), d_toff.as<int64_t>(),
-                                           vec[nl].as<T>(), xt.as<double>(), nt, nrhs, 1);
-        count_launch();
-        s_top_solve<<<nrhs, 1024, 0, s>>>(Dt.as<double>(), tpiv.as<int>(), nt, xt.as<double>());
-        count_launch();
-        s_top_io<T><<<Tl.cnt, 256, 0, s>>>(Tl.d_n.as<int>(), Tl.d_voff.as<int64_t>(), d_toff.as<int64_t>(),
-                                           vec[nl].as<T>(), xt.as<double>(), nt, nrhs, 0);
-        count_launch();
+        for (int dir = 1; dir >= 0; --dir) {
+            if (dir == 0) {
+                s_top_solve<<<dim3(nrhs, (unsigned)tops.size()), 1024, 0, s>>>(
+                    d_tops.as<TopSys>(), d_sys_xt.as<int64_t>(), xt.as<double>(), nrhs);
+                count_launch();
+            }
+            for (size_t a = 0; a <= nl; ++a) {
+                LevelRT& L = lv[a];
+                const int ntb = (int)L.S->top_boxes.size();
+                if (!ntb) continue;
+                s_top_io<T><<<ntb, 256, 0, s>>>(L.d_top_boxes.as<int>(), L.d_n.as<int>(), L.d_voff.as<int64_t>(),
+                                                L.d_ttoff.as<int64_t>(), L.d_tsys.as<int>(), d_tops.as<TopSys>(),
+                                                d_sys_xt.as<int64_t>(), vec[a].as<T>(), xt.as<double>(), nrhs,
+                                                dir);
+                count_launch();
+            }
+        }
     }
     // backward
     for (size_t a = nl; a-- > 0;) {
@@ -353,7 +376,7 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         count_launch();
 
         int nmax = 1;
-        for (int v : L.n) nmax = std::max(nmax, v);
+        for (int i : S.skel_boxes) nmax = std::max(nmax, L.n[i]);
         const int qsm = nmax * nrhs * (int)sizeof(T);
         for (int c = S.ncolour - 1; c >= 0; --c) {
             const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;

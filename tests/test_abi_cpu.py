@@ -86,3 +86,55 @@ def test_descriptor_validation_errors():
     # a null descriptor
     rc = binding.lib().h2_plan_query(None, 0, None, None, None, None, None, None)
     assert rc == -1
+
+
+def _small_batch():
+    from h2gen import make_batch
+    from conftest import problem as pr
+    batch = make_batch("gauss3d", nsys=4, nmin=300, nmax=3000, leaf=32)
+    # plus one system with no admissible block (its top matrix is its leaf near field)
+    return [pb.A for pb in batch] + [pr("cov2d", n=256, leaf=16, eta=1e-6).A]
+
+
+def test_uneven_sizes_are_log_uniform_and_seeded():
+    from h2gen import uneven_sizes
+    n = uneven_sizes()
+    assert n == uneven_sizes() and len(n) == 64
+    assert min(n) >= 2048 and max(n) <= 131072
+    # log-uniform: about half the systems below the geometric mean sqrt(2048 * 131072)
+    assert 20 <= sum(v < 16384 for v in n) <= 44
+
+
+def test_batch_plan_is_the_union_of_the_single_plans():
+    """Forest levels aligned by height: every system's boxes, colours and block rows at
+    forest level a equal its own plan at level a (shifted by its box offset); its top
+    boxes sit at the level after its last skeletonised one; boxes above are inert."""
+    from paper_2509_11152_b300 import h2_plan_query, h2_plan_query_batch
+    As = _small_batch()
+    depths = [A.depth for A in As]
+    assert len(set(depths)) >= 3                    # genuinely uneven
+    nlev = [0 if A.top_level() is None else A.depth - A.top_level() + 1 for A in As]
+    for a in range(max(nlev) + 1):
+        q = h2_plan_query_batch(As, a)
+        for z, A in enumerate(As):
+            boxes = np.flatnonzero(q["system"] == z)
+            assert len(boxes) == 1 << (A.depth - a) if a <= A.depth else len(boxes) == 0
+            if not len(boxes):
+                continue
+            assert np.array_equal(boxes, np.arange(boxes[0], boxes[0] + len(boxes)))
+            st_ = q["state"][boxes]
+            rows = [q["col"][q["row_ptr"][i]:q["row_ptr"][i + 1]] - boxes[0] for i in boxes]
+            kinds = [q["kind"][q["row_ptr"][i]:q["row_ptr"][i + 1]] for i in boxes]
+            if a < nlev[z]:
+                assert (st_ == 1).all()
+                s1 = h2_plan_query(A, a)
+                assert np.array_equal(q["colour"][boxes], s1["colour"])
+                for i, (r, k) in enumerate(zip(rows, kinds)):
+                    lo, hi = s1["row_ptr"][i], s1["row_ptr"][i + 1]
+                    assert np.array_equal(r, s1["col"][lo:hi]) and np.array_equal(k, s1["kind"][lo:hi])
+            elif a == nlev[z]:
+                assert (st_ == 2).all() and (q["colour"][boxes] == -1).all()
+                for r, k in zip(rows, kinds):          # dense top matrix: all pairs near
+                    assert np.array_equal(r, np.arange(len(boxes))) and (k == 0).all()
+            else:
+                assert (st_ == 0).all() and all(len(r) == 0 for r in rows)
