@@ -5,6 +5,10 @@ One step = factorise the H^2 matrix in float32 (float64 top level) and solve wit
 float64 iterative refinement until the normwise backward error
 ||Ax-b|| / (||A|| ||x||) <= 1e-10, on the 1,048,576-point Fibonacci-sphere problem
 (kernel 1/(4 pi r), leaf 128, eta 1, eps_lu 1e-5, one N(0,1) right-hand side).
+``--workload uneven`` instead runs the uneven batch: independent Gaussian-kernel
+systems (3D, leaf 64, eta 1, eps_lu 1e-6, 4 right-hand sides each, sizes
+log-uniform in [--nmin, --nmax]) factorised and refined together as one forest;
+with several GPUs the systems are split over the ranks (LPT by size).
 
 Prints one JSON line (rank 0).  ``value`` is the device time of a step with the
 matrix and right-hand side resident in HBM; ``e2e`` repeats the step through the
@@ -45,6 +49,9 @@ def _args():
     p.add_argument("--fp64-arm", type=int, default=1, help="also time the float64 factor arm once")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
+    p.add_argument("--nsys", type=int, default=64, help="uneven batch: number of systems")
+    p.add_argument("--nmin", type=int, default=2048, help="uneven batch: smallest system")
+    p.add_argument("--nmax", type=int, default=16384, help="uneven batch: largest system")
     p.add_argument("--matrix-cache", default="", help="load the H^2 matrix from this .npz if it exists, "
                    "else build and save it there (lets a profiler run skip the construction)")
     return p.parse_args()
@@ -155,6 +162,23 @@ def _problem(args, device):
     return pb
 
 
+def _problems(args, device, rank, ws):
+    """(problems of this rank, description) for the chosen workload."""
+    if args.workload != "uneven":
+        pb = _problem(args, device)
+        w = pb.workload
+        return [pb], f"{w.name} N={pb.A.n} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs}"
+    from h2gen import make_problem, uneven_sizes
+    from paper_2509_11152_b300.shard import lpt_partition
+    sizes = uneven_sizes(args.nsys, args.nmin, args.nmax)
+    mine = lpt_partition(sizes, ws)[rank]
+    pbs = [make_problem("gauss3d", device=device, n=sizes[s], seed=s) for s in mine]
+    w = pbs[0].workload
+    return pbs, (f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}] "
+                 f"(total {sum(sizes)}; this rank {len(mine)} systems, {sum(sizes[s] for s in mine)} points), "
+                 f"leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs} each")
+
+
 def _rhs(n, nrhs, device):
     import torch
     g = torch.Generator(device="cpu").manual_seed(0)
@@ -204,22 +228,28 @@ def _cpu_baseline(workload: str, n_full: int, n_sample: int) -> dict:
 def run_reference(args, dist, rank, ws):
     if rank != 0:
         return
-    from h2gen import WORKLOADS
-    n_full = args.n or WORKLOADS[args.workload].n
-    n_sample = min(n_full, 16384)
+    from h2gen import WORKLOADS, uneven_sizes
+    if args.workload == "uneven":
+        family, n_full, n_sample = "gauss3d", sum(uneven_sizes(args.nsys, args.nmin, args.nmax)), 4096
+        wdesc = f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}]"
+    else:
+        family = args.workload
+        n_full = args.n or WORKLOADS[args.workload].n
+        n_sample = min(n_full, 16384)
+        wdesc = f"{args.workload} N={n_full}"
     for _ in range(args.warmup):
-        _oracle_sample(args.workload, min(n_sample, 4096))
+        _oracle_sample(family, min(n_sample, 4096))
     times = []
     info = None
     for _ in range(args.steps):
-        sec, ns, it, berr = _oracle_sample(args.workload, n_sample)
+        sec, ns, it, berr = _oracle_sample(family, n_sample)
         times.append(sec * n_full / ns)
         info = (sec, ns, it, berr)
     v = statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload} N={n_full}", "precision": "float64 oracle"},
+            "config": {"workload": wdesc, "precision": "float64 oracle"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
                              "sample": f"each step: oracle factor + refined solve at N={info[1]} "
                                        f"({info[0]:.1f} s), scaled linearly to N={n_full}"},
@@ -238,19 +268,22 @@ def run_ours(args, dist, rank, ws):
     dev_index = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev_index)
     t0 = time.perf_counter()
-    pb = _problem(args, "cuda")
-    A = pb.A
-    w = pb.workload
+    pbs, desc = _problems(args, "cuda", rank, ws)
+    As = [pb.A for pb in pbs]
+    norms = [pb.norm_a for pb in pbs]
+    norm_arg = norms[0] if len(norms) == 1 else norms
+    w = pbs[0].workload
     nrhs = w.nrhs
+    n_tot = sum(A.n for A in As)
     setup_s = time.perf_counter() - t0
-    M = h.h2_matrix_create(A)
+    M = h.h2_matrix_create_batch(As)
     torch.cuda.empty_cache()              # construction temporaries held by torch's cache
-    b = h.colmajor(_rhs(A.n, nrhs, "cuda"))
+    b = h.colmajor(_rhs(n_tot, nrhs, "cuda"))
     x = h.colmajor(torch.zeros_like(b))
     stream = torch.cuda.current_stream().cuda_stream
 
     def step(prec, flags=0):
-        Z = h.h2_factor_create(M, w.tol, pb.norm_a, prec, stream=stream, flags=flags)
+        Z = h.h2_factor_create(M, w.tol, norm_arg, prec, stream=stream, flags=flags)
         x.zero_()
         it, berr, ok = h.h2_refine_solve(Z, M, b, x, BERR_TOL, MAXIT)
         return Z, it, berr, ok
@@ -286,7 +319,8 @@ def run_ours(args, dist, rank, ws):
     clk = clocks.stop()
     t_step = e0.elapsed_time(e1) / 1e3 / args.steps
     t_step = _max_over_ranks(dist, t_step)
-    value = t_step / ws
+    uneven = args.workload == "uneven"
+    value = t_step if uneven else t_step / ws        # batch: all ranks share one batch
 
     # dominant factorisation kernel and its roofline
     peaks, peak_kind = _peaks()
@@ -314,12 +348,14 @@ def run_ours(args, dist, rank, ws):
 
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{w.name} N={A.n} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={nrhs}",
+            "scaling": "strong" if uneven else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc,
                        "precision": "float32 factor/solve, float64 top LU + refinement",
-                       "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (matrix "
-                       f"{A.nbytes() / 1e9:.1f} GB)", "setup_s": round(setup_s, 1),
-                       "csp": pb.stats["csp"], "kmax": pb.stats["kmax"]},
+                       "parallelism": (f"systems split over {ws} GPUs (LPT)" if uneven else f"replicas x{ws}"),
+                       "l2": "inputs larger than L2 (matrix "
+                       f"{sum(A.nbytes() for A in As) / 1e9:.1f} GB)", "setup_s": round(setup_s, 1),
+                       "csp": max(pb.stats["csp"] for pb in pbs), "kmax": max(pb.stats["kmax"] for pb in pbs)},
             "refinement": {"iters": [r[0] for r in results], "berr": [r[1] for r in results],
                            "converged": all(r[2] for r in results)},
             "phase_ms": {k: round(v, 2) for k, v in last_stats["phase_ms"].items()},
@@ -341,9 +377,8 @@ def run_ours(args, dist, rank, ws):
     # end to end through the C-ABI with host buffers
     if args.e2e_steps > 0:
         from dataclasses import replace
-        host = {k: getattr(A, k).cpu().pin_memory() for k in ("U", "E", "S", "D")}
+        Ahs = [replace(A, **{k: getattr(A, k).cpu().pin_memory() for k in ("U", "E", "S", "D")}) for A in As]
         bh = b.cpu().t().contiguous().pin_memory().t()           # column-major, pinned
-        Ah = replace(A, **host)
         del M
         torch.cuda.synchronize()
         e2e = []
@@ -351,21 +386,22 @@ def run_ours(args, dist, rank, ws):
             xh = torch.zeros_like(bh)
             torch.cuda.synchronize()
             f0 = time.perf_counter()
-            Mh = h.h2_matrix_create(Ah, stream=stream)
-            Z = h.h2_factor_create(Mh, w.tol, pb.norm_a, h.H2_PREC_FP32, stream=stream)
+            Mh = h.h2_matrix_create_batch(Ahs, stream=stream)
+            Z = h.h2_factor_create(Mh, w.tol, norm_arg, h.H2_PREC_FP32, stream=stream)
             it, berr, ok = h.h2_refine_solve(Z, Mh, bh, xh, BERR_TOL, MAXIT)
             torch.cuda.synchronize()
             e2e.append(time.perf_counter() - f0)
             del Z, Mh
-        idx_bytes = sum(np.asarray(getattr(A, k)).nbytes for k in
+        idx_bytes = sum(np.asarray(getattr(A, k)).nbytes for A in As for k in
                         ("node_start", "node_size", "rank", "U_off", "E_off", "adm_ptr", "adm_col", "S_off",
                          "inad_ptr", "inad_col", "D_off"))
-        h2d = A.nbytes() + idx_bytes + bh.numel() * 8
-        line["e2e"] = {"value": _max_over_ranks(dist, statistics.mean(e2e)) / ws, "unit": "s",
+        h2d = sum(A.nbytes() for A in As) + idx_bytes + bh.numel() * 8
+        e2e_v = _max_over_ranks(dist, statistics.mean(e2e))
+        line["e2e"] = {"value": e2e_v if uneven else e2e_v / ws, "unit": "s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(bh.numel() * 8)}
 
     if args.cpu_baseline and rank == 0 and ws == 1:
-        line["cpu_baseline"] = _cpu_baseline(w.name, A.n, min(A.n, 16384))
+        line["cpu_baseline"] = _cpu_baseline(w.name, n_tot, min(n_tot, 4096 if uneven else 16384))
     if rank == 0:
         print(json.dumps(line), flush=True)
 
