@@ -285,61 +285,61 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
         dr.alloc(vbytes, s);
         const HostStructure& HS = A->m.H;
         const int nseg = HS.nsys;
-        dn.alloc(std::max(2 * nseg, 1) * nrhs * sizeof(double), s);
+        dn.alloc(2 * (size_t)nseg * nrhs * sizeof(double), s);
         const int64_t* seg = A->m.d_sys_voff.as<int64_t>();
         H2_CUDA_CHECK(cudaMemcpy2DAsync(xd, lx * sizeof(double), bd, lb * sizeof(double), n * sizeof(double),
                                         nrhs, cudaMemcpyDeviceToDevice, s));
         F.solve_dev(xd, nrhs, lx);
         const std::vector<double>& nA = F.norm_sys;
-        std::vector<double> h(std::max(2 * nseg, 1) * nrhs), xscale(nrhs);
-        // backward error of x (max over systems and columns of ||r|| / (||A_s|| ||x||));
-        // r = b - A x is left in dr.  xscale[c] = min over systems of ||A_s|| ||x_s,c||.
+        // channels q = c * nseg + z: column c of system z
+        const int nq = nrhs * nseg;
+        std::vector<double> h(2 * (size_t)nq), xscale(nq);
+        // backward error of x (max over channels of ||r_q|| / (||A_z|| ||x_q||)); r = b - A x
+        // is left in dr, and xscale[q] = ||A_z|| ||x_q||.
         auto residual = [&]() -> double {
             matvec_dev(A->m, nrhs, xd, lx, dy.as<double>(), n, s);
             residual_dev(bd, lb, dy.as<double>(), n, dr.as<double>(), n, n, nrhs, s);
             segnorm2_dev(dr.as<double>(), n, seg, nseg, nrhs, dn.as<double>(), s);
-            segnorm2_dev(xd, lx, seg, nseg, nrhs, dn.as<double>() + (size_t)nseg * nrhs, s);
-            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, 2 * (size_t)nseg * nrhs * sizeof(double),
+            segnorm2_dev(xd, lx, seg, nseg, nrhs, dn.as<double>() + nq, s);
+            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, 2 * (size_t)nq * sizeof(double),
                                           cudaMemcpyDeviceToHost, s));
             H2_CUDA_CHECK(cudaStreamSynchronize(s));
             double be = 0;
-            for (int c = 0; c < nrhs; ++c) {
-                xscale[c] = INFINITY;
-                for (int z = 0; z < nseg; ++z) {
-                    const double r2 = h[(size_t)c * nseg + z], x2 = h[(size_t)nseg * nrhs + (size_t)c * nseg + z];
-                    const double xs = nA[z] * std::sqrt(x2);
-                    const double e = xs > 0 ? std::sqrt(r2) / xs : (r2 > 0 ? INFINITY : 0.0);
-                    be = std::max(be, e);
-                    xscale[c] = std::min(xscale[c], xs);
-                }
+            for (int q = 0; q < nq; ++q) {
+                const double r2 = h[q], x2 = h[nq + q];
+                xscale[q] = nA[q % nseg] * std::sqrt(x2);
+                const double e = xscale[q] > 0 ? std::sqrt(r2) / xscale[q] : (r2 > 0 ? INFINITY : 0.0);
+                be = std::max(be, e);
             }
             H2_REQUIRE(std::isfinite(be), H2_ERR_NONFINITE, "non-finite residual in refinement");
             return be;
         };
         // One restarted-GMRES cycle on A d = r, right-preconditioned by the factor
         // (A M^-1 u = r, d = M^-1 u), classical Gram-Schmidt applied twice; float64.
-        // Used once plain correction steps stop contracting (eps_lu * cond(A) near 1).
+        // Every channel (right-hand side of one system) has its own Krylov basis and
+        // Hessenberg matrix, so a batch converges like its slowest system.  Used once
+        // plain correction steps stop contracting (eps_lu * cond(A) near 1).
         DevBuf Vb, hb, tb;
         auto gmres_cycle = [&](int m, double target_rel) -> int {
             Vb.alloc((size_t)(m + 1) * vbytes, s);
-            hb.alloc((size_t)(m + 1) * nrhs * sizeof(double), s);
+            hb.alloc((size_t)(m + 1) * nq * sizeof(double), s);
             tb.alloc(vbytes, s);
             double* V = Vb.as<double>();
             double* hd = hb.as<double>();
-            std::vector<double> beta(nrhs), sc(nrhs);
-            colnorm2_dev(dr.as<double>(), n, n, nrhs, dn.as<double>(), s);
-            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+            std::vector<double> beta(nq), sc(nq);
+            segnorm2_dev(dr.as<double>(), n, seg, nseg, nrhs, dn.as<double>(), s);
+            H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, s));
             H2_CUDA_CHECK(cudaStreamSynchronize(s));
-            for (int c = 0; c < nrhs; ++c) {
-                beta[c] = std::sqrt(h[c]);
-                sc[c] = beta[c] > 0 ? 1.0 / beta[c] : 0.0;
+            for (int q = 0; q < nq; ++q) {
+                beta[q] = std::sqrt(h[q]);
+                sc[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
             }
-            H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-            scale_dev(dr.as<double>(), dn.as<double>(), n, nrhs, V, s);
-            std::vector<double> H((size_t)(m + 1) * m * nrhs, 0.0), g((size_t)(m + 1) * nrhs, 0.0),
-                cs((size_t)m * nrhs), sn((size_t)m * nrhs), hh((size_t)(m + 1) * nrhs), h2((size_t)(m + 1) * nrhs);
-            for (int c = 0; c < nrhs; ++c) g[c] = beta[c];
-            auto Hc = [&](int row, int col, int c) -> double& { return H[((size_t)col * (m + 1) + row) * nrhs + c]; };
+            H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nq * sizeof(double), cudaMemcpyHostToDevice, s));
+            scale_dev(dr.as<double>(), dn.as<double>(), n, nrhs, seg, nseg, V, s);
+            std::vector<double> H((size_t)(m + 1) * m * nq, 0.0), g((size_t)(m + 1) * nq, 0.0),
+                cs((size_t)m * nq), sn((size_t)m * nq), hh((size_t)(m + 1) * nq), h2((size_t)(m + 1) * nq);
+            for (int q = 0; q < nq; ++q) g[q] = beta[q];
+            auto Hc = [&](int row, int col, int q) -> double& { return H[((size_t)col * (m + 1) + row) * nq + q]; };
             int k = 0;
             for (int j = 0; j < m; ++j) {
                 double* vj = V + (size_t)j * n * nrhs;
@@ -348,59 +348,59 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
                 F.solve_dev(tb.as<double>(), nrhs, n);                       // M^-1 v_j
                 matvec_dev(A->m, nrhs, tb.as<double>(), n, w, n, s);          // A M^-1 v_j
                 for (int pass = 0; pass < 2; ++pass) {
-                    multidot_dev(V, w, j + 1, n, nrhs, hd, s);
-                    H2_CUDA_CHECK(cudaMemcpyAsync(h2.data(), hd, (size_t)(j + 1) * nrhs * sizeof(double),
+                    multidot_dev(V, w, j + 1, n, nrhs, seg, nseg, hd, s);
+                    H2_CUDA_CHECK(cudaMemcpyAsync(h2.data(), hd, (size_t)(j + 1) * nq * sizeof(double),
                                                   cudaMemcpyDeviceToHost, s));
                     H2_CUDA_CHECK(cudaStreamSynchronize(s));
-                    for (size_t q = 0; q < (size_t)(j + 1) * nrhs; ++q) {
+                    for (size_t q = 0; q < (size_t)(j + 1) * nq; ++q) {
                         if (pass == 0) hh[q] = h2[q]; else hh[q] += h2[q];
                         h2[q] = -h2[q];
                     }
-                    H2_CUDA_CHECK(cudaMemcpyAsync(hd, h2.data(), (size_t)(j + 1) * nrhs * sizeof(double),
+                    H2_CUDA_CHECK(cudaMemcpyAsync(hd, h2.data(), (size_t)(j + 1) * nq * sizeof(double),
                                                   cudaMemcpyHostToDevice, s));
-                    combine_dev(V, hd, j + 1, n, nrhs, w, s);
+                    combine_dev(V, hd, j + 1, n, nrhs, seg, nseg, w, s);
                 }
-                colnorm2_dev(w, n, n, nrhs, dn.as<double>(), s);
-                H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+                segnorm2_dev(w, n, seg, nseg, nrhs, dn.as<double>(), s);
+                H2_CUDA_CHECK(cudaMemcpyAsync(h.data(), dn.ptr, nq * sizeof(double), cudaMemcpyDeviceToHost, s));
                 H2_CUDA_CHECK(cudaStreamSynchronize(s));
                 bool done = true;
-                for (int c = 0; c < nrhs; ++c) {
-                    const double hn = std::sqrt(h[c]);
-                    sc[c] = hn > 0 ? 1.0 / hn : 0.0;
-                    for (int i = 0; i <= j; ++i) Hc(i, j, c) = hh[(size_t)i * nrhs + c];
-                    Hc(j + 1, j, c) = hn;
+                for (int q = 0; q < nq; ++q) {
+                    const double hn = std::sqrt(h[q]);
+                    sc[q] = hn > 0 ? 1.0 / hn : 0.0;
+                    for (int i = 0; i <= j; ++i) Hc(i, j, q) = hh[(size_t)i * nq + q];
+                    Hc(j + 1, j, q) = hn;
                     for (int i = 0; i < j; ++i) {                            // previous rotations
-                        const double a0 = Hc(i, j, c), a1 = Hc(i + 1, j, c);
-                        Hc(i, j, c) = cs[(size_t)i * nrhs + c] * a0 + sn[(size_t)i * nrhs + c] * a1;
-                        Hc(i + 1, j, c) = -sn[(size_t)i * nrhs + c] * a0 + cs[(size_t)i * nrhs + c] * a1;
+                        const double a0 = Hc(i, j, q), a1 = Hc(i + 1, j, q);
+                        Hc(i, j, q) = cs[(size_t)i * nq + q] * a0 + sn[(size_t)i * nq + q] * a1;
+                        Hc(i + 1, j, q) = -sn[(size_t)i * nq + q] * a0 + cs[(size_t)i * nq + q] * a1;
                     }
-                    const double a0 = Hc(j, j, c), a1 = Hc(j + 1, j, c);
+                    const double a0 = Hc(j, j, q), a1 = Hc(j + 1, j, q);
                     const double rr = std::hypot(a0, a1);
                     const double cj = rr > 0 ? a0 / rr : 1.0, sj = rr > 0 ? a1 / rr : 0.0;
-                    cs[(size_t)j * nrhs + c] = cj;
-                    sn[(size_t)j * nrhs + c] = sj;
-                    Hc(j, j, c) = rr;
-                    Hc(j + 1, j, c) = 0.0;
-                    g[(size_t)(j + 1) * nrhs + c] = -sj * g[(size_t)j * nrhs + c];
-                    g[(size_t)j * nrhs + c] = cj * g[(size_t)j * nrhs + c];
-                    if (std::fabs(g[(size_t)(j + 1) * nrhs + c]) > target_rel * xscale[c]) done = false;
+                    cs[(size_t)j * nq + q] = cj;
+                    sn[(size_t)j * nq + q] = sj;
+                    Hc(j, j, q) = rr;
+                    Hc(j + 1, j, q) = 0.0;
+                    g[(size_t)(j + 1) * nq + q] = -sj * g[(size_t)j * nq + q];
+                    g[(size_t)j * nq + q] = cj * g[(size_t)j * nq + q];
+                    if (std::fabs(g[(size_t)(j + 1) * nq + q]) > target_rel * xscale[q]) done = false;
                 }
-                H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-                scale_dev(w, dn.as<double>(), n, nrhs, w, s);
+                H2_CUDA_CHECK(cudaMemcpyAsync(dn.ptr, sc.data(), nq * sizeof(double), cudaMemcpyHostToDevice, s));
+                scale_dev(w, dn.as<double>(), n, nrhs, seg, nseg, w, s);
                 k = j + 1;
                 if (done) break;
             }
-            // y = R^-1 g per column; u = V y; d = M^-1 u (left in dr)
-            std::vector<double> y((size_t)k * nrhs, 0.0);
-            for (int c = 0; c < nrhs; ++c)
+            // y = R^-1 g per channel; u = V y; d = M^-1 u (left in dr)
+            std::vector<double> y((size_t)k * nq, 0.0);
+            for (int q = 0; q < nq; ++q)
                 for (int i = k - 1; i >= 0; --i) {
-                    double t = g[(size_t)i * nrhs + c];
-                    for (int q = i + 1; q < k; ++q) t -= Hc(i, q, c) * y[(size_t)q * nrhs + c];
-                    y[(size_t)i * nrhs + c] = Hc(i, i, c) != 0 ? t / Hc(i, i, c) : 0.0;
+                    double t = g[(size_t)i * nq + q];
+                    for (int p = i + 1; p < k; ++p) t -= Hc(i, p, q) * y[(size_t)p * nq + q];
+                    y[(size_t)i * nq + q] = Hc(i, i, q) != 0 ? t / Hc(i, i, q) : 0.0;
                 }
             H2_CUDA_CHECK(cudaMemcpyAsync(hd, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
             H2_CUDA_CHECK(cudaMemsetAsync(dr.ptr, 0, vbytes, s));
-            combine_dev(V, hd, k, n, nrhs, dr.as<double>(), s);
+            combine_dev(V, hd, k, n, nrhs, seg, nseg, dr.as<double>(), s);
             F.solve_dev(dr.as<double>(), nrhs, n);
             return k;
         };

@@ -137,77 +137,74 @@ __global__ void v_add(double* __restrict__ x, int64_t ldx, const double* __restr
     x[a + c * ldx] += d[a + c * ldd];
 }
 
-// out[c] = ||v_c||^2 (one block per column)
-__global__ void v_colnorm2(const double* __restrict__ v, int64_t ldv, int64_t n, double* __restrict__ out) {
-    __shared__ double red[32];
-    const int c = blockIdx.x;
-    double acc = 0;
-    for (int64_t a = threadIdx.x; a < n; a += blockDim.x) {
-        const double t = v[a + c * ldv];
-        acc += t * t;
+// Segments: the rows of system z are seg[z] .. seg[z+1]-1; channel q = c * nseg + z is
+// column c restricted to system z (each channel is an independent Krylov space).
+__device__ inline int seg_of(const int64_t* __restrict__ seg, int nseg, int64_t a) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg[mid] <= a) lo = mid; else hi = mid - 1;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        out[c] = s;
-    }
+    return lo;
 }
 
-// h[i*nrhs + c] = <V_i[:, c], w[:, c]> for i < m (V_i = V + i * n * nrhs, ld n); one block
-// per (i, c)
+// h[i*nq + q] = <V_i, w> over channel q (blockIdx: x = i, y = column, z = segment)
 __global__ void v_multidot(const double* __restrict__ V, const double* __restrict__ w, int64_t n, int nrhs,
-                           double* __restrict__ h) {
+                           const int64_t* __restrict__ seg, int nseg, double* __restrict__ h) {
     __shared__ double red[32];
-    const int i = blockIdx.x, c = blockIdx.y;
+    const int i = blockIdx.x, c = blockIdx.y, z = blockIdx.z;
     const double* vi = V + ((int64_t)i * nrhs + c) * n;
     const double* wc = w + (int64_t)c * n;
     double acc = 0;
-    for (int64_t a = threadIdx.x; a < n; a += blockDim.x) acc += vi[a] * wc[a];
+    for (int64_t a = seg[z] + threadIdx.x; a < seg[z + 1]; a += blockDim.x) acc += vi[a] * wc[a];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-        h[(int64_t)i * nrhs + c] = t;
+        h[(int64_t)i * nrhs * nseg + (int64_t)c * nseg + z] = t;
     }
 }
 
-// w[:, c] += sum_{i < m} coef[i*nrhs + c] V_i[:, c]
+// w += sum_{i < m} coef[i*nq + q] V_i, per channel q
 __global__ void v_combine(const double* __restrict__ V, const double* __restrict__ coef, int m, int64_t n,
-                          int nrhs, double* __restrict__ w) {
+                          int nrhs, const int64_t* __restrict__ seg, int nseg, double* __restrict__ w) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * nrhs) return;
     const int64_t a = e % n;
     const int c = (int)(e / n);
+    const int64_t q = (int64_t)c * nseg + seg_of(seg, nseg, a);
+    const int64_t nq = (int64_t)nrhs * nseg;
     double acc = w[e];
-    for (int i = 0; i < m; ++i) acc += coef[(int64_t)i * nrhs + c] * V[((int64_t)i * nrhs + c) * n + a];
+    for (int i = 0; i < m; ++i) acc += coef[i * nq + q] * V[((int64_t)i * nrhs + c) * n + a];
     w[e] = acc;
 }
 
-// y[:, c] = s[c] * x[:, c]
+// y = s[q] x per channel q
 __global__ void v_scale(const double* __restrict__ x, const double* __restrict__ sc, int64_t n, int nrhs,
-                        double* __restrict__ y) {
+                        const int64_t* __restrict__ seg, int nseg, double* __restrict__ y) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * nrhs) return;
-    y[e] = sc[e / n] * x[e];
+    const int64_t a = e % n;
+    y[e] = sc[(e / n) * nseg + seg_of(seg, nseg, a)] * x[e];
 }
 
-void multidot_dev(const double* V, const double* w, int m, int64_t n, int nrhs, double* h, cudaStream_t s) {
-    v_multidot<<<dim3(m, nrhs), 256, 0, s>>>(V, w, n, nrhs, h);
+void multidot_dev(const double* V, const double* w, int m, int64_t n, int nrhs, const int64_t* seg, int nseg,
+                  double* h, cudaStream_t s) {
+    v_multidot<<<dim3(m, nrhs, nseg), 256, 0, s>>>(V, w, n, nrhs, seg, nseg, h);
     count_launch();
 }
 
-void combine_dev(const double* V, const double* coef, int m, int64_t n, int nrhs, double* w, cudaStream_t s) {
-    v_combine<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(V, coef, m, n, nrhs, w);
+void combine_dev(const double* V, const double* coef, int m, int64_t n, int nrhs, const int64_t* seg, int nseg,
+                 double* w, cudaStream_t s) {
+    v_combine<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(V, coef, m, n, nrhs, seg, nseg, w);
     count_launch();
 }
 
-void scale_dev(const double* x, const double* sc, int64_t n, int nrhs, double* y, cudaStream_t s) {
-    v_scale<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(x, sc, n, nrhs, y);
+void scale_dev(const double* x, const double* sc, int64_t n, int nrhs, const int64_t* seg, int nseg, double* y,
+               cudaStream_t s) {
+    v_scale<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(x, sc, n, nrhs, seg, nseg, y);
     count_launch();
 }
 
@@ -247,11 +244,6 @@ __global__ void v_segnorm2(const double* __restrict__ v, int64_t ldv, const int6
 void segnorm2_dev(const double* v, int64_t ldv, const int64_t* seg, int nseg, int nrhs, double* out,
                   cudaStream_t s) {
     v_segnorm2<<<dim3(nseg, nrhs), 256, 0, s>>>(v, ldv, seg, nseg, out);
-    count_launch();
-}
-
-void colnorm2_dev(const double* v, int64_t ldv, int64_t n, int nrhs, double* out, cudaStream_t s) {
-    v_colnorm2<<<nrhs, 256, 0, s>>>(v, ldv, n, out);
     count_launch();
 }
 
