@@ -77,14 +77,25 @@ static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
 }
 
-// Schur tile edge
-template <class T> constexpr int schur_tile() { return 64; }
+// Schur tile: 128 x 64 on the tensor cores (float32 factor), 64 x 64 on the FP64 pipe
+template <class T> constexpr int schur_bm() { return sizeof(T) == 4 ? tc::TBM : 64; }
+template <class T> constexpr int schur_bn() { return sizeof(T) == 4 ? tc::TBN : 64; }
 
-template <class T>
-static void launch_schur(int ntile, cudaStream_t s, const LevelArgs<T>& ar, int c, const int* tb,
+static void launch_schur(int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
                          const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
                          const int* tmn) {
-    k_schur<T><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+    k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+}
+
+static void launch_schur(int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c, const int* tb,
+                         const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
+                         const int* tmn) {
+    static const bool ready = [] {
+        H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
+        return true;
+    }();
+    (void)ready;
+    k_schur_tc<<<ntile, 128, tc::kSmem, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
 }
 
 template <class T>
@@ -96,7 +107,7 @@ template <class T>
 static const SmemLimits<T>& smem_limits() {
     static SmemLimits<T> lim = [] {
         SmemLimits<T> x{};
-        x.basis = raise_smem(k_basis<T>);
+        x.basis = std::min(raise_smem(k_basis<T, false>), raise_smem(k_basis<T, true>));
         x.lu = raise_smem(k_lu<T>);
         x.proj_l = std::min({raise_smem(k_proj<T, 1, false>), raise_smem(k_proj<T, 2, false>),
                              raise_smem(k_proj<T, 4, false>), raise_smem(k_proj<T, 8, false>)});
@@ -433,9 +444,8 @@ void FactorImpl<T>::run_level(size_t a) {
         for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
             const int tb = S.sch_tblk[t];
             const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
-            const int ts = schur_tile<T>();
-            for (int tm = 0; tm * ts < m; ++tm)
-                for (int tn = 0; tn * ts < nn; ++tn) {
+            for (int tm = 0; tm * schur_bm<T>() < m; ++tm)
+                for (int tn = 0; tn * schur_bn<T>() < nn; ++tn) {
                     W.tile_tgt.push_back(t);
                     W.tile_mn.push_back((tm << 16) | tn);
                 }
@@ -522,8 +532,12 @@ void FactorImpl<T>::run_level(size_t a) {
             H2_LAUNCHED();
         }
         kbegin(H2_K_BASIS);
-        k_basis<T><<<nbx, 256, W.smem_basis[c], s>>>(ar, CL, c, scratch.as<T>(), scratch.as<T>(),
-                                                     W.w_in_smem[c]);
+        if (W.nmax[c] <= 128)
+            k_basis<T, false><<<nbx, 256, W.smem_basis[c], s>>>(ar, CL, c, scratch.as<T>(), scratch.as<T>(),
+                                                                W.w_in_smem[c]);
+        else
+            k_basis<T, true><<<nbx, 256, W.smem_basis[c], s>>>(ar, CL, c, scratch.as<T>(), scratch.as<T>(),
+                                                               W.w_in_smem[c]);
         kend();
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
@@ -584,7 +598,7 @@ void FactorImpl<T>::run_level(size_t a) {
         const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
         if (ntile) {
             kbegin(H2_K_SCHUR);
-            launch_schur<T>(ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
+            launch_schur(ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
                             d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
                             d_tile_mn.as<int>() + t0);
             kend();

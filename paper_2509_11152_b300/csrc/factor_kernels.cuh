@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "factor_args.cuh"
+#include "schur_tc.cuh"
 
 namespace h2rs {
 
@@ -215,8 +216,10 @@ __device__ void rfactor_stream(const LevelArgs<T>& a, const ColourLists& L, int 
 //   n-k of them) form Vbar
 //   Householder QR of [V, Vbar]: its Q columns k.. give Vbar orthonormalised against
 //   V and the complement V~perp; Q~ = [V~perp, V, Vbar].
-template <class T>
-__global__ void __launch_bounds__(256)
+// BIG: boxes up to 256 (one CTA per SM: 64 rows per thread in the R-factor); otherwise
+// boxes up to 128, register-capped so that two boxes share an SM.
+template <class T, bool BIG>
+__global__ void __launch_bounds__(256, BIG ? 1 : 2)
 k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
         T* __restrict__ gwork, int w_in_smem) {
     const int slot = blockIdx.x;
@@ -255,60 +258,8 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
         __syncthreads();
         if (n <= 32) rfactor_stream<T, 8>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
         else if (n <= 64) rfactor_stream<T, 16>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
-        else if (n <= 128) rfactor_stream<T, 32>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
-        else if (n <= 256) rfactor_stream<T, 64>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
-        else {
-            // Every step's trailing update gives tpc threads to a column (a power of two,
-            // rows interleaved), so a column's dot product needs log2(tpc) shuffles only.
-            int tpc = 1;
-            while (tpc * 2 <= 16 && tpc * 2 * n <= 256) tpc *= 2;
-            const int cstep = 256 / tpc, part = tid % tpc, cofs = tid / tpc;
-            for (int s = s0; s < s1; ++s) {
-                const int j = L.seg_j[s];
-                const int nj = a.n[j];
-                const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
-                const int64_t yoff = L.seg_yoff[s];
-                for (int r0 = skip; r0 < nj; r0 += CH) {
-                    const int rows = min(CH, nj - r0);
-                    for (int x = tid; x < CH * n; x += blockDim.x) {
-                        const int rr = x % CH, col = x / CH;
-                        C[rr + col * ldc] = rr < rows ? Yt[(yoff + r0 + rr) + (int64_t)col * ld] : T(0);
-                    }
-                    __syncthreads();
-                    for (int jj = 0; jj < n; ++jj) {
-                        const T* cj = C + jj * ldc;
-                        T ss = 0;
-                        for (int r = 0; r < rows; ++r) ss += cj[r] * cj[r];
-                        if (ss == T(0)) continue;                       // uniform
-                        const T x0 = W[(int64_t)jj * ldw + jj];
-                        const T nrm = sqrt(x0 * x0 + ss);
-                        const T beta = x0 > T(0) ? -nrm : nrm;
-                        const T v0 = x0 - beta;
-                        const T tw = -v0 / beta;
-                        const T inv = T(1) / v0;
-                        for (int cb = jj + 1; cb < n; cb += cstep) {    // uniform trip count
-                            const int col = cb + cofs;
-                            const bool act = col < n;
-                            T* cc = C + (act ? col : jj) * ldc;
-                            T d = 0;
-                            for (int r = part; r < rows; r += tpc) d += cj[r] * cc[r];
-                            for (int o = 1; o < tpc; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                            if (act) {
-                                const T w = W[(int64_t)jj * ldw + col] + d * inv;
-                                const T tww = tw * w;
-                                const T f = tww * inv;
-                                for (int r = part; r < rows; r += tpc) cc[r] -= f * cj[r];
-                                if (part == 0) W[(int64_t)jj * ldw + col] -= tww;
-                            }
-                        }
-                        __syncthreads();
-                        if (tid == 0) W[(int64_t)jj * ldw + jj] = beta;
-                    }
-                    __syncthreads();
-                }
-            }
-            __syncthreads();
-        }
+        else if (!BIG || n <= 128) rfactor_stream<T, 32>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
+        else rfactor_stream<T, BIG ? 64 : 32>(a, L, slot, cur, n, Yt, ld, W, ldw, C);   // n <= 256
         __syncthreads();
         // ---------------- one-sided Jacobi on M = R^T (column p of M = row p of R)
         // Round-robin pairs over the active columns, tpp threads per pair (rows
@@ -928,6 +879,49 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
             const int gr = m0 + tx + 16 * u, gc = n0 + ty + 16 * v;
             if (gr < m && gc < nn) Cm[gr + (int64_t)gc * nj] -= acc[u][v];
         }
+}
+
+// Float32 factor: the same target-owned update on the tcgen05 tensor cores (one
+// 128 x 64 target tile per CTA of 128 threads; split-TF32 products with float32-level
+// accuracy, see schur_tc.cuh).  K runs over the contributors in 32-wide slices.
+__global__ void __launch_bounds__(128, 4)
+k_schur_tc(LevelArgs<float> a, int cur, const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
+           const int* __restrict__ c_box, const int* __restrict__ c_ablk, const int* __restrict__ c_kpos,
+           const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn) {
+    extern __shared__ __align__(1024) unsigned char sm_tc[];
+    const int tt = tile_tgt[blockIdx.x];
+    const int mn = tile_mn[blockIdx.x];
+    const int tb = tgt_blk[tt];
+    const int j = a.brow[tb], kb = a.bcol[tb];
+    const int nj = a.n[j], nk = a.n[kb];
+    const int row_lo = (a.colour[j] == cur) ? nj - a.kt[j] : 0;
+    const int col_lo = (a.colour[kb] == cur) ? nk - a.kt[kb] : 0;
+    const int m = nj - row_lo, nn = nk - col_lo;
+    const int m0 = (mn >> 16) * tc::TBM, n0 = (mn & 0xffff) * tc::TBN;
+    if (m0 >= m || n0 >= nn) return;                 // whole block: before any barrier
+    float* C = a.blk + a.blk_off[tb] + row_lo + m0 + (int64_t)(col_lo + n0) * nj;
+    const int mv = min(tc::TBM, m - m0), nv = min(tc::TBN, nn - n0);
+    int c = tgt_ptr[tt];
+    const int cend = tgt_ptr[tt + 1];
+    int k0 = 0;
+    auto next = [&](tc::Slice& sl) -> bool {
+        for (; c < cend; ++c, k0 = 0) {
+            const int i = c_box[c];
+            const int ri = a.n[i] - a.kt[i];
+            if (k0 >= ri) continue;
+            // D_{j, i_R}: m x ri (ld nj); W_U^i columns of the target: ri x nn (ld ri)
+            sl.A = a.blk + a.blk_off[c_ablk[c]] + row_lo + m0 + (int64_t)k0 * nj;
+            sl.lda = nj;
+            sl.B = a.WU + a.WU_off[i] + ((int64_t)a.nbofs[a.nb_ptr[i] + c_kpos[c]] + n0) * ri + k0;
+            sl.ldb = ri;
+            sl.kv = min(tc::TBK, ri - k0);
+            k0 += tc::TBK;
+            return true;
+        }
+        return false;
+    };
+    if (!tc::tile_sub(C, nj, mv, nv, next, sm_tc) && threadIdx.x == 0)
+        dev_fail(a.status, H2_ERR_TIMEOUT, a.level, j);
 }
 
 // ================================================================== level close
