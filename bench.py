@@ -150,6 +150,22 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def _traffic(kernel: str, algorithmic_bytes: float, steps: int):
+    """DRAM bytes per step of ``kernel`` from the committed ncu summary
+    (profiles/traffic.json: DRAM read+write over algorithmic bytes, measured on a
+    smaller case of the same workload family and scaled by the algorithmic bytes of
+    this run), or None when no capture of the current kernel exists."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f).get(kernel)
+    if not t:
+        return None
+    return {"bytes_per_step": t["dram_over_algorithmic"] * algorithmic_bytes,
+            "dram_over_algorithmic": t["dram_over_algorithmic"], "source": t["source"]}
+
+
 def _problem(args, device):
     from h2gen import make_problem
     from h2gen.problems import load_problem, save_problem
@@ -330,21 +346,28 @@ def run_ours(args, dist, rank, ws):
     phase = names.get(dom)
     flops = last_stats["phase_flops"].get(phase, 0.0) if phase else 0.0
     bytes_ = last_stats["phase_bytes"].get(phase, 0.0) if phase else 0.0
-    sm_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    alu = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
     hbm = peaks["hbm_gbs"]
+    if dom == "schur":
+        # split-TF32 tensor-core GEMM (3 TF32 MMAs per float32 product); TF32 peak = the
+        # measured sustained bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25)
+        cpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.1 / 2.25) / 3.0
+        cbound, csrc = "tensor", (" (tensor: 3xTF32 = measured sustained bf16 x 1.1/2.25 / 3)")
+    else:
+        cpeak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+        cbound, csrc = "alu", " (alu: 148 SMs x 128 FP32 lanes x 2 x max SM clock)"
     ach_gbs = bytes_ / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     ach_tf = flops / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
     ai = flops / bytes_ if bytes_ else float("inf")
-    if ai * hbm / 1e3 < alu:          # bandwidth roof is the lower one
+    if ai * hbm / 1e3 < cpeak:        # bandwidth roof is the lower one
         roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm}
     else:
-        roof = {"bound": "alu", "achieved": ach_tf, "peak": alu, "unit": "TFLOP/s", "frac": ach_tf / alu}
+        roof = {"bound": cbound, "achieved": ach_tf, "peak": cpeak, "unit": "TFLOP/s", "frac": ach_tf / cpeak}
     roof.update({"kernel": dom, "ms_per_step": dom_ms, "launches_per_step": kernel[dom][1] / args.steps,
                  "algorithmic_flops": flops, "algorithmic_bytes": bytes_,
-                 "peak_source": peak_kind + (" (alu: 148 SMs x 128 FP32 lanes x 2 x max SM clock)"
-                                            if roof["bound"] == "alu" else ""),
-                 "traffic": None})
+                 "compute_roof": {"bound": cbound, "peak_tflops": cpeak, "achieved_tflops": ach_tf,
+                                  "frac": ach_tf / cpeak if cpeak else None},
+                 "peak_source": "measured (MEASURED_PEAKS.json)" + (csrc if roof["bound"] != "hbm" else ""),
+                 "traffic": _traffic(dom, bytes_, args.steps)})
 
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
@@ -359,6 +382,8 @@ def run_ours(args, dist, rank, ws):
             "refinement": {"iters": [r[0] for r in results], "berr": [r[1] for r in results],
                            "converged": all(r[2] for r in results)},
             "phase_ms": {k: round(v, 2) for k, v in last_stats["phase_ms"].items()},
+            "phase_gflop": {k: round(v / 1e9, 3) for k, v in last_stats["phase_flops"].items()},
+            "phase_gbytes": {k: round(v / 1e9, 3) for k, v in last_stats["phase_bytes"].items()},
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 2) for k, v in kernel.items()},
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
