@@ -49,6 +49,11 @@ def _args():
     p.add_argument("--fp64-arm", type=int, default=1, help="also time the float64 factor arm once")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
+    p.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32x3"],
+                   help="reduced-precision arm: float32 factor with the Schur update on the FMA pipes "
+                        "(fp32) or on the tensor cores as split TF32 (tf32x3); auto = tf32x3 for the "
+                        "sphere, fp32 for the uneven batch (whose ill-conditioned systems need the "
+                        "more accurate factor)")
     p.add_argument("--nsys", type=int, default=64, help="uneven batch: number of systems")
     p.add_argument("--nmin", type=int, default=2048, help="uneven batch: smallest system")
     p.add_argument("--nmax", type=int, default=16384, help="uneven batch: largest system")
@@ -298,6 +303,10 @@ def run_ours(args, dist, rank, ws):
     x = h.colmajor(torch.zeros_like(b))
     stream = torch.cuda.current_stream().cuda_stream
 
+    if args.precision == "auto":
+        args.precision = "fp32" if args.workload == "uneven" else "tf32x3"
+    prec_mixed = h.H2_PREC_TF32X3 if args.precision == "tf32x3" else h.H2_PREC_FP32
+
     def step(prec, flags=0):
         Z = h.h2_factor_create(M, w.tol, norm_arg, prec, stream=stream, flags=flags)
         x.zero_()
@@ -305,7 +314,7 @@ def run_ours(args, dist, rank, ws):
         return Z, it, berr, ok
 
     for _ in range(max(args.warmup, 0)):
-        Z, it, berr, ok = step(h.H2_PREC_FP32)
+        Z, it, berr, ok = step(prec_mixed)
         del Z
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
@@ -319,7 +328,7 @@ def run_ours(args, dist, rank, ws):
     results = []
     kernel = {}
     for s in range(args.steps):
-        Z, it, berr, ok = step(h.H2_PREC_FP32, flags=binding.H2_FLAG_TIME_KERNELS)
+        Z, it, berr, ok = step(prec_mixed, flags=binding.H2_FLAG_TIME_KERNELS)
         results.append((it, berr, ok))
         st = h.h2_factor_stats_get(Z)
         for k, v in st["kernel_ms"].items():
@@ -347,7 +356,7 @@ def run_ours(args, dist, rank, ws):
     flops = last_stats["phase_flops"].get(phase, 0.0) if phase else 0.0
     bytes_ = last_stats["phase_bytes"].get(phase, 0.0) if phase else 0.0
     hbm = peaks["hbm_gbs"]
-    if dom == "schur":
+    if dom == "schur" and args.precision == "tf32x3":
         # split-TF32 tensor-core GEMM (3 TF32 MMAs per float32 product); TF32 peak = the
         # measured sustained bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25)
         cpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.1 / 2.25) / 3.0
@@ -367,14 +376,17 @@ def run_ours(args, dist, rank, ws):
                  "compute_roof": {"bound": cbound, "peak_tflops": cpeak, "achieved_tflops": ach_tf,
                                   "frac": ach_tf / cpeak if cpeak else None},
                  "peak_source": "measured (MEASURED_PEAKS.json)" + (csrc if roof["bound"] != "hbm" else ""),
-                 "traffic": _traffic(dom, bytes_, args.steps)})
+                 "traffic": _traffic("schur_tc" if dom == "schur" and args.precision == "tf32x3" else dom,
+                                     bytes_, args.steps)})
 
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
             "scaling": "strong" if uneven else "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": desc,
-                       "precision": "float32 factor/solve, float64 top LU + refinement",
+                       "precision": "float32 factor/solve" + (", Schur update on tcgen05 tensor cores as split "
+                                     "TF32 (hi*hi + hi*lo + lo*hi)" if args.precision == "tf32x3" else "")
+                                     + ", float64 top LU + refinement",
                        "parallelism": (f"systems split over {ws} GPUs (LPT)" if uneven else f"replicas x{ws}"),
                        "l2": "inputs larger than L2 (matrix "
                        f"{sum(A.nbytes() for A in As) / 1e9:.1f} GB)", "setup_s": round(setup_s, 1),
@@ -412,7 +424,7 @@ def run_ours(args, dist, rank, ws):
             torch.cuda.synchronize()
             f0 = time.perf_counter()
             Mh = h.h2_matrix_create_batch(Ahs, stream=stream)
-            Z = h.h2_factor_create(Mh, w.tol, norm_arg, h.H2_PREC_FP32, stream=stream)
+            Z = h.h2_factor_create(Mh, w.tol, norm_arg, prec_mixed, stream=stream)
             it, berr, ok = h.h2_refine_solve(Z, Mh, bh, xh, BERR_TOL, MAXIT)
             torch.cuda.synchronize()
             e2e.append(time.perf_counter() - f0)

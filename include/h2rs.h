@@ -55,8 +55,13 @@ enum {
 /* working precision of the factorisation and of the solve that applies it */
 enum {
     H2_PREC_FP64 = 0,           /* float64 everywhere                                 */
-    H2_PREC_FP32 = 1            /* float32 factor and solve; the top-level dense LU
+    H2_PREC_FP32 = 1,           /* float32 factor and solve; the top-level dense LU
                                    and the refinement residual stay float64           */
+    H2_PREC_TF32X3 = 2          /* as H2_PREC_FP32, with the Schur update on the tensor
+                                   cores: float32 operands split into two TF32 parts
+                                   (hi*hi + hi*lo + lo*hi, float32 accumulation; about
+                                   7e-7 relative error per product sum against 1e-7
+                                   for float32 FMA)                                  */
 };
 
 /* ------------------------------------------------------------------ H^2 matrix */

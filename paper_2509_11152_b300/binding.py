@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libh2rs.so")
 
 H2_PREC_FP64 = 0
 H2_PREC_FP32 = 1
+H2_PREC_TF32X3 = 2
 
 ERRORS = {0: "H2_OK", -1: "H2_ERR_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SINGULAR",
           -4: "H2_ERR_RANK_CAP", -5: "H2_ERR_NONFINITE", -6: "H2_ERR_NO_CONVERGENCE",

@@ -217,8 +217,9 @@ int h2_factor_create(const h2_matrix* A, const h2_factor_opts* o, h2_factor** ou
         H2_REQUIRE(o->eps_lu >= 0 && std::isfinite(o->eps_lu), H2_ERR_ARG, "eps_lu must be >= 0");
         H2_REQUIRE((o->norm_a > 0 && std::isfinite(o->norm_a)) || o->sys_norm_a, H2_ERR_ARG,
                    "norm_a must be > 0");
-        H2_REQUIRE(o->precision == H2_PREC_FP64 || o->precision == H2_PREC_FP32, H2_ERR_ARG,
-                   "unknown precision");
+        H2_REQUIRE(o->precision == H2_PREC_FP64 || o->precision == H2_PREC_FP32 ||
+                       o->precision == H2_PREC_TF32X3,
+                   H2_ERR_ARG, "unknown precision");
         Z = new h2_factor();
         Z->f = make_factor(&A->m, *o);
         Z->f->factorize();

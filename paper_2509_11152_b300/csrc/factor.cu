@@ -77,19 +77,23 @@ static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
 }
 
-// Schur tile: 128 x 64 on the tensor cores (float32 factor), 64 x 64 on the FP64 pipe
-template <class T> constexpr int schur_bm() { return sizeof(T) == 4 ? tc::TBM : 64; }
-template <class T> constexpr int schur_bn() { return sizeof(T) == 4 ? tc::TBN : 64; }
+// Schur tile: 128 x 64 on the tensor cores (H2_PREC_TF32X3), 64 x 64 on the FMA pipes
+static int schur_bm(bool tensor) { return tensor ? tc::TBM : 64; }
+static int schur_bn(bool tensor) { return tensor ? tc::TBN : 64; }
 
-static void launch_schur(int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
+static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
                          const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
                          const int* tmn) {
     k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
 }
 
-static void launch_schur(int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c, const int* tb,
-                         const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
-                         const int* tmn) {
+static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c,
+                         const int* tb, const int* tp, const int* cb, const int* ca, const int* ck,
+                         const int* tt, const int* tmn) {
+    if (!tensor) {
+        k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+        return;
+    }
     static const bool ready = [] {
         H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
         return true;
@@ -130,6 +134,7 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
     eps_lu = o.eps_lu;
     norm_a = o.norm_a;
     precision = o.precision;
+    tensor_schur = o.precision == H2_PREC_TF32X3;
     norm_sys.assign(A->H.nsys, o.norm_a);
     if (o.sys_norm_a)
         for (int z = 0; z < A->H.nsys; ++z) {
@@ -444,8 +449,8 @@ void FactorImpl<T>::run_level(size_t a) {
         for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
             const int tb = S.sch_tblk[t];
             const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
-            for (int tm = 0; tm * schur_bm<T>() < m; ++tm)
-                for (int tn = 0; tn * schur_bn<T>() < nn; ++tn) {
+            for (int tm = 0; tm * schur_bm(tensor_schur) < m; ++tm)
+                for (int tn = 0; tn * schur_bn(tensor_schur) < nn; ++tn) {
                     W.tile_tgt.push_back(t);
                     W.tile_mn.push_back((tm << 16) | tn);
                 }
@@ -526,7 +531,7 @@ void FactorImpl<T>::run_level(size_t a) {
             CG.seg_j = d_seg_j.as<int>() + s0;
             CG.seg_yoff = d_seg_yoff.as<int64_t>() + s0;
             kbegin(H2_K_GATHER);
-            k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, d_seg_slot.as<int>() + s0,
+            k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, d_seg_slot.as<int>() + s0, s0,
                                                               scratch.as<T>());
             kend();
             H2_LAUNCHED();
@@ -598,7 +603,7 @@ void FactorImpl<T>::run_level(size_t a) {
         const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
         if (ntile) {
             kbegin(H2_K_SCHUR);
-            launch_schur(ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
+            launch_schur(tensor_schur, ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
                             d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
                             d_tile_mn.as<int>() + t0);
             kend();
@@ -868,7 +873,8 @@ void FactorImpl<T>::factorize() {
 }
 
 std::unique_ptr<FactorBase> make_factor(const MatrixObj* A, const h2_factor_opts& o) {
-    if (o.precision == H2_PREC_FP32) return std::make_unique<FactorImpl<float>>(A, o);
+    if (o.precision == H2_PREC_FP32 || o.precision == H2_PREC_TF32X3)
+        return std::make_unique<FactorImpl<float>>(A, o);
     return std::make_unique<FactorImpl<double>>(A, o);
 }
 

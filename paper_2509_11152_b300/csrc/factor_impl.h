@@ -51,6 +51,7 @@ std::unique_ptr<FactorBase> make_factor(const MatrixObj* A, const h2_factor_opts
 template <class T>
 struct FactorImpl : FactorBase {
     double eps_lu = 0, norm_a = 0;
+    bool tensor_schur = false;                // H2_PREC_TF32X3: Schur update on tcgen05
     std::vector<LevelRT> lv;
     // dense top matrices (float64), one per system
     int64_t nt = 0;                           // sum of their orders

@@ -83,9 +83,12 @@ __global__ void k_leaf_basis(LevelArgs<T> a, T* V, const double* __restrict__ U,
 // ================================================================== augmentation
 // Y = (I - V V^T) F for the live columns of one fill block of box i; Y^T is written
 // into the box's scratch rows (Alg. 2 truncSVD input).
+// The live rows of all the box's segments are stored back to back (segment order), so
+// that the R-factor streams full chunks across segment boundaries.  L.seg_j is offset to
+// this colour's first segment s0; L.seg_ptr holds global segment indices.
 template <class T>
 __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* __restrict__ seg_slot,
-                             T* __restrict__ scratch) {
+                             int s0, T* __restrict__ scratch) {
     constexpr int PC = 16;
     const int s = blockIdx.x;
     const int slot = seg_slot[s];
@@ -93,10 +96,15 @@ __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* 
     const int b = L.seg_blk[s], j = L.seg_j[s];
     const int n = a.n[i], k = a.k[i], nj = a.n[j];
     const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
+    int64_t lp = 0;                                  // live rows of the box's earlier segments
+    for (int g = L.seg_ptr[slot]; g < s0 + s; ++g) {
+        const int jg = L.seg_j[g - s0];
+        lp += (a.colour[jg] < cur) ? a.kt[jg] : a.n[jg];
+    }
     const T* F = a.blk + a.blk_off[b];
     const T* V = a.V + a.V_off[i];
     const int64_t ld = L.ylead[slot];
-    T* Yt = scratch + L.ybase[slot] + L.seg_yoff[s];
+    T* Yt = scratch + L.ybase[slot] + lp - skip;      // row c of the segment at lp + c - skip
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* Fs = reinterpret_cast<T*>(sm_raw);
     T* Ps = Fs + (size_t)n * PC;
@@ -126,96 +134,81 @@ __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* 
     }
 }
 
-// R-factor of the live rows of Y^T (streamed in chunks of 64 rows) accumulated in W
-// (row-major n x n, row stride ldw).  Each thread keeps RPT = 64 / tpc rows of one
-// column of the chunk in registers (tpc threads per column); per Householder step only
-// the reflector column and its partial norms go through shared memory (double
-// buffered, one barrier per step).  Requires n * tpc <= 256.
+// R-factor of the live rows of Y^T (stored back to back, `live` rows) accumulated in W
+// (row-major n x n, row stride ldw), streamed in chunks of CH rows.  Each thread keeps
+// RPT rows of one column of the chunk in registers (TPC = CH / RPT threads per
+// column); per Householder step only the reflector column and its partial norms go
+// through shared memory (double buffered, one barrier per step).  Requires
+// n * TPC <= blockDim.x.
 // elements of the chunk buffer of k_basis (also holds rfactor_stream's broadcasts)
 __host__ __device__ inline int basis_chunk_elems(int n) {
     const int ch = n <= 192 ? 64 : 32;
     const int e = (ch + 1) * n;
-    return e > 160 ? e : 160;
+    return e > 288 ? e : 288;
 }
 
-template <class T, int RPT>
-__device__ void rfactor_stream(const LevelArgs<T>& a, const ColourLists& L, int slot, int cur, int n,
-                               const T* __restrict__ Yt, int64_t ld, T* W, int ldw, T* vb) {
-    constexpr int CH = 64;
+template <class T, int RPT, int CH>
+__device__ void rfactor_stream(int n, int64_t live, const T* __restrict__ Yt, int64_t ld, T* W, int ldw, T* vb) {
     constexpr int TPC = CH / RPT;
     const int tid = threadIdx.x;
     const int part = tid % TPC, col = tid / TPC;
     const bool own = col < n;
     // vb layout: 2 buffers of [CH reflector values | TPC partial norms | x0]
     const int bufsz = CH + TPC + 1;
-    const int s0 = L.seg_ptr[slot], s1 = L.seg_ptr[slot + 1];
     T x[RPT];
-    for (int s = s0; s < s1; ++s) {
-        const int j = L.seg_j[s];
-        const int nj = a.n[j];
-        const int skip = (a.colour[j] < cur) ? (nj - a.kt[j]) : 0;
-        const int64_t yoff = L.seg_yoff[s];
-        for (int r0 = skip; r0 < nj; r0 += CH) {
-            const int rows = min(CH, nj - r0);
+    for (int64_t r0 = 0; r0 < live; r0 += CH) {
+        const int rows = (int)min((int64_t)CH, live - r0);
 #pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                const int rr = part * RPT + q;
-                x[q] = (own && rr < rows) ? Yt[(yoff + r0 + rr) + (int64_t)col * ld] : T(0);
-            }
-            for (int jj = 0; jj < n; ++jj) {
-                T* buf = vb + (jj & 1) * bufsz;
-                if (col == jj) {
-                    T p2 = 0;
+        for (int q = 0; q < RPT; ++q) {
+            const int rr = part * RPT + q;
+            x[q] = (own && rr < rows) ? Yt[(r0 + rr) + (int64_t)col * ld] : T(0);
+        }
+        for (int jj = 0; jj < n; ++jj) {
+            T* buf = vb + (jj & 1) * bufsz;
+            if (col == jj) {
+                T p2 = 0;
 #pragma unroll
-                    for (int q = 0; q < RPT; ++q) {
-                        buf[part * RPT + q] = x[q];
-                        p2 += x[q] * x[q];
-                    }
-                    buf[CH + part] = p2;
-                    if (part == 0) buf[CH + TPC] = W[(int64_t)jj * ldw + jj];
+                for (int q = 0; q < RPT; ++q) {
+                    buf[part * RPT + q] = x[q];
+                    p2 += x[q] * x[q];
                 }
-                __syncthreads();
-                T ss = 0;
-#pragma unroll
-                for (int p = 0; p < TPC; ++p) ss += buf[CH + p];
-                if (ss == T(0)) continue;                         // uniform; buffers alternate
-                const T x0 = buf[CH + TPC];
-                const T nrm = sqrt(x0 * x0 + ss);
-                const T beta = x0 > T(0) ? -nrm : nrm;
-                const T v0 = x0 - beta;
-                const T tw = -v0 / beta;
-                const T inv = T(1) / v0;
-                const bool act = own && col > jj;
-                T d = 0;
-                if (act) {
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) d += buf[part * RPT + q] * x[q];
-                }
-#pragma unroll
-                for (int o = 1; o < TPC; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                if (act) {
-                    const T w = W[(int64_t)jj * ldw + col] + d * inv;
-                    const T tww = tw * w;
-                    const T f = tww * inv;
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) x[q] -= f * buf[part * RPT + q];
-                    if (part == 0) W[(int64_t)jj * ldw + col] -= tww;
-                } else if (col == jj && part == 0) {
-                    W[(int64_t)jj * ldw + jj] = beta;
-                }
+                buf[CH + part] = p2;
+                if (part == 0) buf[CH + TPC] = W[(int64_t)jj * ldw + jj];
             }
             __syncthreads();
+            T ss = 0;
+#pragma unroll
+            for (int p = 0; p < TPC; ++p) ss += buf[CH + p];
+            if (ss == T(0)) continue;                         // uniform; buffers alternate
+            const T x0 = buf[CH + TPC];
+            const T nrm = sqrt(x0 * x0 + ss);
+            const T beta = x0 > T(0) ? -nrm : nrm;
+            const T v0 = x0 - beta;
+            const T tw = -v0 / beta;
+            const T inv = T(1) / v0;
+            const bool act = own && col > jj;
+            T d = 0;
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) d += buf[part * RPT + q] * x[q];
+            }
+#pragma unroll
+            for (int o = 1; o < TPC; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (act) {
+                const T w = W[(int64_t)jj * ldw + col] + d * inv;
+                const T tww = tw * w;
+                const T f = tww * inv;
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) x[q] -= f * buf[part * RPT + q];
+                if (part == 0) W[(int64_t)jj * ldw + col] -= tww;
+            } else if (col == jj && part == 0) {
+                W[(int64_t)jj * ldw + jj] = beta;
+            }
         }
+        __syncthreads();
     }
 }
 
-// Basis augmentation + completion of one box (Alg. 2, truncSVD option 2):
-//   R  = R-factor of Y^T (Householder, streamed over row chunks, R kept row-major)
-//   one-sided Jacobi on M = R^T: its converged columns are sigma_p w_p with w_p the
-//   left singular vectors of Y; w_p with sigma_p > eps_fill (largest first, at most
-//   n-k of them) form Vbar
-//   Householder QR of [V, Vbar]: its Q columns k.. give Vbar orthonormalised against
-//   V and the complement V~perp; Q~ = [V~perp, V, Vbar].
 // BIG: boxes up to 256 (one CTA per SM: 64 rows per thread in the R-factor); otherwise
 // boxes up to 128, register-capped so that two boxes share an SM.
 template <class T, bool BIG>
@@ -256,10 +249,10 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
         // ---------------- R-factor of Y^T (R row-major in W, row stride ldw)
         for (int x = tid; x < n * ldw; x += blockDim.x) W[x] = T(0);
         __syncthreads();
-        if (n <= 32) rfactor_stream<T, 8>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
-        else if (n <= 64) rfactor_stream<T, 16>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
-        else if (!BIG || n <= 128) rfactor_stream<T, 32>(a, L, slot, cur, n, Yt, ld, W, ldw, C);
-        else rfactor_stream<T, BIG ? 64 : 32>(a, L, slot, cur, n, Yt, ld, W, ldw, C);   // n <= 256
+        if (n <= 32) rfactor_stream<T, 16, 128>(n, live, Yt, ld, W, ldw, C);
+        else if (n <= 64) rfactor_stream<T, 32, 128>(n, live, Yt, ld, W, ldw, C);
+        else if (!BIG || n <= 128) rfactor_stream<T, 32, 64>(n, live, Yt, ld, W, ldw, C);
+        else rfactor_stream<T, BIG ? 64 : 32, 64>(n, live, Yt, ld, W, ldw, C);   // n <= 256
         __syncthreads();
         // ---------------- one-sided Jacobi on M = R^T (column p of M = row p of R)
         // Round-robin pairs over the active columns, tpp threads per pair (rows

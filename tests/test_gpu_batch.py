@@ -108,10 +108,12 @@ def test_batch_equals_separate_factorisations(h):
             assert np.array_equal(lays[a]["ranks"][boxes], h.h2_layout_get(Z1, a)["ranks"])
 
 
-def test_batch_fp32_refinement_reaches_backward_error_per_system(h):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_batch_fp32_refinement_reaches_backward_error_per_system(h, prec):
     pbs = batch()
     M = h.h2_matrix_create_batch([pb.A for pb in pbs])
-    Z = h.h2_factor_create(M, EPS, [pb.norm_a for pb in pbs], h.H2_PREC_FP32)
+    Z = h.h2_factor_create(M, EPS, [pb.norm_a for pb in pbs],
+                           h.H2_PREC_FP32 if prec == "fp32" else h.H2_PREC_TF32X3)
     b = _stacked_rhs()
     bt = h.colmajor(torch.from_numpy(b).cuda())
     xt = h.colmajor(torch.zeros_like(bt))

@@ -82,11 +82,12 @@ def test_fp64_factor_solve_matches_oracle(h, name, over, eps):
         assert np.array_equal(lay["offset"], lv.layout["offset"])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("name,over,eps", CASES, ids=IDS)
-def test_fp32_factor_with_refinement(h, name, over, eps):
+def test_fp32_factor_with_refinement(h, name, over, eps, prec):
     pb, A, b, Z0, x0 = oracle_solution(name, eps, 2, 1, **over)
     M = h.h2_matrix_create(pb.A)
-    Z = h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_FP32)
+    Z = h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_FP32 if prec == "fp32" else h.H2_PREC_TF32X3)
     bt = h.colmajor(torch.from_numpy(b).cuda())
     xt = h.colmajor(torch.zeros_like(bt))
     it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
@@ -190,7 +191,7 @@ def test_gmres_refinement_when_plain_corrections_stall(h):
     pb = problem("gauss3d", n=4096, leaf=32)
     A = pb.A.numpy()
     M = h.h2_matrix_create(pb.A)
-    Z = h.h2_factor_create(M, 1e-2, pb.norm_a, h.H2_PREC_FP32)
+    Z = h.h2_factor_create(M, 1e-2, pb.norm_a, h.H2_PREC_TF32X3)
     b = rhs(A.n, 2, seed=9)
     bt = h.colmajor(torch.from_numpy(b).cuda())
     xt = h.colmajor(torch.zeros_like(bt))
