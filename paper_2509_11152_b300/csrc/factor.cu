@@ -83,23 +83,28 @@ static int schur_bn(bool tensor) { return tensor ? tc::TBN : 64; }
 
 static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
                          const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
-                         const int* tmn) {
+                         const int* tmn, const SchurTgt*, const SchurCon*, int*) {
     k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
 }
 
 static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c,
                          const int* tb, const int* tp, const int* cb, const int* ca, const int* ck,
-                         const int* tt, const int* tmn) {
+                         const int* tt, const int* tmn, const SchurTgt* trec, const SchurCon* crec,
+                         int* counter) {
     if (!tensor) {
         k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
         return;
     }
-    static const bool ready = [] {
+    static const int nsm = [] {
         H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
-        return true;
+        int dev = 0, n = 0;
+        H2_CUDA_CHECK(cudaGetDevice(&dev));
+        H2_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        return n;
     }();
-    (void)ready;
-    k_schur_tc<<<ntile, 128, tc::kSmem, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+    const int grid = std::min(ntile, 4 * nsm);         // persistent: four CTAs per SM
+    H2_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    k_schur_tc<<<grid, 128, tc::kSmem, s>>>(ar, trec, crec, tt, tmn, ntile, counter);
 }
 
 template <class T>
@@ -511,6 +516,12 @@ void FactorImpl<T>::run_level(size_t a) {
     upload(d_c_box, S.sch_ci, s);
     upload(d_c_ablk, S.sch_cA, s);
     upload(d_c_kpos, S.sch_ckpos, s);
+    DevBuf d_trec, d_crec, d_counter;                      // Schur records (tensor-core path)
+    if (tensor_schur) {
+        d_counter.alloc(sizeof(int), s);
+        d_trec.alloc(std::max<size_t>(1, S.sch_tblk.size()) * sizeof(SchurTgt), s);
+        d_crec.alloc(std::max<size_t>(1, S.sch_ci.size()) * sizeof(SchurCon), s);
+    }
     for (int c = 0; c < nc; ++c) {
         const int b0 = W.box_cptr[c], nbx = W.box_cptr[c + 1] - b0;
         if (nbx == 0) continue;
@@ -603,9 +614,19 @@ void FactorImpl<T>::run_level(size_t a) {
         const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
         if (ntile) {
             kbegin(H2_K_SCHUR);
+            if (tensor_schur) {
+                const int tg0 = S.sch_cptr[c], ntg = S.sch_cptr[c + 1] - tg0;
+                const int e0 = S.sch_tptr[tg0], ne = S.sch_tptr[tg0 + ntg] - e0;
+                k_schur_prep<T><<<(unsigned)((ntg + ne + 255) / 256), 256, 0, s>>>(
+                    ar, c, tg0, ntg, e0, ne, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
+                    d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_trec.as<SchurTgt>(), d_crec.as<SchurCon>());
+                H2_LAUNCHED();
+                count_launch();
+            }
             launch_schur(tensor_schur, ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
                             d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
-                            d_tile_mn.as<int>() + t0);
+                            d_tile_mn.as<int>() + t0, d_trec.as<SchurTgt>(), d_crec.as<SchurCon>(),
+                            d_counter.as<int>());
             kend();
         }
         H2_LAUNCHED();

@@ -59,6 +59,22 @@ struct TopSys {
     int64_t nt;
 };
 
+// Schur update records, filled per colour once the colour's ranks and W_U are known
+// (so that a tile walks one record per contributor instead of a chain of index loads).
+struct SchurTgt {
+    int64_t coff;          // element offset of the target's first updated entry in blk
+    int nj;                // leading dimension (rows of the target block)
+    int m, nn;             // updated rows / columns
+    int row_lo;            // first updated row (A operands start there too)
+    int cb, ce;            // contributor records cb .. ce-1
+};
+struct SchurCon {
+    int64_t aoff;          // block (j, i): D_{j, i_R} starts at blk + aoff (+ row_lo)
+    int64_t boff;          // W_U^i columns of the target's column box: WU + boff (ld ri)
+    int ri;                // redundant size of contributor i (0: nothing to add)
+    int pad;
+};
+
 // Per-colour work lists of the basis kernels (device pointers).
 struct ColourLists {
     const int* boxes;          // boxes of the colour

@@ -874,47 +874,106 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
         }
 }
 
-// Float32 factor: the same target-owned update on the tcgen05 tensor cores (one
-// 128 x 64 target tile per CTA of 128 threads; split-TF32 products with float32-level
-// accuracy, see schur_tc.cuh).  K runs over the contributors in 32-wide slices.
+// Records of one colour's Schur targets and contributors (one thread per record).
+template <class T>
+__global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, int ne,
+                             const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
+                             const int* __restrict__ c_box, const int* __restrict__ c_ablk,
+                             const int* __restrict__ c_kpos, SchurTgt* __restrict__ trec,
+                             SchurCon* __restrict__ crec) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < nt) {
+        const int tt = t0 + x;
+        const int tb = tgt_blk[tt];
+        const int j = a.brow[tb], kb = a.bcol[tb];
+        const int nj = a.n[j], nk = a.n[kb];
+        const int row_lo = (a.colour[j] == cur) ? nj - a.kt[j] : 0;
+        const int col_lo = (a.colour[kb] == cur) ? nk - a.kt[kb] : 0;
+        SchurTgt r;
+        r.coff = a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
+        r.nj = nj;
+        r.m = nj - row_lo;
+        r.nn = nk - col_lo;
+        r.row_lo = row_lo;
+        r.cb = tgt_ptr[tt];
+        r.ce = tgt_ptr[tt + 1];
+        trec[tt] = r;
+    } else if (x < nt + ne) {
+        const int e = e0 + (x - nt);
+        const int i = c_box[e];
+        const int ri = a.n[i] - a.kt[i];
+        SchurCon r;
+        r.aoff = a.blk_off[c_ablk[e]];
+        r.boff = a.WU_off[i] + (int64_t)a.nbofs[a.nb_ptr[i] + c_kpos[e]] * ri;
+        r.ri = ri > 0 ? ri : 0;
+        r.pad = 0;
+        crec[e] = r;
+    }
+}
+
+// Float32 factor: the same target-owned update on the tcgen05 tensor cores.  A
+// persistent grid (a few CTAs of 128 threads per SM) takes the colour's 128 x 64
+// target tiles one at a time from a counter (zero before the launch), so that long and
+// short tiles balance; each tile's K runs over its contributors in 16-wide slices;
+// split-TF32 products, see schur_tc.cuh.
 __global__ void __launch_bounds__(128, 4)
-k_schur_tc(LevelArgs<float> a, int cur, const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
-           const int* __restrict__ c_box, const int* __restrict__ c_ablk, const int* __restrict__ c_kpos,
-           const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn) {
+k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon* __restrict__ crec,
+           const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn, int ntile,
+           int* __restrict__ counter) {
     extern __shared__ __align__(1024) unsigned char sm_tc[];
-    const int tt = tile_tgt[blockIdx.x];
-    const int mn = tile_mn[blockIdx.x];
-    const int tb = tgt_blk[tt];
-    const int j = a.brow[tb], kb = a.bcol[tb];
-    const int nj = a.n[j], nk = a.n[kb];
-    const int row_lo = (a.colour[j] == cur) ? nj - a.kt[j] : 0;
-    const int col_lo = (a.colour[kb] == cur) ? nk - a.kt[kb] : 0;
-    const int m = nj - row_lo, nn = nk - col_lo;
-    const int m0 = (mn >> 16) * tc::TBM, n0 = (mn & 0xffff) * tc::TBN;
-    if (m0 >= m || n0 >= nn) return;                 // whole block: before any barrier
-    float* C = a.blk + a.blk_off[tb] + row_lo + m0 + (int64_t)(col_lo + n0) * nj;
-    const int mv = min(tc::TBM, m - m0), nv = min(tc::TBN, nn - n0);
-    int c = tgt_ptr[tt];
-    const int cend = tgt_ptr[tt + 1];
-    int k0 = 0;
-    auto next = [&](tc::Slice& sl) -> bool {
-        for (; c < cend; ++c, k0 = 0) {
-            const int i = c_box[c];
-            const int ri = a.n[i] - a.kt[i];
-            if (k0 >= ri) continue;
-            // D_{j, i_R}: m x ri (ld nj); W_U^i columns of the target: ri x nn (ld ri)
-            sl.A = a.blk + a.blk_off[c_ablk[c]] + row_lo + m0 + (int64_t)k0 * nj;
-            sl.lda = nj;
-            sl.B = a.WU + a.WU_off[i] + ((int64_t)a.nbofs[a.nb_ptr[i] + c_kpos[c]] + n0) * ri + k0;
-            sl.ldb = ri;
-            sl.kv = min(tc::TBK, ri - k0);
-            k0 += tc::TBK;
-            return true;
+    __shared__ int next_tile;
+    int t = 0;                                       // current tile
+    bool active = false;
+    int first = 0;
+    SchurTgt tg{};
+    SchurCon cr{};
+    int c = 0, k0 = 0, m0 = 0, n0 = 0;
+    tc::TileOut out{};
+    auto gen = [&](tc::SliceT& st) -> bool {
+        for (;;) {
+            if (!active) {
+                __syncthreads();                         // every thread calls gen in step
+                if (threadIdx.x == 0) next_tile = atomicAdd(counter, 1);
+                __syncthreads();
+                t = next_tile;
+                if (t >= ntile) return false;
+                tg = trec[tile_tgt[t]];
+                const int mn = tile_mn[t];
+                m0 = (mn >> 16) * tc::TBM;
+                n0 = (mn & 0xffff) * tc::TBN;
+                if (m0 >= tg.m || n0 >= tg.nn) continue;
+                out.C = a.blk + tg.coff + m0 + (int64_t)n0 * tg.nj;
+                out.ldc = tg.nj;
+                out.mv = min(tc::TBM, tg.m - m0);
+                out.nv = min(tc::TBN, tg.nn - n0);
+                c = tg.cb;
+                k0 = 0;
+                if (c < tg.ce) cr = crec[c];
+                first = 1;
+                active = true;
+            }
+            while (c < tg.ce) {
+                if (k0 < cr.ri) {
+                    // D_{j, i_R}: m x ri (ld nj); W_U^i columns of the target: ri x nn (ld ri)
+                    st.sl.A = a.blk + cr.aoff + tg.row_lo + m0 + (int64_t)k0 * tg.nj;
+                    st.sl.lda = tg.nj;
+                    st.sl.B = a.WU + cr.boff + (int64_t)n0 * cr.ri + k0;
+                    st.sl.ldb = cr.ri;
+                    st.sl.kv = min(tc::TBK, cr.ri - k0);
+                    st.out = out;
+                    st.first = first;
+                    first = 0;
+                    k0 += tc::TBK;
+                    return true;
+                }
+                ++c;
+                k0 = 0;
+                if (c < tg.ce) cr = crec[c];
+            }
+            active = false;                          // tile done (no slice: nothing to add)
         }
-        return false;
     };
-    if (!tc::tile_sub(C, nj, mv, nv, next, sm_tc) && threadIdx.x == 0)
-        dev_fail(a.status, H2_ERR_TIMEOUT, a.level, j);
+    if (!tc::tiles_sub(gen, sm_tc) && threadIdx.x == 0) dev_fail(a.status, H2_ERR_TIMEOUT, a.level, -1);
 }
 
 // ================================================================== level close

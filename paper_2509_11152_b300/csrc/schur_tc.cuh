@@ -1,4 +1,4 @@
-// C -= sum_s A_s B_s for one 128 x 64 tile of C on the tcgen05 tensor cores, with
+// C -= sum_s A_s B_s for 128 x 64 tiles of C on the tcgen05 tensor cores, with
 // float32 operands split into two TF32 parts (a = a_hi + a_lo; the product keeps
 // a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in float32 in tensor memory), which
 // gives float32-level accuracy at tensor-core rate.
@@ -95,12 +95,29 @@ __device__ inline void store_slice(unsigned char* stage, const float (&ra)[kRA],
     }
 }
 
-// C[0:mv, 0:nv] (column-major, ldc) -= sum over the slices produced by next(Slice&)
-// (returns false when there are no more, and from then on).  Returns false if a
-// bounded wait gave up (C is then left unchanged).  smem: kSmem bytes of dynamic
-// shared memory, 1024-aligned.
-template <class Next>
-__device__ bool tile_sub(float* C, int64_t ldc, int mv, int nv, Next next, unsigned char* smem) {
+// Epilogue target of a tile: C[0:mv, 0:nv] (column-major, ldc) -= accumulator.
+struct TileOut {
+    float* C;
+    int64_t ldc;
+    int mv, nv;
+};
+
+// One K-slice plus the tile it belongs to; `first` marks the tile's first slice.
+struct SliceT {
+    Slice sl;
+    TileOut out;
+    int first;
+};
+
+// Persistent form: the slices of many tiles (produced in order by gen(SliceT&), false
+// when there are none left) flow through one tensor-memory accumulator, one pair of
+// shared-memory stages and one register prefetch pipeline, so a tile's loads start
+// while the previous tile is still being finished.  When a tile's first slice is
+// staged, the previous tile's MMAs are waited for and its accumulator is subtracted
+// from its C (all 128 threads; row 32w + lane, 64 columns).  Returns false if a
+// bounded wait gave up (tiles not yet finished are then left unchanged).
+template <class Gen>
+__device__ bool tiles_sub(Gen gen, unsigned char* smem) {
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * kStage + 16);
@@ -120,30 +137,56 @@ __device__ bool tile_sub(float* C, int64_t ldc, int mv, int nv, Next next, unsig
     fence_after();
     const uint32_t tmem = *tslot;
     constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
-    Slice sl;
+    const uint32_t trow = tmem + ((uint32_t)(32 * w) << 16);
+    auto epilogue = [&](const TileOut& o) {
+        const int r = 32 * w + l;
+#pragma unroll
+        for (int cc = 0; cc < TBN / 16; ++cc) {
+            float v[16];
+            tmem_ld16(trow + 16 * cc, v);
+            if (r < o.mv)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = 16 * cc + j;
+                    if (col < o.nv) o.C[r + (int64_t)col * o.ldc] -= v[j];
+                }
+        }
+    };
+    SliceT t0, t1;
     float ra0[kRA], rb0[kRB], ra1[kRA], rb1[kRB];
-    bool have0 = next(sl);
-    if (have0) load_slice(sl, mv, nv, ra0, rb0);
-    bool have1 = have0 && next(sl);
-    if (have1) load_slice(sl, mv, nv, ra1, rb1);
+    bool have0 = gen(t0);
+    if (have0) load_slice(t0.sl, t0.out.mv, t0.out.nv, ra0, rb0);
+    bool have1 = have0 && gen(t1);
+    if (have1) load_slice(t1.sl, t1.out.mv, t1.out.nv, ra1, rb1);
     int s = 0;
-    // one step: stage the slice held in (ra, rb), refill the registers with the slice
-    // two ahead, and let the tensor core consume the stage.  Every thread checks that
-    // the MMAs of two steps back have released the buffer; one barrier per step then
-    // both publishes the stage and agrees on giving up.
-    auto step = [&](float (&ra)[kRA], float (&rb)[kRB], bool& have) -> bool {
+    bool acc_valid = false;
+    TileOut acc{};
+    auto step = [&](SliceT& t, float (&ra)[kRA], float (&rb)[kRB], bool& have) -> bool {
         if (!have) return false;
         const int buf = s & 1;
-        const int late = (s >= 2 && !mbar_wait(&mbar[buf], ((s >> 1) - 1) & 1, kWaitCycles)) ? 1 : 0;
+        int late = 0;
+        if (t.first && acc_valid) {
+            // finish the previous tile: all its MMAs (up to step s-1) must be complete
+            if (!mbar_wait(&mbar[(s - 1) & 1], ((s - 1) >> 1) & 1, kWaitCycles)) late = 1;
+            if (!__syncthreads_or(late)) {
+                fence_after();
+                epilogue(acc);
+                fence_before();
+            } else {
+                late = 1;
+            }
+        } else if (s >= 2 && !mbar_wait(&mbar[buf], ((s >> 1) - 1) & 1, kWaitCycles)) {
+            late = 1;
+        }
         if (!late) store_slice(smem + buf * kStage, ra, rb);
         fence_proxy_async();
         if (__syncthreads_or(late)) {
             if (tid == 0) *flag = 1;
             return false;
         }
-        have = next(sl);
-        if (have) load_slice(sl, mv, nv, ra, rb);
-        if (tid == 0) {
+        const int first = t.first;
+        if (first) { acc = t.out; acc_valid = true; }
+        if (tid == 0) {                                  // the MMAs first: gen may wait on loads
             fence_after();
             const uint32_t base = smem_u32(smem + buf * kStage);
 #pragma unroll
@@ -152,35 +195,26 @@ __device__ bool tile_sub(float* C, int64_t ldc, int mv, int nv, Next next, unsig
                 const uint64_t aH = sdesc(base + o, kLBO, kSBO), aL = sdesc(base + kAbytes + o, kLBO, kSBO);
                 const uint64_t bH = sdesc(base + 2 * kAbytes + o, kLBO, kSBO);
                 const uint64_t bL = sdesc(base + 2 * kAbytes + kBbytes + o, kLBO, kSBO);
-                mma_tf32(tmem, aL, bH, idesc, (s > 0 || kk > 0) ? 1 : 0);   // small terms first
+                mma_tf32(tmem, aL, bH, idesc, (first && kk == 0) ? 0 : 1);   // small terms first
                 mma_tf32(tmem, aH, bL, idesc, 1);
                 mma_tf32(tmem, aH, bH, idesc, 1);
             }
             mma_commit(&mbar[buf]);
         }
+        have = gen(t);                                   // the slice two steps ahead
+        if (have) load_slice(t.sl, t.out.mv, t.out.nv, ra, rb);
         ++s;
         return true;
     };
-    while (step(ra0, rb0, have0) && step(ra1, rb1, have1)) {
+    while (step(t0, ra0, rb0, have0) && step(t1, ra1, rb1, have1)) {
     }
-    // every MMA issued must be complete before the accumulator is read or freed
+    // the last tile: wait for every MMA issued, then finish it
     if (s > 0 && tid == 0 && !mbar_wait(&mbar[(s - 1) & 1], ((s - 1) >> 1) & 1, kWaitCycles)) *flag = 1;
     __syncthreads();
     const bool ok = *flag == 0;
-    if (ok && s > 0) {
+    if (ok && acc_valid) {
         fence_after();
-        const int r = 32 * w + l;
-#pragma unroll
-        for (int cc = 0; cc < TBN / 16; ++cc) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * w) << 16) + 16 * cc, v);
-            if (r < mv)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = 16 * cc + j;
-                    if (col < nv) C[r + (int64_t)col * ldc] -= v[j];
-                }
-        }
+        epilogue(acc);
     }
     fence_before();
     __syncthreads();
