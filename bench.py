@@ -397,6 +397,7 @@ def run_ours(args, dist, rank, ws):
             "phase_gflop": {k: round(v / 1e9, 3) for k, v in last_stats["phase_flops"].items()},
             "phase_gbytes": {k: round(v / 1e9, 3) for k, v in last_stats["phase_bytes"].items()},
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 2) for k, v in kernel.items()},
+            "factor_host_ms": {k: round(v, 1) for k, v in last_stats["host_ms"].items()},
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
     # float64 factor arm (mixed vs float64 at the same backward error)

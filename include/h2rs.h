@@ -235,6 +235,9 @@ typedef struct {
     double phase_bytes[8];      /* algorithmic bytes of the same phases                */
     double kernel_ms[16];       /* H2_FLAG_TIME_KERNELS: summed launch times per H2_K_* */
     int64_t kernel_launches[16];
+    double host_ms[4];          /* host time of the factorisation: per-level work lists,
+                                   their uploads, level setup + close bookkeeping, and
+                                   waits for the per-level rank read-back            */
 } h2_factor_stats;
 
 H2_API int h2_factor_stats_get(const h2_factor* Z, h2_factor_stats* out);

@@ -50,7 +50,8 @@ class h2_factor_stats(ctypes.Structure):
                 ("error_level", ctypes.c_int32), ("error_box", ctypes.c_int32),
                 ("factor_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
                 ("phase_flops", ctypes.c_double * 8), ("phase_bytes", ctypes.c_double * 8),
-                ("kernel_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_int64 * 16)]
+                ("kernel_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_int64 * 16),
+                ("host_ms", ctypes.c_double * 4)]
 
 
 PHASES = ["augment", "project", "lu_trsm", "schur", "close", "top", "leaf_load", "other"]
@@ -302,7 +303,9 @@ def h2_factor_stats_get(Z: Factor) -> dict:
                 phase_flops=dict(zip(PHASES, list(s.phase_flops))),
                 phase_bytes=dict(zip(PHASES, list(s.phase_bytes))),
                 kernel_ms=dict(zip(KERNELS, list(s.kernel_ms))),
-                kernel_launches=dict(zip(KERNELS, list(s.kernel_launches))))
+                kernel_launches=dict(zip(KERNELS, list(s.kernel_launches))),
+                host_ms=dict(zip(["work_lists", "uploads", "level_setup_close", "rank_readback"],
+                                 list(s.host_ms))))
 
 
 def h2_layout_get(Z: Factor, level: int) -> dict:

@@ -158,6 +158,7 @@ int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_matrix*
         for (int64_t g = 0; g < nn; ++g) M.coef_off[g + 1] = M.coef_off[g] + H.rank[g];
         upload(M.d_coef_off, M.coef_off, s);
         build_plan(H, M.plan);
+        upload_plan(M.plan, s);
         H2_CUDA_CHECK(cudaStreamSynchronize(s));
     });
     if (rc != H2_OK) { delete A; return rc; }

@@ -3,12 +3,24 @@
 // the top level.  One host synchronisation per level reads back the augmented ranks,
 // which fix the sizes (and prefix-sum offsets) of the parent level.
 #include <algorithm>
+#include <chrono>
 #include <numeric>
 
 #include "factor_impl.h"
 #include "factor_kernels.cuh"
 
 namespace h2rs {
+
+// host stopwatch for h2_factor_stats.host_ms
+struct HostTimer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double lap() {
+        const auto t1 = std::chrono::steady_clock::now();
+        const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        t0 = t1;
+        return ms;
+    }
+};
 
 enum { PH_AUG = 0, PH_PROJ = 1, PH_LU = 2, PH_SCHUR = 3, PH_CLOSE = 4, PH_TOP = 5, PH_LOAD = 6,
        PH_OTHER = 7 };
@@ -77,9 +89,9 @@ static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
 }
 
-// Schur tile: 128 x 64 on the tensor cores (H2_PREC_TF32X3), 64 x 64 on the FMA pipes
-static int schur_bm(bool tensor) { return tensor ? tc::TBM : 64; }
-static int schur_bn(bool tensor) { return tensor ? tc::TBN : 64; }
+// Schur tiles of the FMA kernel: 64 x 64 (the tensor-core kernel walks each target's
+// 128 x 64 tiles itself)
+constexpr int kSchurTile = 64;
 
 static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
                          const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
@@ -95,6 +107,7 @@ static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs
         k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
         return;
     }
+    // tensor path: ntile = number of targets of the colour, trec offset to the first
     static const int nsm = [] {
         H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
         int dev = 0, n = 0;
@@ -104,7 +117,7 @@ static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs
     }();
     const int grid = std::min(ntile, 4 * nsm);         // persistent: four CTAs per SM
     H2_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), s));
-    k_schur_tc<<<grid, 128, tc::kSmem, s>>>(ar, trec, crec, tt, tmn, ntile, counter);
+    k_schur_tc<<<grid, 128, tc::kSmem, s>>>(ar, trec, crec, ntile, counter);
 }
 
 template <class T>
@@ -264,16 +277,25 @@ void FactorImpl<T>::setup_level(size_t a) {
     cudaStream_t s = stream;
     upload(L.d_n, L.n, s);
     upload(L.d_k, L.k, s);
-    upload(L.d_colour, S.colour, s);
+    L.d_colour.ptr = S.dev.colour.ptr;
+    L.d_brow.ptr = S.dev.brow.ptr;
+    L.d_bcol.ptr = S.dev.bcol.ptr;
+    L.d_top_boxes.ptr = S.dev.top_boxes.ptr;
+    L.d_skel_boxes.ptr = S.dev.skel_boxes.ptr;
+    L.d_nb_ptr.ptr = S.dev.nb_ptr.ptr;
+    L.d_nb_col.ptr = S.dev.nb_col.ptr;
+    L.d_nb_blk.ptr = S.dev.nb_blk.ptr;
+    L.d_nb_blkT.ptr = S.dev.nb_blkT.ptr;
+    L.d_diag_blk.ptr = S.dev.diag_blk.ptr;
+    L.d_fl_tbox.ptr = S.dev.fl_tbox.ptr;
+    L.d_fl_tptr.ptr = S.dev.fl_tptr.ptr;
+    L.d_fl_ci.ptr = S.dev.fl_ci.ptr;
+    L.d_fl_cpos.ptr = S.dev.fl_cpos.ptr;
     upload(L.d_blk_off, L.blk_off, s);
-    upload(L.d_brow, L.brow, s);
-    upload(L.d_bcol, S.bcol, s);
     upload(L.d_V_off, L.V_off, s);
     upload(L.d_voff, L.voff, s);
     upload(L.d_ttoff, L.ttoff, s);
     upload(L.d_tsys, L.tsys, s);
-    upload(L.d_top_boxes, S.top_boxes, s);
-    upload(L.d_skel_boxes, S.skel_boxes, s);
     upload(L.d_eps, eps, s);
     L.kt.assign(S.cnt, 0);
     upload(L.d_kt, L.kt, s);
@@ -287,7 +309,6 @@ void FactorImpl<T>::setup_level(size_t a) {
     prefix(L.piv_off, [&](int i) { return sk(i) ? (int64_t)L.n[i] : 0; });
     L.Nsum.assign(S.cnt, 0);
     L.nbofs.assign(S.nb_col.size(), 0);
-    L.diag_blk.assign(S.cnt, -1);
     for (int i = 0; i < S.cnt; ++i) {
         int o = 0;
         for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
@@ -295,7 +316,6 @@ void FactorImpl<T>::setup_level(size_t a) {
         L.Nsum[i] = o;
         for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
             if (S.nb_col[p] == i) L.nbofs[p] = o;
-        L.diag_blk[i] = S.find(i, i);
     }
     L.WLld.resize(S.cnt);
     for (int i = 0; i < S.cnt; ++i) L.WLld[i] = L.Nsum[i] + L.n[i];
@@ -307,17 +327,8 @@ void FactorImpl<T>::setup_level(size_t a) {
     upload(L.d_WU_off, L.WU_off, s);
     upload(L.d_WL_off, L.WL_off, s);
     upload(L.d_WLld, L.WLld, s);
-    upload(L.d_nb_ptr, S.nb_ptr, s);
-    upload(L.d_nb_col, S.nb_col, s);
     upload(L.d_nbofs, L.nbofs, s);
     upload(L.d_Nsum, L.Nsum, s);
-    upload(L.d_nb_blk, S.nb_blk, s);
-    upload(L.d_nb_blkT, S.nb_blkT, s);
-    upload(L.d_diag_blk, L.diag_blk, s);
-    upload(L.d_fl_tbox, S.fl_tbox, s);
-    upload(L.d_fl_tptr, S.fl_tptr, s);
-    upload(L.d_fl_ci, S.fl_ci, s);
-    upload(L.d_fl_cpos, S.fl_cpos, s);
     track(this, L.Q, std::max<int64_t>(1, L.Q_off[S.cnt]) * sizeof(T), s);
     track(this, L.LU, std::max<int64_t>(1, L.LU_off[S.cnt]) * sizeof(T), s);
     track(this, L.DI, std::max<int64_t>(1, L.Q_off[S.cnt]) * sizeof(T), s);
@@ -353,11 +364,9 @@ void FactorImpl<T>::run_level(size_t a) {
     cudaStream_t s = stream;
     LevelArgs<T> ar = args_of<T>(L, status.as<DevStatus>());
     if (a == 0) {
-        DevBuf d_near;
-        upload(d_near, S.near_entry, s);
         kbegin(H2_K_LOAD);
         k_leaf_load<T><<<S.nblocks(), 256, 0, s>>>(ar, M.D.as<double>(), M.d_D_off.as<int64_t>(),
-                                                 d_near.as<int64_t>());
+                                                 S.dev.near_entry.as<int64_t>());
         kend();
         H2_LAUNCHED();
         std::vector<int64_t> uoff(M.H.U_off.begin(), M.H.U_off.end());
@@ -375,6 +384,7 @@ void FactorImpl<T>::run_level(size_t a) {
         account(PH_LOAD, 0, bytes);
     }
     // ---------------- work lists
+    HostTimer ht;
     ColourWork W;
     const int nc = S.ncolour;
     W.box_cptr.push_back(0);
@@ -450,12 +460,12 @@ void FactorImpl<T>::run_level(size_t a) {
         W.zn_cptr.push_back((int)W.zn_box.size());
         W.wu_cptr.push_back((int)W.wu_box.size());
         W.wl_cptr.push_back((int)W.wl_box.size());
-        // schur tiles
-        for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
+        // schur tiles (the tensor-core kernel walks the targets' tiles itself)
+        for (int t = S.sch_cptr[c]; t < (tensor_schur ? S.sch_cptr[c] : S.sch_cptr[c + 1]); ++t) {
             const int tb = S.sch_tblk[t];
             const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
-            for (int tm = 0; tm * schur_bm(tensor_schur) < m; ++tm)
-                for (int tn = 0; tn * schur_bn(tensor_schur) < nn; ++tn) {
+            for (int tm = 0; tm * kSchurTile < m; ++tm)
+                for (int tn = 0; tn * kSchurTile < nn; ++tn) {
                     W.tile_tgt.push_back(t);
                     W.tile_mn.push_back((tm << 16) | tn);
                 }
@@ -475,6 +485,7 @@ void FactorImpl<T>::run_level(size_t a) {
         W.nmax.push_back(nmax);
         W.scratch_need.push_back(ysum + (in_sm ? 0 : wsum));
     }
+    stats.host_ms[0] += ht.lap();
     int64_t scratch_max = 1;
     for (auto v : W.scratch_need) scratch_max = std::max(scratch_max, v);
     DevBuf scratch;
@@ -483,7 +494,9 @@ void FactorImpl<T>::run_level(size_t a) {
     DevBuf d_boxes, d_seg_ptr, d_seg_blk, d_seg_j, d_seg_slot, d_seg_yoff, d_ybase, d_ylead, d_wbase;
     DevBuf d_pl_box, d_pl_blk, d_pl_pan, d_pr_box, d_pr_blk, d_pr_pan;
     DevBuf d_zf_box, d_zf_blk, d_zf_col, d_zn_box, d_zn_blk, d_zn_col, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
-    DevBuf d_tile_tgt, d_tile_mn, d_tgt_blk, d_tgt_ptr, d_c_box, d_c_ablk, d_c_kpos;
+    DevBuf d_tile_tgt, d_tile_mn;
+    const DevBuf &d_tgt_blk = S.dev.sch_tblk, &d_tgt_ptr = S.dev.sch_tptr, &d_c_box = S.dev.sch_ci,
+                 &d_c_ablk = S.dev.sch_cA, &d_c_kpos = S.dev.sch_ckpos;
     upload(d_boxes, W.boxes, s);
     upload(d_seg_ptr, W.seg_ptr, s);
     upload(d_seg_blk, W.seg_blk, s);
@@ -511,17 +524,13 @@ void FactorImpl<T>::run_level(size_t a) {
     upload(d_wl_mn, W.wl_mn, s);
     upload(d_tile_tgt, W.tile_tgt, s);
     upload(d_tile_mn, W.tile_mn, s);
-    upload(d_tgt_blk, S.sch_tblk, s);
-    upload(d_tgt_ptr, S.sch_tptr, s);
-    upload(d_c_box, S.sch_ci, s);
-    upload(d_c_ablk, S.sch_cA, s);
-    upload(d_c_kpos, S.sch_ckpos, s);
     DevBuf d_trec, d_crec, d_counter;                      // Schur records (tensor-core path)
     if (tensor_schur) {
         d_counter.alloc(sizeof(int), s);
         d_trec.alloc(std::max<size_t>(1, S.sch_tblk.size()) * sizeof(SchurTgt), s);
         d_crec.alloc(std::max<size_t>(1, S.sch_ci.size()) * sizeof(SchurCon), s);
     }
+    stats.host_ms[1] += ht.lap();
     for (int c = 0; c < nc; ++c) {
         const int b0 = W.box_cptr[c], nbx = W.box_cptr[c + 1] - b0;
         if (nbx == 0) continue;
@@ -611,11 +620,12 @@ void FactorImpl<T>::run_level(size_t a) {
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_LU);
         // ---- Schur update and zeroing of the eliminated rows / columns
-        const int t0 = W.tile_cptr[c], ntile = W.tile_cptr[c + 1] - t0;
+        const int t0 = W.tile_cptr[c];
+        const int tg0 = S.sch_cptr[c], ntg = S.sch_cptr[c + 1] - tg0;
+        const int ntile = tensor_schur ? ntg : W.tile_cptr[c + 1] - t0;   // targets on the tensor path
         if (ntile) {
             kbegin(H2_K_SCHUR);
             if (tensor_schur) {
-                const int tg0 = S.sch_cptr[c], ntg = S.sch_cptr[c + 1] - tg0;
                 const int e0 = S.sch_tptr[tg0], ne = S.sch_tptr[tg0 + ntg] - e0;
                 k_schur_prep<T><<<(unsigned)((ntg + ne + 255) / 256), 256, 0, s>>>(
                     ar, c, tg0, ntg, e0, ne, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
@@ -624,12 +634,11 @@ void FactorImpl<T>::run_level(size_t a) {
                 count_launch();
             }
             launch_schur(tensor_schur, ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
-                            d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
-                            d_tile_mn.as<int>() + t0, d_trec.as<SchurTgt>(), d_crec.as<SchurCon>(),
-                            d_counter.as<int>());
+                         d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
+                         d_tile_mn.as<int>() + t0, d_trec.as<SchurTgt>() + tg0, d_crec.as<SchurCon>(),
+                         d_counter.as<int>());
             kend();
         }
-        H2_LAUNCHED();
         const int zn0 = W.zn_cptr[c], nzn = W.zn_cptr[c + 1] - zn0;
         if (nzn) {
             kbegin(H2_K_ZERO);
@@ -642,9 +651,11 @@ void FactorImpl<T>::run_level(size_t a) {
         mark(PH_SCHUR);
     }
     // ---------------- ranks back to the host (sizes of the parent level)
+    ht.lap();
     check_status("factorize level");
     H2_CUDA_CHECK(cudaMemcpyAsync(L.kt.data(), L.d_kt.ptr, L.cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
     H2_CUDA_CHECK(cudaStreamSynchronize(s));
+    stats.host_ms[3] += ht.lap();
     untrack(this, scratch);
     // ---------------- algorithmic counts of this level (for roofline fractions)
     const double w = sizeof(T);
@@ -699,10 +710,7 @@ void FactorImpl<T>::close_level(size_t a) {
     const MatrixObj& M = *A;
     cudaStream_t s = stream;
     LevelArgs<T> ar = args_of<T>(L, status.as<DevStatus>());
-    DevBuf d_cd, d_cf, d_ca;
-    upload(d_cd, S.cl_dblk, s);
-    upload(d_cf, S.cl_fblk, s);
-    upload(d_ca, S.cl_adm, s);
+    const DevBuf &d_cd = S.dev.cl_dblk, &d_cf = S.dev.cl_fblk, &d_ca = S.dev.cl_adm;
     const int nbp = Pn.S->nblocks();
     if (nbp) {
         kbegin(H2_K_CLOSE);
@@ -753,10 +761,10 @@ void FactorImpl<T>::assemble_tops(size_t a) {
     for (int i : S.top_boxes)
         for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) blist.push_back(b);
     if (blist.empty()) return;
-    DevBuf d_blist, d_near;
+    DevBuf d_blist;
     upload(d_blist, blist, s);
     const bool leaf = S.l == M.H.d;                  // float64 blocks straight from A
-    if (leaf) upload(d_near, S.near_entry, s);
+    const DevBuf& d_near = S.dev.near_entry;
     kbegin(H2_K_TOP);
     k_top_assemble<T><<<(unsigned)blist.size(), 256, 0, s>>>(
         d_blist.as<int>(), L.blk.as<T>(), L.d_blk_off.as<int64_t>(), leaf ? M.D.as<double>() : nullptr,
@@ -842,11 +850,14 @@ void FactorImpl<T>::factorize() {
     stats.peak_bytes = 0;
     mark(-1);
     setup_level(0);
+    for (int q = 0; q < 4; ++q) stats.host_ms[q] = 0;
     for (size_t a = 0; a < P.levels.size(); ++a) {
         run_level(a);
+        HostTimer hs;
         assemble_tops(a);
         setup_level(a + 1);
         close_level(a);
+        stats.host_ms[2] += hs.lap();
     }
     top_factor();
     H2_CUDA_CHECK(cudaStreamSynchronize(stream));

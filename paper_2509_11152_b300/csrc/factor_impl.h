@@ -14,17 +14,19 @@ struct LevelRT {
     const LevelStruct* S = nullptr;
     std::vector<int> n, k, kt;
     std::vector<int64_t> blk_off, V_off, Q_off, LU_off, piv_off, WU_off, WL_off, voff;
-    std::vector<int> WLld, Nsum, nbofs, diag_blk, brow;
+    std::vector<int> WLld, Nsum, nbofs, brow;
     int64_t vtot = 0;
     // boxes of dense top matrices at this level: offset inside their system's matrix
     std::vector<int64_t> ttoff;
     std::vector<int> tsys;
-    DevBuf d_ttoff, d_tsys, d_top_boxes, d_skel_boxes, d_eps;
-    // device: structure and offsets
-    DevBuf d_n, d_k, d_kt, d_colour, d_blk_off, d_brow, d_bcol;
+    DevBuf d_ttoff, d_tsys, d_eps;
+    // device: sizes and offsets of this factorisation
+    DevBuf d_n, d_k, d_kt, d_blk_off;
     DevBuf d_V_off, d_Q_off, d_LU_off, d_piv_off, d_WU_off, d_WL_off, d_WLld;
-    DevBuf d_nb_ptr, d_nb_col, d_nbofs, d_Nsum, d_nb_blk, d_nb_blkT, d_diag_blk, d_voff;
-    DevBuf d_fl_tbox, d_fl_tptr, d_fl_ci, d_fl_cpos;
+    DevBuf d_nbofs, d_Nsum, d_voff;
+    // device: the level's structure (views of the matrix's LevelStruct::dev)
+    DevView d_colour, d_brow, d_bcol, d_top_boxes, d_skel_boxes, d_nb_ptr, d_nb_col, d_nb_blk, d_nb_blkT,
+        d_diag_blk, d_fl_tbox, d_fl_tptr, d_fl_ci, d_fl_cpos;
     // device: factor data
     DevBuf Q, LU, DI, piv, WU, WL;
     // device: working data (freed after the level close)

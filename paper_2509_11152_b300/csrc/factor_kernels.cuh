@@ -912,49 +912,52 @@ __global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, in
 }
 
 // Float32 factor: the same target-owned update on the tcgen05 tensor cores.  A
-// persistent grid (a few CTAs of 128 threads per SM) takes the colour's 128 x 64
-// target tiles one at a time from a counter (zero before the launch), so that long and
-// short tiles balance; each tile's K runs over its contributors in 16-wide slices;
-// split-TF32 products, see schur_tc.cuh.
+// persistent grid (a few CTAs of 128 threads per SM) takes the colour's targets one at
+// a time from a counter (zero before the launch), so that long and short targets
+// balance, and walks each target's 128 x 64 tiles in turn; a tile's K runs over its
+// contributors in 16-wide slices; split-TF32 products, see schur_tc.cuh.
 __global__ void __launch_bounds__(128, 4)
-k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon* __restrict__ crec,
-           const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn, int ntile,
+k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon* __restrict__ crec, int ntgt,
            int* __restrict__ counter) {
     extern __shared__ __align__(1024) unsigned char sm_tc[];
-    __shared__ int next_tile;
-    int t = 0;                                       // current tile
-    bool active = false;
+    __shared__ int next_tgt;
+    bool active = false;                             // a target is being walked
     int first = 0;
     SchurTgt tg{};
     SchurCon cr{};
-    int c = 0, k0 = 0, m0 = 0, n0 = 0;
+    int c = 0, k0 = 0, tm = 0, tn = 0, ntm = 0, ntn = 0;
     tc::TileOut out{};
+    auto start_tile = [&]() {
+        const int m0 = tm * tc::TBM, n0 = tn * tc::TBN;
+        out.C = a.blk + tg.coff + m0 + (int64_t)n0 * tg.nj;
+        out.ldc = tg.nj;
+        out.mv = min(tc::TBM, tg.m - m0);
+        out.nv = min(tc::TBN, tg.nn - n0);
+        c = tg.cb;
+        k0 = 0;
+        if (c < tg.ce) cr = crec[c];
+        first = 1;
+    };
     auto gen = [&](tc::SliceT& st) -> bool {
         for (;;) {
             if (!active) {
                 __syncthreads();                         // every thread calls gen in step
-                if (threadIdx.x == 0) next_tile = atomicAdd(counter, 1);
+                if (threadIdx.x == 0) next_tgt = atomicAdd(counter, 1);
                 __syncthreads();
-                t = next_tile;
-                if (t >= ntile) return false;
-                tg = trec[tile_tgt[t]];
-                const int mn = tile_mn[t];
-                m0 = (mn >> 16) * tc::TBM;
-                n0 = (mn & 0xffff) * tc::TBN;
-                if (m0 >= tg.m || n0 >= tg.nn) continue;
-                out.C = a.blk + tg.coff + m0 + (int64_t)n0 * tg.nj;
-                out.ldc = tg.nj;
-                out.mv = min(tc::TBM, tg.m - m0);
-                out.nv = min(tc::TBN, tg.nn - n0);
-                c = tg.cb;
-                k0 = 0;
-                if (c < tg.ce) cr = crec[c];
-                first = 1;
+                const int t = next_tgt;
+                if (t >= ntgt) return false;
+                tg = trec[t];
+                ntm = (tg.m + tc::TBM - 1) / tc::TBM;
+                ntn = (tg.nn + tc::TBN - 1) / tc::TBN;
+                if (ntm <= 0 || ntn <= 0) continue;
+                tm = tn = 0;
+                start_tile();
                 active = true;
             }
             while (c < tg.ce) {
                 if (k0 < cr.ri) {
                     // D_{j, i_R}: m x ri (ld nj); W_U^i columns of the target: ri x nn (ld ri)
+                    const int m0 = tm * tc::TBM, n0 = tn * tc::TBN;
                     st.sl.A = a.blk + cr.aoff + tg.row_lo + m0 + (int64_t)k0 * tg.nj;
                     st.sl.lda = tg.nj;
                     st.sl.B = a.WU + cr.boff + (int64_t)n0 * cr.ri + k0;
@@ -970,7 +973,10 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
                 k0 = 0;
                 if (c < tg.ce) cr = crec[c];
             }
-            active = false;                          // tile done (no slice: nothing to add)
+            // tile done (no slice: nothing to add); next tile of the target, or next target
+            if (++tn == ntn) { tn = 0; ++tm; }
+            if (tm < ntm) start_tile();
+            else active = false;
         }
     };
     if (!tc::tiles_sub(gen, sm_tc) && threadIdx.x == 0) dev_fail(a.status, H2_ERR_TIMEOUT, a.level, -1);

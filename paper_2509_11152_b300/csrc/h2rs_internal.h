@@ -66,6 +66,12 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// non-owning view of device memory owned elsewhere (same accessor as DevBuf)
+struct DevView {
+    void* ptr = nullptr;
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
 // upload a host vector into a fresh device buffer
 template <class T>
 void upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
@@ -142,6 +148,15 @@ struct LevelStruct {
 
     int find(int i, int j) const;             // merged block id of (i, j) or -1
     int nblocks() const { return (int)bcol.size(); }
+
+    // device copies of the structure above, uploaded once with the matrix
+    struct Dev {
+        DevBuf colour, brow, bcol, top_boxes, skel_boxes, nb_ptr, nb_col, nb_blk, nb_blkT, diag_blk;
+        DevBuf fl_tbox, fl_tptr, fl_ci, fl_cpos, near_entry;
+        DevBuf sch_tblk, sch_tptr, sch_ci, sch_cA, sch_ckpos, cl_dblk, cl_fblk, cl_adm;
+        DevBuf cboxes;                        // boxes of every colour, in colour order
+    } dev;
+    std::vector<int> cbox_ptr;                // ncolour+1 offsets into dev.cboxes
 };
 
 struct Plan {
@@ -155,6 +170,8 @@ struct Plan {
 };
 
 void build_plan(const HostStructure& H, Plan& P);
+// device copies of every level's structure (LevelStruct::dev)
+void upload_plan(Plan& P, cudaStream_t s);
 
 // one tree (heap numbering) from a descriptor, with consistency checks
 void read_structure(const h2_matrix_desc* d, HostStructure& H);

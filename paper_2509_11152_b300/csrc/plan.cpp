@@ -314,4 +314,48 @@ void build_plan(const HostStructure& H, Plan& P) {
     }
 }
 
+static void upload_level(LevelStruct& L, cudaStream_t s) {
+    std::vector<int> brow(L.nblocks()), diag(L.cnt, -1);
+    for (int i = 0; i < L.cnt; ++i) {
+        for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) brow[b] = i;
+        diag[i] = L.find(i, i);
+    }
+    std::vector<int> all;
+    L.cbox_ptr.assign(1, 0);
+    for (auto& cb : L.cboxes) {
+        all.insert(all.end(), cb.begin(), cb.end());
+        L.cbox_ptr.push_back((int)all.size());
+    }
+    LevelStruct::Dev& d = L.dev;
+    upload(d.colour, L.colour, s);
+    upload(d.brow, brow, s);
+    upload(d.bcol, L.bcol, s);
+    upload(d.top_boxes, L.top_boxes, s);
+    upload(d.skel_boxes, L.skel_boxes, s);
+    upload(d.nb_ptr, L.nb_ptr, s);
+    upload(d.nb_col, L.nb_col, s);
+    upload(d.nb_blk, L.nb_blk, s);
+    upload(d.nb_blkT, L.nb_blkT, s);
+    upload(d.diag_blk, diag, s);
+    upload(d.fl_tbox, L.fl_tbox, s);
+    upload(d.fl_tptr, L.fl_tptr, s);
+    upload(d.fl_ci, L.fl_ci, s);
+    upload(d.fl_cpos, L.fl_cpos, s);
+    upload(d.near_entry, L.near_entry, s);
+    upload(d.sch_tblk, L.sch_tblk, s);
+    upload(d.sch_tptr, L.sch_tptr, s);
+    upload(d.sch_ci, L.sch_ci, s);
+    upload(d.sch_cA, L.sch_cA, s);
+    upload(d.sch_ckpos, L.sch_ckpos, s);
+    upload(d.cl_dblk, L.cl_dblk, s);
+    upload(d.cl_fblk, L.cl_fblk, s);
+    upload(d.cl_adm, L.cl_adm, s);
+    upload(d.cboxes, all, s);
+}
+
+void upload_plan(Plan& P, cudaStream_t s) {
+    for (auto& L : P.levels) upload_level(L, s);
+    upload_level(P.toplev, s);
+}
+
 }  // namespace h2rs

@@ -293,19 +293,7 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
     s_load<T><<<L0.cnt, 256, 0, s>>>(b, ldb, nrhs, d_start.as<int64_t>(), L0.d_n.as<int>(),
                                      L0.d_voff.as<int64_t>(), vec[0].as<T>());
     count_launch();
-    DevBuf d_boxes;
-    std::vector<std::vector<int>> cptr(nl);
-    {
-        std::vector<int> all;
-        for (size_t a = 0; a < nl; ++a) {
-            cptr[a].push_back((int)all.size());
-            for (auto& cb : P.levels[a].cboxes) {
-                all.insert(all.end(), cb.begin(), cb.end());
-                cptr[a].push_back((int)all.size());
-            }
-        }
-        upload(d_boxes, all, s);
-    }
+    // boxes of each colour: the plan's device list, colour c at cbox_ptr[c]
     // forward
     for (size_t a = 0; a < nl; ++a) {
         LevelRT& L = lv[a];
@@ -314,8 +302,8 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         for (int i : S.skel_boxes) nmax = std::max(nmax, L.n[i]);
         const int qsm = nmax * nrhs * (int)sizeof(T);
         for (int c = 0; c < S.ncolour; ++c) {
-            const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;
-            s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
+            const int b0 = S.cbox_ptr[c], nb = S.cbox_ptr[c + 1] - b0;
+            s_apply_q<T><<<nb, 256, qsm, s>>>(S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
                                               L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                               vec[a].as<T>(), nrhs, 1);
             count_launch();
@@ -379,13 +367,13 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         for (int i : S.skel_boxes) nmax = std::max(nmax, L.n[i]);
         const int qsm = nmax * nrhs * (int)sizeof(T);
         for (int c = S.ncolour - 1; c >= 0; --c) {
-            const int b0 = cptr[a][c], nb = cptr[a][c + 1] - b0;
-            launch_bwd_u<T>(nmax, nb, s, d_boxes.as<int>() + b0, L.d_n.as<int>(), L.d_kt.as<int>(),
+            const int b0 = S.cbox_ptr[c], nb = S.cbox_ptr[c + 1] - b0;
+            launch_bwd_u<T>(nmax, nb, s, S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.d_kt.as<int>(),
                             L.d_nb_ptr.as<int>(), L.d_nb_col.as<int>(), L.d_nbofs.as<int>(),
                             L.WU.as<T>(), L.d_WU_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                             vec[a].as<T>(), nrhs);
             count_launch();
-            s_apply_q<T><<<nb, 256, qsm, s>>>(d_boxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
+            s_apply_q<T><<<nb, 256, qsm, s>>>(S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
                                               L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                                               vec[a].as<T>(), nrhs, 0);
             count_launch();
