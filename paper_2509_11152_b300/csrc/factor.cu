@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <numeric>
+#include <string>
 
 #include "factor_impl.h"
 #include "factor_kernels.cuh"
@@ -80,12 +81,13 @@ static int raise_smem(K kern) {
 }
 
 template <class T, bool RIGHT>
-static void launch_proj(int rpt, int nwork, int smem, cudaStream_t s, LevelArgs<T> ar, const int* box,
-                        const int* blk, const int* pan) {
-    if (rpt <= 1) k_proj<T, 1, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
-    else if (rpt <= 2) k_proj<T, 2, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
-    else if (rpt <= 4) k_proj<T, 4, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
-    else if (rpt <= 8) k_proj<T, 8, RIGHT><<<nwork, 256, smem, s>>>(ar, box, blk, pan);
+static void launch_proj(int rpt, int nwork, int npan, int smem, cudaStream_t s, LevelArgs<T> ar, const int* box,
+                        const int* blk) {
+    const dim3 g(nwork, npan);                        // y: 32-wide panel of the block
+    if (rpt <= 1) k_proj<T, 1, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
+    else if (rpt <= 2) k_proj<T, 2, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
+    else if (rpt <= 4) k_proj<T, 4, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
+    else if (rpt <= 8) k_proj<T, 8, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
 }
 
@@ -337,23 +339,13 @@ void FactorImpl<T>::setup_level(size_t a) {
     track(this, L.WL, std::max<int64_t>(1, L.WL_off[S.cnt]) * sizeof(T), s);
 }
 
-// per-colour work lists of one level (host built, uploaded once)
+// size-dependent work data of one level (the structural lists live in the plan)
 struct ColourWork {
-    // basis
-    std::vector<int> boxes, box_cptr;                      // boxes per colour
-    std::vector<int> seg_ptr, seg_blk, seg_j, seg_slot, seg_cptr;
-    std::vector<int64_t> seg_yoff, ybase, ylead, wbase;
+    std::vector<int64_t> seg_yoff, ybase, ylead, wbase;   // basis: per segment / per box
     std::vector<int64_t> scratch_need;                     // per colour (elements)
     std::vector<int> smem_basis, w_in_smem, smem_gather, nmax;
-    // projection / zeroing
-    std::vector<int> pl_box, pl_blk, pl_pan, pl_cptr;
-    std::vector<int> pr_box, pr_blk, pr_pan, pr_cptr;
-    std::vector<int> zf_box, zf_blk, zf_col, zf_cptr;
-    std::vector<int> zn_box, zn_blk, zn_col, zn_cptr;
-    // W_U / W_L GEMM tiles
-    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;
-    // schur tiles
-    std::vector<int> tile_tgt, tile_mn, tile_cptr;
+    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;   // W_U / W_L GEMM tiles
+    std::vector<int> tile_tgt, tile_mn, tile_cptr;         // FMA Schur tiles
 };
 
 template <class T>
@@ -383,65 +375,40 @@ void FactorImpl<T>::run_level(size_t a) {
             bytes += (double)(L.blk_off[b + 1] - L.blk_off[b]) * (S.bkind[b] == 0 ? 8 + sizeof(T) : sizeof(T));
         account(PH_LOAD, 0, bytes);
     }
-    // ---------------- work lists
+    // ---------------- size-dependent work data (the structural lists live in the plan)
     HostTimer ht;
     ColourWork W;
     const int nc = S.ncolour;
-    W.box_cptr.push_back(0);
-    W.seg_cptr.push_back(0);
-    W.pl_cptr.push_back(0);
-    W.pr_cptr.push_back(0);
-    W.zf_cptr.push_back(0);
-    W.zn_cptr.push_back(0);
+    const int PW = 32;
+    const int nbox_all = S.cbox_ptr[nc];
+    W.seg_yoff.resize(S.seg_blk.size());
+    W.ybase.resize(nbox_all);
+    W.ylead.resize(nbox_all);
+    W.wbase.resize(nbox_all);
     W.wu_cptr.push_back(0);
     W.wl_cptr.push_back(0);
     W.tile_cptr.push_back(0);
-    W.seg_ptr.push_back(0);
-    const int PW = 32;
+    int nmax_level = 1;
+    for (int v : L.n) nmax_level = std::max(nmax_level, v);
     for (int c = 0; c < nc; ++c) {
         int64_t ysum = 0, wsum = 0;
         int nmax = 0, gsm = 0, csz = 0;
-        const size_t wfirst = W.wbase.size();
-        for (int i : S.cboxes[c]) {
-            const int slot = (int)W.boxes.size();
-            W.boxes.push_back(i);
+        for (int q = S.cbox_ptr[c]; q < S.cbox_ptr[c + 1]; ++q) {
+            const int i = S.cboxes[c][q - S.cbox_ptr[c]];
             const int n = L.n[i];
             nmax = std::max(nmax, n);
             int64_t yrows = 0;
-            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
-                if (S.bkind[b] != 1 || S.first_touch[b] >= c) continue;
-                W.seg_blk.push_back(b);
-                W.seg_j.push_back(S.bcol[b]);
-                W.seg_yoff.push_back(yrows);
-                W.seg_slot.push_back(slot - W.box_cptr[c]);
-                yrows += L.n[S.bcol[b]];
+            for (int g = S.seg_ptr[q]; g < S.seg_ptr[q + 1]; ++g) {
+                W.seg_yoff[g] = yrows;
+                yrows += L.n[S.seg_j[g]];
             }
-            W.seg_ptr.push_back((int)W.seg_blk.size());
-            W.ybase.push_back(ysum);
-            W.ylead.push_back(yrows);
+            W.ybase[q] = ysum;
+            W.ylead[q] = yrows;
             ysum += yrows * n;
-            W.wbase.push_back(wsum);
+            W.wbase[q] = wsum;
             wsum += (int64_t)n * (n + 1);
             gsm = std::max(gsm, (int)((n + L.k[i]) * 16 * sizeof(T)));
             csz = std::max(csz, basis_chunk_elems(n));
-            // projection pairs (near blocks + fill blocks already holding fill)
-            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
-                const bool live = S.bkind[b] == 0 || S.first_touch[b] < c;
-                if (!live) continue;
-                const int j = S.bcol[b];
-                const int bt = S.btr[b];
-                for (int p = 0; p * PW < L.n[j]; ++p) {
-                    W.pl_box.push_back(i); W.pl_blk.push_back(b); W.pl_pan.push_back(p);
-                    W.pr_box.push_back(i); W.pr_blk.push_back(bt); W.pr_pan.push_back(p);
-                }
-                if (S.bkind[b] == 1) {
-                    W.zf_box.push_back(i); W.zf_blk.push_back(b); W.zf_col.push_back(0);
-                    W.zf_box.push_back(i); W.zf_blk.push_back(bt); W.zf_col.push_back(1);
-                } else {
-                    W.zn_box.push_back(i); W.zn_blk.push_back(b); W.zn_col.push_back(0);
-                    W.zn_box.push_back(i); W.zn_blk.push_back(bt); W.zn_col.push_back(1);
-                }
-            }
             const int wide = L.Nsum[i] + n;
             for (int tm = 0; tm * 64 < n; ++tm)
                 for (int tn = 0; tn * 64 < wide; ++tn) {
@@ -451,25 +418,20 @@ void FactorImpl<T>::run_level(size_t a) {
                     W.wl_mn.push_back((tn << 16) | tm);
                 }
         }
-        for (size_t q = wfirst; q < W.wbase.size(); ++q) W.wbase[q] += ysum;   // after the Y^T rows
-        W.box_cptr.push_back((int)W.boxes.size());
-        W.seg_cptr.push_back((int)W.seg_blk.size());
-        W.pl_cptr.push_back((int)W.pl_box.size());
-        W.pr_cptr.push_back((int)W.pr_box.size());
-        W.zf_cptr.push_back((int)W.zf_box.size());
-        W.zn_cptr.push_back((int)W.zn_box.size());
+        for (int q = S.cbox_ptr[c]; q < S.cbox_ptr[c + 1]; ++q) W.wbase[q] += ysum;   // after the Y^T rows
         W.wu_cptr.push_back((int)W.wu_box.size());
         W.wl_cptr.push_back((int)W.wl_box.size());
-        // schur tiles (the tensor-core kernel walks the targets' tiles itself)
-        for (int t = S.sch_cptr[c]; t < (tensor_schur ? S.sch_cptr[c] : S.sch_cptr[c + 1]); ++t) {
-            const int tb = S.sch_tblk[t];
-            const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
-            for (int tm = 0; tm * kSchurTile < m; ++tm)
-                for (int tn = 0; tn * kSchurTile < nn; ++tn) {
-                    W.tile_tgt.push_back(t);
-                    W.tile_mn.push_back((tm << 16) | tn);
-                }
-        }
+        // schur tiles of the FMA kernel (the tensor-core kernel walks targets' tiles itself)
+        if (!tensor_schur)
+            for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
+                const int tb = S.sch_tblk[t];
+                const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
+                for (int tm = 0; tm * kSchurTile < m; ++tm)
+                    for (int tn = 0; tn * kSchurTile < nn; ++tn) {
+                        W.tile_tgt.push_back(t);
+                        W.tile_mn.push_back((tm << 16) | tn);
+                    }
+            }
         W.tile_cptr.push_back((int)W.tile_tgt.size());
         const size_t base = (size_t)(csz + 2 * nmax + 33) * sizeof(T) + 16;
         const size_t wsm = (size_t)nmax * (nmax + 1) * sizeof(T);
@@ -490,40 +452,20 @@ void FactorImpl<T>::run_level(size_t a) {
     for (auto v : W.scratch_need) scratch_max = std::max(scratch_max, v);
     DevBuf scratch;
     track(this, scratch, scratch_max * sizeof(T), s);
-    // seg_ptr is per box (global over colours): make it per-colour local
-    DevBuf d_boxes, d_seg_ptr, d_seg_blk, d_seg_j, d_seg_slot, d_seg_yoff, d_ybase, d_ylead, d_wbase;
-    DevBuf d_pl_box, d_pl_blk, d_pl_pan, d_pr_box, d_pr_blk, d_pr_pan;
-    DevBuf d_zf_box, d_zf_blk, d_zf_col, d_zn_box, d_zn_blk, d_zn_col, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
+    DevBuf d_seg_yoff, d_ybase, d_ylead, d_wbase, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
     DevBuf d_tile_tgt, d_tile_mn;
-    const DevBuf &d_tgt_blk = S.dev.sch_tblk, &d_tgt_ptr = S.dev.sch_tptr, &d_c_box = S.dev.sch_ci,
-                 &d_c_ablk = S.dev.sch_cA, &d_c_kpos = S.dev.sch_ckpos;
-    upload(d_boxes, W.boxes, s);
-    upload(d_seg_ptr, W.seg_ptr, s);
-    upload(d_seg_blk, W.seg_blk, s);
-    upload(d_seg_j, W.seg_j, s);
-    upload(d_seg_slot, W.seg_slot, s);
     upload(d_seg_yoff, W.seg_yoff, s);
     upload(d_ybase, W.ybase, s);
     upload(d_ylead, W.ylead, s);
     upload(d_wbase, W.wbase, s);
-    upload(d_pl_box, W.pl_box, s);
-    upload(d_pl_blk, W.pl_blk, s);
-    upload(d_pl_pan, W.pl_pan, s);
-    upload(d_pr_box, W.pr_box, s);
-    upload(d_pr_blk, W.pr_blk, s);
-    upload(d_pr_pan, W.pr_pan, s);
-    upload(d_zf_box, W.zf_box, s);
-    upload(d_zf_blk, W.zf_blk, s);
-    upload(d_zf_col, W.zf_col, s);
-    upload(d_zn_box, W.zn_box, s);
-    upload(d_zn_blk, W.zn_blk, s);
-    upload(d_zn_col, W.zn_col, s);
     upload(d_wu_box, W.wu_box, s);
     upload(d_wu_mn, W.wu_mn, s);
     upload(d_wl_box, W.wl_box, s);
     upload(d_wl_mn, W.wl_mn, s);
     upload(d_tile_tgt, W.tile_tgt, s);
     upload(d_tile_mn, W.tile_mn, s);
+    const DevBuf &d_tgt_blk = S.dev.sch_tblk, &d_tgt_ptr = S.dev.sch_tptr, &d_c_box = S.dev.sch_ci,
+                 &d_c_ablk = S.dev.sch_cA, &d_c_kpos = S.dev.sch_ckpos;
     DevBuf d_trec, d_crec, d_counter;                      // Schur records (tensor-core path)
     if (tensor_schur) {
         d_counter.alloc(sizeof(int), s);
@@ -532,26 +474,26 @@ void FactorImpl<T>::run_level(size_t a) {
     }
     stats.host_ms[1] += ht.lap();
     for (int c = 0; c < nc; ++c) {
-        const int b0 = W.box_cptr[c], nbx = W.box_cptr[c + 1] - b0;
+        const int b0 = S.cbox_ptr[c], nbx = S.cbox_ptr[c + 1] - b0;
         if (nbx == 0) continue;
         ColourLists CL{};
-        CL.boxes = d_boxes.as<int>() + b0;
-        CL.seg_ptr = d_seg_ptr.as<int>() + b0;      // per-box pointers into global seg arrays
-        CL.seg_blk = d_seg_blk.as<int>();
-        CL.seg_j = d_seg_j.as<int>();
+        CL.boxes = S.dev.cboxes.as<int>() + b0;
+        CL.seg_ptr = S.dev.seg_ptr.as<int>() + b0;  // per-box pointers into global seg arrays
+        CL.seg_blk = S.dev.seg_blk.as<int>();
+        CL.seg_j = S.dev.seg_j.as<int>();
         CL.seg_yoff = d_seg_yoff.as<int64_t>();
         CL.ybase = d_ybase.as<int64_t>() + b0;
         CL.ylead = d_ylead.as<int64_t>() + b0;
         CL.wbase = d_wbase.as<int64_t>() + b0;
-        const int s0 = W.seg_cptr[c], ns = W.seg_cptr[c + 1] - s0;
+        const int s0 = S.seg_cptr[c], ns = S.seg_cptr[c + 1] - s0;
         // ---- augmentation
         if (ns > 0) {
             ColourLists CG = CL;
-            CG.seg_blk = d_seg_blk.as<int>() + s0;
-            CG.seg_j = d_seg_j.as<int>() + s0;
+            CG.seg_blk = S.dev.seg_blk.as<int>() + s0;
+            CG.seg_j = S.dev.seg_j.as<int>() + s0;
             CG.seg_yoff = d_seg_yoff.as<int64_t>() + s0;
             kbegin(H2_K_GATHER);
-            k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, d_seg_slot.as<int>() + s0, s0,
+            k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, S.dev.seg_slot.as<int>() + s0, s0,
                                                               scratch.as<T>());
             kend();
             H2_LAUNCHED();
@@ -568,29 +510,29 @@ void FactorImpl<T>::run_level(size_t a) {
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_AUG);
         // ---- projection + fill truncation
-        const int pl0 = W.pl_cptr[c], npl = W.pl_cptr[c + 1] - pl0;
-        const int pr0 = W.pr_cptr[c], npr = W.pr_cptr[c + 1] - pr0;
+        const int pj0 = S.pj_cptr[c], npj = S.pj_cptr[c + 1] - pj0;
         const int smp = 2 * PW * ((W.nmax[c] + 31) / 32 * 32 + 1) * (int)sizeof(T);
         const int rpt = (W.nmax[c] + 31) / 32;
-        if (npl) {
+        const int npan = (nmax_level + PW - 1) / PW;        // panels of the other dimension
+        if (npj) {
             kbegin(H2_K_PROJ);
-            launch_proj<T, false>(rpt, npl, smp, s, ar, d_pl_box.as<int>() + pl0, d_pl_blk.as<int>() + pl0,
-                                  d_pl_pan.as<int>() + pl0);
+            launch_proj<T, false>(rpt, npj, npan, smp, s, ar, S.dev.pj_box.as<int>() + pj0,
+                                  S.dev.pj_blk.as<int>() + pj0);
             kend();
         }
         H2_LAUNCHED();
-        if (npr) {
+        if (npj) {
             kbegin(H2_K_PROJ);
-            launch_proj<T, true>(rpt, npr, smp, s, ar, d_pr_box.as<int>() + pr0, d_pr_blk.as<int>() + pr0,
-                                 d_pr_pan.as<int>() + pr0);
+            launch_proj<T, true>(rpt, npj, npan, smp, s, ar, S.dev.pj_box.as<int>() + pj0,
+                                 S.dev.pj_blkT.as<int>() + pj0);
             kend();
         }
         H2_LAUNCHED();
-        const int zf0 = W.zf_cptr[c], nzf = W.zf_cptr[c + 1] - zf0;
+        const int zf0 = S.zf_cptr[c], nzf = S.zf_cptr[c + 1] - zf0;
         if (nzf) {
             kbegin(H2_K_ZERO);
-            k_zero_redundant<T><<<nzf, 256, 0, s>>>(ar, d_zf_box.as<int>() + zf0, d_zf_blk.as<int>() + zf0,
-                                                            d_zf_col.as<int>() + zf0);
+            k_zero_redundant<T><<<nzf, 256, 0, s>>>(ar, S.dev.zf_box.as<int>() + zf0, S.dev.zf_blk.as<int>() + zf0,
+                                                    S.dev.zf_col.as<int>() + zf0);
             kend();
         }
         H2_LAUNCHED();
@@ -600,7 +542,7 @@ void FactorImpl<T>::run_level(size_t a) {
         const size_t lu_sm = (size_t)W.nmax[c] * W.nmax[c] * sizeof(T);
         const int lu_in = lu_sm <= (size_t)smem_limits<T>().lu;
         kbegin(H2_K_LU);
-        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, d_boxes.as<int>() + b0, lu_in);
+        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, S.dev.cboxes.as<int>() + b0, lu_in);
         kend();
         H2_LAUNCHED();
         const int wu0 = W.wu_cptr[c], nwu = W.wu_cptr[c + 1] - wu0;
@@ -639,11 +581,11 @@ void FactorImpl<T>::run_level(size_t a) {
                          d_counter.as<int>());
             kend();
         }
-        const int zn0 = W.zn_cptr[c], nzn = W.zn_cptr[c + 1] - zn0;
+        const int zn0 = S.zn_cptr[c], nzn = S.zn_cptr[c + 1] - zn0;
         if (nzn) {
             kbegin(H2_K_ZERO);
-            k_zero_redundant<T><<<nzn, 256, 0, s>>>(ar, d_zn_box.as<int>() + zn0, d_zn_blk.as<int>() + zn0,
-                                                            d_zn_col.as<int>() + zn0);
+            k_zero_redundant<T><<<nzn, 256, 0, s>>>(ar, S.dev.zn_box.as<int>() + zn0, S.dev.zn_blk.as<int>() + zn0,
+                                                    S.dev.zn_col.as<int>() + zn0);
             kend();
         }
         H2_LAUNCHED();

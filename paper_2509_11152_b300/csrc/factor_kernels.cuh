@@ -466,13 +466,13 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
 // completely into shared memory before anything is written back.
 template <class T, int RPT, bool RIGHT>
 __global__ void __launch_bounds__(256)
-k_proj(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_blk,
-       const int* __restrict__ w_panel) {
+k_proj(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_blk) {
     constexpr int PW = 32, KC = 32;
     const int w = blockIdx.x;
-    const int i = w_box[w], b = w_blk[w], p0 = w_panel[w] * PW;
+    const int i = w_box[w], b = w_blk[w], p0 = blockIdx.y * PW;
     const int n = a.n[i];
     const int nj = RIGHT ? a.n[a.brow[b]] : a.n[a.bcol[b]];   // the block's other dimension
+    if (p0 >= nj) return;                                     // panel beyond the block
     const int pw = min(PW, nj - p0);
     const T* __restrict__ Q = a.Q + a.Q_off[i];
     T* B = a.blk + a.blk_off[b];

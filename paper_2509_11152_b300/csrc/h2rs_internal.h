@@ -135,6 +135,12 @@ struct LevelStruct {
     std::vector<int> sch_ckpos;               // position of k in N(i)
     // per near-field position (nb_ptr order): block ids of (i, j) and (j, i)
     std::vector<int> nb_blk, nb_blkT;
+    // per-colour work lists (boxes in cboxes order): fill segments of the basis
+    // augmentation (seg_slot = box position in its colour, seg_ptr = per box, global),
+    // live blocks to project (row block b and its transpose), blocks to zero
+    std::vector<int> seg_blk, seg_j, seg_slot, seg_ptr, seg_cptr;
+    std::vector<int> pj_box, pj_blk, pj_blkT, pj_cptr;
+    std::vector<int> zf_box, zf_blk, zf_col, zf_cptr, zn_box, zn_blk, zn_col, zn_cptr;
     // forward-solve L updates, per colour: target boxes j and contributors i
     std::vector<int> fl_cptr;                 // ncolour+1 -> ranges of targets
     std::vector<int> fl_tbox;                 // target box j
@@ -155,6 +161,8 @@ struct LevelStruct {
         DevBuf fl_tbox, fl_tptr, fl_ci, fl_cpos, near_entry;
         DevBuf sch_tblk, sch_tptr, sch_ci, sch_cA, sch_ckpos, cl_dblk, cl_fblk, cl_adm;
         DevBuf cboxes;                        // boxes of every colour, in colour order
+        DevBuf seg_blk, seg_j, seg_slot, seg_ptr, pj_box, pj_blk, pj_blkT;
+        DevBuf zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col;
     } dev;
     std::vector<int> cbox_ptr;                // ncolour+1 offsets into dev.cboxes
 };

@@ -203,6 +203,49 @@ static void solve_lists(LevelStruct& L) {
     }
 }
 
+// structure-only work lists of every colour (first_touch is final after schur_lists)
+static void work_lists(LevelStruct& L) {
+    L.seg_blk.clear(); L.seg_j.clear(); L.seg_slot.clear();
+    L.seg_ptr.assign(1, 0);
+    L.seg_cptr.assign(1, 0);
+    L.pj_box.clear(); L.pj_blk.clear(); L.pj_blkT.clear();
+    L.pj_cptr.assign(1, 0);
+    L.zf_box.clear(); L.zf_blk.clear(); L.zf_col.clear();
+    L.zn_box.clear(); L.zn_blk.clear(); L.zn_col.clear();
+    L.zf_cptr.assign(1, 0);
+    L.zn_cptr.assign(1, 0);
+    for (int c = 0; c < L.ncolour; ++c) {
+        int slot = 0;
+        for (int i : L.cboxes[c]) {
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
+                if (L.bkind[b] != 1 || L.first_touch[b] >= c) continue;
+                L.seg_blk.push_back(b);
+                L.seg_j.push_back(L.bcol[b]);
+                L.seg_slot.push_back(slot);
+            }
+            L.seg_ptr.push_back((int)L.seg_blk.size());
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
+                const bool live = L.bkind[b] == 0 || L.first_touch[b] < c;
+                if (!live) continue;
+                const int bt = L.btr[b];
+                L.pj_box.push_back(i);
+                L.pj_blk.push_back(b);
+                L.pj_blkT.push_back(bt);
+                auto& zb = L.bkind[b] == 1 ? L.zf_box : L.zn_box;
+                auto& zk = L.bkind[b] == 1 ? L.zf_blk : L.zn_blk;
+                auto& zc = L.bkind[b] == 1 ? L.zf_col : L.zn_col;
+                zb.push_back(i); zk.push_back(b); zc.push_back(0);
+                zb.push_back(i); zk.push_back(bt); zc.push_back(1);
+            }
+            ++slot;
+        }
+        L.seg_cptr.push_back((int)L.seg_blk.size());
+        L.pj_cptr.push_back((int)L.pj_box.size());
+        L.zf_cptr.push_back((int)L.zf_box.size());
+        L.zn_cptr.push_back((int)L.zn_box.size());
+    }
+}
+
 static int64_t adm_entry(const HostStructure& H, int64_t gs, int64_t gt) {
     auto b = H.adm_col.begin() + H.adm_ptr[gs];
     auto e = H.adm_col.begin() + H.adm_ptr[gs + 1];
@@ -285,6 +328,7 @@ void build_plan(const HostStructure& H, Plan& P) {
         block_list(L, carried);
         schur_lists(L);
         solve_lists(L);
+        work_lists(L);
         if (l == H.d) leaf_entries(H, L);
         else L.near_entry.assign(L.nblocks(), -1);
         // fill carried to the parent level: parents of fill pairs
@@ -351,6 +395,19 @@ static void upload_level(LevelStruct& L, cudaStream_t s) {
     upload(d.cl_fblk, L.cl_fblk, s);
     upload(d.cl_adm, L.cl_adm, s);
     upload(d.cboxes, all, s);
+    upload(d.seg_blk, L.seg_blk, s);
+    upload(d.seg_j, L.seg_j, s);
+    upload(d.seg_slot, L.seg_slot, s);
+    upload(d.seg_ptr, L.seg_ptr, s);
+    upload(d.pj_box, L.pj_box, s);
+    upload(d.pj_blk, L.pj_blk, s);
+    upload(d.pj_blkT, L.pj_blkT, s);
+    upload(d.zf_box, L.zf_box, s);
+    upload(d.zf_blk, L.zf_blk, s);
+    upload(d.zf_col, L.zf_col, s);
+    upload(d.zn_box, L.zn_box, s);
+    upload(d.zn_blk, L.zn_blk, s);
+    upload(d.zn_col, L.zn_col, s);
 }
 
 void upload_plan(Plan& P, cudaStream_t s) {
