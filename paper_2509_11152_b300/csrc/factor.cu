@@ -137,7 +137,7 @@ static const SmemLimits<T>& smem_limits() {
                              raise_smem(k_proj<T, 4, false>), raise_smem(k_proj<T, 8, false>)});
         x.proj_r = std::min({raise_smem(k_proj<T, 1, true>), raise_smem(k_proj<T, 2, true>),
                              raise_smem(k_proj<T, 4, true>), raise_smem(k_proj<T, 8, true>)});
-        x.gather = raise_smem(k_aug_gather<T>);
+        x.gather = std::min(raise_smem(k_aug_gather<T, true>), raise_smem(k_aug_gather<T, false>));
 
         return x;
     }();
@@ -343,7 +343,7 @@ void FactorImpl<T>::setup_level(size_t a) {
 struct ColourWork {
     std::vector<int64_t> seg_yoff, ybase, ylead, wbase;   // basis: per segment / per box
     std::vector<int64_t> scratch_need;                     // per colour (elements)
-    std::vector<int> smem_basis, w_in_smem, smem_gather, nmax;
+    std::vector<int> smem_basis, w_in_smem, smem_gather, gather_pc, gather_vs, nmax;
     std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;   // W_U / W_L GEMM tiles
     std::vector<int> tile_tgt, tile_mn, tile_cptr;         // FMA Schur tiles
 };
@@ -392,7 +392,7 @@ void FactorImpl<T>::run_level(size_t a) {
     for (int v : L.n) nmax_level = std::max(nmax_level, v);
     for (int c = 0; c < nc; ++c) {
         int64_t ysum = 0, wsum = 0;
-        int nmax = 0, gsm = 0, csz = 0;
+        int nmax = 0, kmax = 0, csz = 0;
         for (int q = S.cbox_ptr[c]; q < S.cbox_ptr[c + 1]; ++q) {
             const int i = S.cboxes[c][q - S.cbox_ptr[c]];
             const int n = L.n[i];
@@ -407,7 +407,7 @@ void FactorImpl<T>::run_level(size_t a) {
             ysum += yrows * n;
             W.wbase[q] = wsum;
             wsum += (int64_t)n * (n + 1);
-            gsm = std::max(gsm, (int)((n + L.k[i]) * 16 * sizeof(T)));
+            kmax = std::max(kmax, L.k[i]);
             csz = std::max(csz, basis_chunk_elems(n));
             const int wide = L.Nsum[i] + n;
             for (int tm = 0; tm * 64 < n; ++tm)
@@ -436,14 +436,25 @@ void FactorImpl<T>::run_level(size_t a) {
         const size_t base = (size_t)(csz + 2 * nmax + 33) * sizeof(T) + 16;
         const size_t wsm = (size_t)nmax * (nmax + 1) * sizeof(T);
         const auto& lim = smem_limits<T>();
-        H2_REQUIRE(base <= (size_t)lim.basis && (size_t)gsm <= (size_t)lim.gather &&
+        // gather: the widest chunk of F that fits, with V staged when it fits too
+        size_t gsm = 0;
+        int gpc = 0, gvs = 0;
+        for (int vs = 1; vs >= 0 && !gpc; --vs)
+            for (int pc : {64, 32, 16}) {
+                const size_t need = ((size_t)(nmax + 1) * pc + (size_t)(kmax + 1) * pc +
+                                     (vs ? (size_t)(nmax + 1) * kmax : 0)) * sizeof(T);
+                if (need <= (size_t)lim.gather) { gsm = need; gpc = pc; gvs = vs; break; }
+            }
+        H2_REQUIRE(gpc > 0 && base <= (size_t)lim.basis &&
                        (size_t)2 * 32 * ((nmax + 31) / 32 * 32 + 1) * sizeof(T) <= (size_t)std::min(lim.proj_l, lim.proj_r) &&
                        nmax <= 256,
                    H2_ERR_ARG, "box size too large for the shared-memory kernels");
+        W.gather_pc.push_back(gpc);
+        W.gather_vs.push_back(gvs);
         const int in_sm = base + wsm <= (size_t)lim.basis;
         W.w_in_smem.push_back(in_sm);
         W.smem_basis.push_back((int)(base + (in_sm ? wsm : 0)));
-        W.smem_gather.push_back(gsm);
+        W.smem_gather.push_back((int)gsm);
         W.nmax.push_back(nmax);
         W.scratch_need.push_back(ysum + (in_sm ? 0 : wsum));
     }
@@ -493,8 +504,12 @@ void FactorImpl<T>::run_level(size_t a) {
             CG.seg_j = S.dev.seg_j.as<int>() + s0;
             CG.seg_yoff = d_seg_yoff.as<int64_t>() + s0;
             kbegin(H2_K_GATHER);
-            k_aug_gather<T><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, S.dev.seg_slot.as<int>() + s0, s0,
-                                                              scratch.as<T>());
+            if (W.gather_vs[c])
+                k_aug_gather<T, true><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, S.dev.seg_slot.as<int>() + s0, s0,
+                                                                        W.gather_pc[c], scratch.as<T>());
+            else
+                k_aug_gather<T, false><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, S.dev.seg_slot.as<int>() + s0,
+                                                                         s0, W.gather_pc[c], scratch.as<T>());
             kend();
             H2_LAUNCHED();
         }

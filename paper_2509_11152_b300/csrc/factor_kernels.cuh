@@ -86,10 +86,11 @@ __global__ void k_leaf_basis(LevelArgs<T> a, T* V, const double* __restrict__ U,
 // The live rows of all the box's segments are stored back to back (segment order), so
 // that the R-factor streams full chunks across segment boundaries.  L.seg_j is offset to
 // this colour's first segment s0; L.seg_ptr holds global segment indices.
-template <class T>
+// PC columns of F at a time; V is staged in shared memory when VS (ld n + 1), the
+// chunk of F (ld n + 1) and P = V^T F (ld k + 1) always are (padded: no bank conflicts).
+template <class T, bool VS>
 __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* __restrict__ seg_slot,
-                             int s0, T* __restrict__ scratch) {
-    constexpr int PC = 16;
+                             int s0, int PC, T* __restrict__ scratch) {
     const int s = blockIdx.x;
     const int slot = seg_slot[s];
     const int i = L.boxes[slot];
@@ -102,32 +103,41 @@ __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* 
         lp += (a.colour[jg] < cur) ? a.kt[jg] : a.n[jg];
     }
     const T* F = a.blk + a.blk_off[b];
-    const T* V = a.V + a.V_off[i];
+    const T* Vg = a.V + a.V_off[i];
     const int64_t ld = L.ylead[slot];
     T* Yt = scratch + L.ybase[slot] + lp - skip;      // row c of the segment at lp + c - skip
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* Fs = reinterpret_cast<T*>(sm_raw);
-    T* Ps = Fs + (size_t)n * PC;
+    const int lf = n + 1, lq = k + 1;
+    T* Fs = reinterpret_cast<T*>(sm_raw);             // PC x (n+1): column c at c * lf
+    T* Ps = Fs + (size_t)lf * PC;                     // PC x (k+1)
+    T* Vs = Ps + (size_t)lq * PC;                     // k x (n+1) when VS
     const int tid = threadIdx.x, bs = blockDim.x;
+    if (VS) {
+        for (int x = tid; x < n * k; x += bs) Vs[(x % n) + (x / n) * lf] = Vg[x];
+    }
+    const T* V = VS ? Vs : Vg;
+    const int lv = VS ? lf : n;
     for (int c0 = skip; c0 < nj; c0 += PC) {
         const int pc = min(PC, nj - c0);
         for (int x = tid; x < n * pc; x += bs) {
             const int r = x % n, c = x / n;
-            Fs[r + c * n] = F[r + (int64_t)(c0 + c) * n];
+            Fs[r + c * lf] = F[r + (int64_t)(c0 + c) * n];
         }
         __syncthreads();
-        for (int x = tid; x < k * pc; x += bs) {
+        for (int x = tid; x < k * pc; x += bs) {         // P = V^T F
             const int r = x % k, c = x / k;
-            const T* vr = V + (int64_t)r * n;
+            const T* vr = V + (int64_t)r * lv;
+            const T* fc = Fs + c * lf;
             T acc = 0;
-            for (int q = 0; q < n; ++q) acc += vr[q] * Fs[q + c * n];
-            Ps[r + c * k] = acc;
+            for (int q = 0; q < n; ++q) acc += vr[q] * fc[q];
+            Ps[r + c * lq] = acc;
         }
         __syncthreads();
-        for (int x = tid; x < n * pc; x += bs) {
+        for (int x = tid; x < n * pc; x += bs) {         // Y^T rows: F - V P (coalesced on c)
             const int c = x % pc, r = x / pc;
-            T acc = Fs[r + c * n];
-            for (int q = 0; q < k; ++q) acc -= V[r + (int64_t)q * n] * Ps[q + c * k];
+            T acc = Fs[r + c * lf];
+            const T* pcol = Ps + c * lq;
+            for (int q = 0; q < k; ++q) acc -= V[r + (int64_t)q * lv] * pcol[q];
             Yt[(c0 + c) + (int64_t)r * ld] = acc;
         }
         __syncthreads();
