@@ -9,7 +9,9 @@
 * the projection identities of Sec. 2.1: Q~ orthogonal, Q~^T V = [0; I; 0], the
   truncation identity ||V~V~^T F - F|| = ||Vbar Vbar^T Y - Y||;
 * symmetry of the working near-field and fill blocks after each level;
-* colouring validity and brute-force fill pattern / prefix-sum layouts.
+* colouring validity and brute-force fill pattern / prefix-sum layouts;
+* linear complexity (Sec. 2.4): factor memory per point converges as N doubles;
+* the 2D near-field degree is in the range the paper reports (sanity only).
 """
 import numpy as np
 import pytest
@@ -183,3 +185,40 @@ def test_truncation_keeps_strictly_above_threshold():
         Vt = rs._augment(V, F, thr)
         assert Vt.shape[1] == 3 + keep
         assert np.allclose(Vt.T @ Vt, np.eye(3 + keep), atol=1e-13)
+
+
+def _factor_words(Z) -> int:
+    """Numbers stored by an oracle factor: Q~, the LU of D_RR, W_U, W_L per box and the
+    dense top matrix (the memory of Sec. 2.4's complexity estimate)."""
+    w = 0
+    for lv in Z.levels:
+        for bx in lv.boxes:
+            w += bx.Q.size + bx.r * bx.r
+            w += sum(m.size for m in bx.WL.values()) + sum(m.size for m in bx.WU.values())
+    nt = sum(Z.top_sizes)
+    return w + nt * nt
+
+
+def test_factor_memory_grows_linearly():
+    """Sec. 2.4: with bounded near-field degree and ranks the factor memory is O(N).
+    At these sizes the mean near-field degree still grows (boundary boxes have fewer
+    neighbours), so memory per point grows pre-asymptotically; the pin is that the
+    growth per doubling shrinks and the last doubling's log-log slope is within
+    1 +- 0.15 (2D exponential kernel, leaf 64, N = 4096 .. 16384)."""
+    ns, words = [4096, 8192, 16384], []
+    for n in ns:
+        pb = problem("cov2d", n=n, leaf=64)
+        Z = rs.factorize(pb.A.numpy(), 1e-6, pb.norm_a)
+        words.append(_factor_words(Z))
+    slopes = [np.log(words[q + 1] / words[q]) / np.log(ns[q + 1] / ns[q]) for q in range(2)]
+    assert slopes[1] < slopes[0], slopes
+    assert 0.85 <= slopes[1] <= 1.15, (slopes, words)
+
+
+def test_cov2d_near_field_degree_is_in_the_papers_range():
+    """The 4,096-point 2D covariance structure (leaf 64, eta = 1) has a mean near-field
+    degree C_sp of the order the paper reports for 2D problems (Table 1: about 11; a
+    sanity range only, the construction differs)."""
+    A = problem("cov2d").A
+    degs = [len(nb) for nb in st.neighbours(A, A.depth)]
+    assert 8 <= np.mean(degs) <= 20 and max(degs) <= 32, (np.mean(degs), max(degs))
