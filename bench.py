@@ -251,13 +251,17 @@ def run_reference(args, dist, rank, ws):
         return
     from h2gen import WORKLOADS, uneven_sizes
     if args.workload == "uneven":
-        family, n_full, n_sample = "gauss3d", sum(uneven_sizes(args.nsys, args.nmin, args.nmax)), 4096
-        wdesc = f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}]"
+        sizes = uneven_sizes(args.nsys, args.nmin, args.nmax)
+        family, n_full, n_sample = "gauss3d", sum(sizes), 4096
+        w = WORKLOADS[family]
+        wdesc = (f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}] "
+                 f"(total {n_full}), leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs} each")
     else:
         family = args.workload
-        n_full = args.n or WORKLOADS[args.workload].n
+        w = WORKLOADS[family]
+        n_full = args.n or w.n
         n_sample = min(n_full, 16384)
-        wdesc = f"{args.workload} N={n_full}"
+        wdesc = f"{w.name} N={n_full} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs}"
     for _ in range(args.warmup):
         _oracle_sample(family, min(n_sample, 4096))
     times = []

@@ -9,7 +9,6 @@
 // close).  Everything here depends only on the block partition, so it is built once
 // per matrix; box sizes and ranks are applied per level by the driver.
 #include <algorithm>
-#include <unordered_set>
 
 #include "h2rs_internal.h"
 
@@ -22,8 +21,6 @@ int LevelStruct::find(int i, int j) const {
     if (it == e || *it != j) return -1;
     return (int)(it - bcol.begin());
 }
-
-static inline uint64_t key(int a, int b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
 
 // near-field CSR of level l (local indices), from A's inadmissible CSR; boxes that are
 // not reached at this level (state 0) get empty rows
