@@ -46,6 +46,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sphere")
     p.add_argument("--n", type=int, default=0, help="override the problem size (testing only)")
+    p.add_argument("--nrhs", type=int, default=0, help="override the number of right-hand sides")
     p.add_argument("--fp64-arm", type=int, default=1, help="also time the float64 factor arm once")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
@@ -188,7 +189,8 @@ def _problems(args, device, rank, ws):
     if args.workload != "uneven":
         pb = _problem(args, device)
         w = pb.workload
-        return [pb], f"{w.name} N={pb.A.n} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs}"
+        return [pb], (f"{w.name} N={pb.A.n} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} "
+                      f"nrhs={args.nrhs or w.nrhs}")
     from h2gen import make_problem, uneven_sizes
     from paper_2509_11152_b300.shard import lpt_partition
     sizes = uneven_sizes(args.nsys, args.nmin, args.nmax)
@@ -197,7 +199,7 @@ def _problems(args, device, rank, ws):
     w = pbs[0].workload
     return pbs, (f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}] "
                  f"(total {sum(sizes)}; this rank {len(mine)} systems, {sum(sizes[s] for s in mine)} points), "
-                 f"leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs} each")
+                 f"leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={args.nrhs or w.nrhs} each")
 
 
 def _rhs(n, nrhs, device):
@@ -298,7 +300,7 @@ def run_ours(args, dist, rank, ws):
     norms = [pb.norm_a for pb in pbs]
     norm_arg = norms[0] if len(norms) == 1 else norms
     w = pbs[0].workload
-    nrhs = w.nrhs
+    nrhs = args.nrhs or w.nrhs
     n_tot = sum(A.n for A in As)
     setup_s = time.perf_counter() - t0
     M = h.h2_matrix_create_batch(As)
