@@ -138,3 +138,29 @@ def test_batch_plan_is_the_union_of_the_single_plans():
                     assert np.array_equal(r, np.arange(len(boxes))) and (k == 0).all()
             else:
                 assert (st_ == 0).all() and all(len(r) == 0 for r in rows)
+
+
+def test_batch_plan_edge_cases():
+    """A batch mixing a single-box system (depth 0), a system with nothing admissible
+    and a regular one: the lone box and the dense system are top boxes at the leaf
+    level, and a batch of one equals the single plan."""
+    from paper_2509_11152_b300 import h2_plan_query, h2_plan_query_batch
+    from paper_2509_11152_b300 import binding
+    lone = problem("cov2d", n=50, leaf=64).A
+    dense_sys = problem("cov2d", n=256, leaf=16, eta=1e-6).A
+    reg = problem("cov2d", n=1024, leaf=32).A
+    q = h2_plan_query_batch([lone, dense_sys, reg], 0)
+    for z, A in enumerate([lone, dense_sys]):
+        boxes = np.flatnonzero(q["system"] == z)
+        assert len(boxes) == 1 << A.depth and (q["state"][boxes] == 2).all()
+    assert (q["state"][q["system"] == 2] == 1).all()
+    one = h2_plan_query_batch([reg], 0)
+    single = h2_plan_query(reg, 0)
+    for key in ("colour", "row_ptr", "col", "kind"):
+        assert np.array_equal(one[key], single[key])
+    # bad arguments are reported, not trapped
+    d, keep = binding.make_desc(reg)
+    arr = (binding.h2_matrix_desc * 1)(d)
+    assert binding.lib().h2_plan_query_batch(0, arr, 0, None, None, None, None, None, None, None, None) == -1
+    assert binding.lib().h2_plan_query_batch(1, None, 0, None, None, None, None, None, None, None, None) == -1
+    assert binding.lib().h2_plan_query_batch(1, arr, 99, None, None, None, None, None, None, None, None) == -1
