@@ -341,7 +341,7 @@ void FactorImpl<T>::setup_level(size_t a) {
 
 // size-dependent work data of one level (the structural lists live in the plan)
 struct ColourWork {
-    std::vector<int64_t> seg_yoff, ybase, ylead, wbase;   // basis: per segment / per box
+    std::vector<int64_t> ybase, ylead, wbase;             // basis: per box
     std::vector<int64_t> scratch_need;                     // per colour (elements)
     std::vector<int> smem_basis, w_in_smem, smem_gather, gather_pc, gather_vs, nmax;
     std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;   // W_U / W_L GEMM tiles
@@ -381,7 +381,6 @@ void FactorImpl<T>::run_level(size_t a) {
     const int nc = S.ncolour;
     const int PW = 32;
     const int nbox_all = S.cbox_ptr[nc];
-    W.seg_yoff.resize(S.seg_blk.size());
     W.ybase.resize(nbox_all);
     W.ylead.resize(nbox_all);
     W.wbase.resize(nbox_all);
@@ -398,10 +397,7 @@ void FactorImpl<T>::run_level(size_t a) {
             const int n = L.n[i];
             nmax = std::max(nmax, n);
             int64_t yrows = 0;
-            for (int g = S.seg_ptr[q]; g < S.seg_ptr[q + 1]; ++g) {
-                W.seg_yoff[g] = yrows;
-                yrows += L.n[S.seg_j[g]];
-            }
+            for (int g = S.seg_ptr[q]; g < S.seg_ptr[q + 1]; ++g) yrows += L.n[S.seg_j[g]];
             W.ybase[q] = ysum;
             W.ylead[q] = yrows;
             ysum += yrows * n;
@@ -463,9 +459,8 @@ void FactorImpl<T>::run_level(size_t a) {
     for (auto v : W.scratch_need) scratch_max = std::max(scratch_max, v);
     DevBuf scratch;
     track(this, scratch, scratch_max * sizeof(T), s);
-    DevBuf d_seg_yoff, d_ybase, d_ylead, d_wbase, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
+    DevBuf d_ybase, d_ylead, d_wbase, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
     DevBuf d_tile_tgt, d_tile_mn;
-    upload(d_seg_yoff, W.seg_yoff, s);
     upload(d_ybase, W.ybase, s);
     upload(d_ylead, W.ylead, s);
     upload(d_wbase, W.wbase, s);
@@ -492,7 +487,6 @@ void FactorImpl<T>::run_level(size_t a) {
         CL.seg_ptr = S.dev.seg_ptr.as<int>() + b0;  // per-box pointers into global seg arrays
         CL.seg_blk = S.dev.seg_blk.as<int>();
         CL.seg_j = S.dev.seg_j.as<int>();
-        CL.seg_yoff = d_seg_yoff.as<int64_t>();
         CL.ybase = d_ybase.as<int64_t>() + b0;
         CL.ylead = d_ylead.as<int64_t>() + b0;
         CL.wbase = d_wbase.as<int64_t>() + b0;
@@ -502,7 +496,6 @@ void FactorImpl<T>::run_level(size_t a) {
             ColourLists CG = CL;
             CG.seg_blk = S.dev.seg_blk.as<int>() + s0;
             CG.seg_j = S.dev.seg_j.as<int>() + s0;
-            CG.seg_yoff = d_seg_yoff.as<int64_t>() + s0;
             kbegin(H2_K_GATHER);
             if (W.gather_vs[c])
                 k_aug_gather<T, true><<<ns, 256, W.smem_gather[c], s>>>(ar, CG, c, S.dev.seg_slot.as<int>() + s0, s0,

@@ -81,7 +81,6 @@ struct ColourLists {
     const int* seg_ptr;        // nbox+1: fill segments of each box
     const int* seg_blk;        // fill block (i, j)
     const int* seg_j;          // column box j
-    const int64_t* seg_yoff;   // row offset of the segment in the box's Y^T
     const int64_t* ybase;      // scratch offset of the box's Y^T
     const int64_t* ylead;      // leading dimension (total rows) of the box's Y^T
     const int64_t* wbase;      // scratch offset of the box's n x n work matrix
