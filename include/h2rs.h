@@ -221,9 +221,12 @@ H2_API int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs,
 
 /* ------------------------------------------------------------------ inspection */
 typedef struct {
-    int32_t nlevels;            /* skeletonised levels (d .. t)                        */
-    int32_t top_level;          /* t, or -1 when no block is admissible                */
-    int64_t top_size;           /* order of the dense top-level matrix                 */
+    int32_t nlevels;            /* skeletonised levels (d .. t); for a batch, forest
+                                   levels holding at least one skeletonised box       */
+    int32_t top_level;          /* t, or -1 when no block is admissible; for a batch,
+                                   the smallest t over the systems (forest levels)    */
+    int64_t top_size;           /* order of the dense top-level matrix; for a batch,
+                                   the sum of the systems' top orders                 */
     int64_t factor_bytes;       /* device bytes held by the factor                     */
     int64_t peak_bytes;         /* peak device bytes during the factorisation          */
     int32_t error_level;        /* level / local box of the last singular pivot, or -1 */
@@ -243,7 +246,8 @@ typedef struct {
 H2_API int h2_factor_stats_get(const h2_factor* Z, h2_factor_stats* out);
 
 /* Per-level layout of the factorisation, levels numbered 0 = leaves (depth d) up to
- * nlevels-1 (level t).  h2_layout_counts gives the number of boxes and blocks;
+ * nlevels-1 (level t); for a batch, forest levels (every system's boxes at that height,
+ * see h2_plan_query_batch for each box's system and state).  h2_layout_counts gives the number of boxes and blocks;
  * h2_layout_get fills caller arrays (any may be NULL):
  *   sizes[nbox]   n_i at that level       ranks[nbox]  augmented rank k~_i
  *   colour[nbox]  greedy colour            row_ptr[nbox+1], col[nblk], kind[nblk]
