@@ -164,3 +164,18 @@ def test_batch_plan_edge_cases():
     assert binding.lib().h2_plan_query_batch(0, arr, 0, None, None, None, None, None, None, None, None) == -1
     assert binding.lib().h2_plan_query_batch(1, None, 0, None, None, None, None, None, None, None, None) == -1
     assert binding.lib().h2_plan_query_batch(1, arr, 99, None, None, None, None, None, None, None, None) == -1
+
+
+def test_empty_and_oversized_descriptors_are_rejected():
+    """n = 0 and absurd depths are argument errors (reported, not trapped)."""
+    from paper_2509_11152_b300 import binding
+    A = problem("cov2d", n=512, leaf=32).A
+    d, keep = binding.make_desc(A)
+    lib = binding.lib()
+    for field, bad in (("n", 0), ("n", -5), ("depth", -1), ("depth", 40)):
+        old = getattr(d, field)
+        setattr(d, field, bad)
+        rc = lib.h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None)
+        assert rc == -1, (field, bad)
+        setattr(d, field, old)
+    assert lib.h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None) == 0
