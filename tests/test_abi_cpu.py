@@ -179,3 +179,31 @@ def test_empty_and_oversized_descriptors_are_rejected():
         assert rc == -1, (field, bad)
         setattr(d, field, old)
     assert lib.h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None) == 0
+
+
+def test_plain_c_caller_builds_and_plans():
+    """The C-ABI is usable from plain C (no torch, no Python): the example builds with
+    gcc against include/h2rs.h and libh2rs.so and runs the host-only plan query."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_2509_11152_b300 import binding
+    binding.lib()                                     # the library is built
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = os.path.join(ROOT, "paper_2509_11152_b300", "examples", "plan_query.c")
+    libdir = os.path.dirname(binding.LIB_PATH)
+    with tempfile.TemporaryDirectory() as td:
+        exe = os.path.join(td, "plan_query")
+        r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", src, "-I", os.path.join(ROOT, "include"),
+                            "-L", libdir, "-lh2rs", f"-Wl,-rpath,{libdir}", "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = r.stdout.splitlines()
+    assert lines[0].startswith("h2rs")
+    assert "4 boxes, 14 blocks" in lines[1]
+    assert lines[2] == "box 0 colour 0: 0 1 2f"          # distance-two fill through box 1
+    assert "partition" in lines[-1]
