@@ -115,17 +115,30 @@ def _transfer(A, g):
 
 
 # ------------------------------------------------------------------ one box
-def _augment(V, Frow, eps_fill):
-    """Alg. 2 truncSVD + augment: returns V~ = [V, Vbar]."""
+def _augment(V, Frow, eps_fill, method="qr"):
+    """Alg. 2 truncSVD + augment: returns V~ = [V, Vbar].
+
+    method "qr" (Sec. 2.1, the second approach, the one the paper uses): QR of Y^T,
+    SVD of R, keep sigma > eps_fill.
+    method "gram" (Sec. 2.1, the first approach; named again in the conclusions as
+    trading accuracy for speed): the eigendecomposition of the Gram matrix Y Y^T, keep
+    lambda > eps_fill^2.  The same subspace as "qr" while the kept sigma are well above
+    sqrt(machine eps) * sigma_max; below that the squared values sink into rounding."""
     n, k = V.shape
     if Frow is None or Frow.shape[1] == 0 or k >= n:
         return V
     Y = Frow - V @ (V.T @ Frow)
-    R = np.linalg.qr(Y.T, mode="r")                      # QR of Y^T
-    _, s, Wt = np.linalg.svd(R, full_matrices=False)     # R = U_R diag(s) W_R^T
-    keep = int(np.count_nonzero(s > eps_fill))
-    keep = min(keep, n - k)
-    Vbar = Wt[:keep].T                                   # right sing. vectors of R
+    if method == "gram":
+        lam, W = np.linalg.eigh(Y @ Y.T)                 # ascending eigenvalues
+        lam, W = lam[::-1], W[:, ::-1]                   # largest first
+        keep = min(int(np.count_nonzero(lam > eps_fill * eps_fill)), n - k)
+        Vbar = W[:, :keep]
+    else:
+        R = np.linalg.qr(Y.T, mode="r")                  # QR of Y^T
+        _, s, Wt = np.linalg.svd(R, full_matrices=False) # R = U_R diag(s) W_R^T
+        keep = int(np.count_nonzero(s > eps_fill))
+        keep = min(keep, n - k)
+        Vbar = Wt[:keep].T                               # right sing. vectors of R
     if keep:
         # they lie in range(Y), orthogonal to V in exact arithmetic; one pass of
         # block Gram-Schmidt + QR restores that in floating point
@@ -143,11 +156,11 @@ def _complete(Vt):
     return np.hstack([Qh[:, kt:], Vt])
 
 
-def _augment_box(i, sizes, V, F, frow, eps_fill, hook=None):
+def _augment_box(i, sizes, V, F, frow, eps_fill, hook=None, method="qr"):
     """Alg. 2, first parallel loop: V~_i = [V_i, truncSVD((I - V V^T) F_i*)]."""
     frow_keys = [(i, j) for j in frow.get(i, [])]
     Frow = np.hstack([F[key] for key in frow_keys]) if frow_keys else None
-    Vt = _augment(V[i], Frow, eps_fill)
+    Vt = _augment(V[i], Frow, eps_fill, method)
     if hook is not None:
         hook("augment", i=i, V=V[i], Vt=Vt, Frow=Frow)
     return Vt
@@ -199,12 +212,12 @@ def _partial_lu(i, n, r, nbrs, sizes, D, F):
     return lu, WL, WU
 
 
-def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None):
+def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None, method="qr"):
     """Alg. 2 for one colour: augment every box from the same fill matrix, then
     project every box, then the partial LU of every box.  (Boxes of one colour share
     no near-field block, but two of them can share a fill block, so augmenting one
     after projecting the other would not be Alg. 2.)"""
-    Vt = {i: _augment_box(i, sizes, V, F, frow, eps_fill, hook) for i in C}
+    Vt = {i: _augment_box(i, sizes, V, F, frow, eps_fill, hook, method) for i in C}
     Qs = {i: _complete(Vt[i]) for i in C}
     for i in C:
         _project_box(i, Qs[i], sizes[i] - Vt[i].shape[1], nbrs, D, F, frow, fcol)
@@ -217,10 +230,13 @@ def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None
 
 
 # ------------------------------------------------------------------ driver
-def factorize(A, eps_lu: float, norm_a: float, hook=None) -> Factor:
+def factorize(A, eps_lu: float, norm_a: float, hook=None, augment: str = "qr") -> Factor:
     """Alg. 1: factorise the H^2 matrix ``A`` (flat numpy storage) with threshold
     ``eps_lu``; ``norm_a`` is ``||A||_2`` (so ``eps_fill = eps_lu * norm_a``).
-    ``hook(event, **state)``, if given, observes intermediate states (tests only)."""
+    ``hook(event, **state)``, if given, observes intermediate states (tests only).
+    ``augment``: "qr" (truncSVD option 2) or "gram" (Gram matrix + eigendecomposition)."""
+    if augment not in ("qr", "gram"):
+        raise ValueError(augment)
     eps_fill = eps_lu * norm_a
     d = A.depth
     t = A.top_level()
@@ -248,7 +264,7 @@ def factorize(A, eps_lu: float, norm_a: float, hook=None) -> Factor:
             hook("level_start", l=l, D=D, F=F, V=V, sizes=sizes)
         for c in range(max(colour) + 1):
             C = [i for i in range(cnt) if colour[i] == c]
-            done = _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook)
+            done = _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook, augment)
             for i in C:
                 boxes[i] = done[i]
                 if hook is not None:

@@ -222,3 +222,55 @@ def test_cov2d_near_field_degree_is_in_the_papers_range():
     A = problem("cov2d").A
     degs = [len(nb) for nb in st.neighbours(A, A.depth)]
     assert 8 <= np.mean(degs) <= 20 and max(degs) <= 32, (np.mean(degs), max(degs))
+
+
+def _augment_case(seed, n=40, k=6, m=90):
+    """V (n x k orthonormal) and a fill row F whose projection Y = (I - VV^T) F has
+    singular values 10^0 .. 10^-3 (kept) and 10^-9 .. (dropped) around eps = 1e-6."""
+    rng = np.random.default_rng(seed)
+    V = np.linalg.qr(rng.standard_normal((n, k)))[0]
+    P = np.eye(n) - V @ V.T
+    Ul = np.linalg.qr(P @ rng.standard_normal((n, n - k)))[0]          # range orthogonal to V
+    Wr = np.linalg.qr(rng.standard_normal((m, n - k)))[0]
+    sig = np.concatenate([np.logspace(0, -3, 10), np.logspace(-9, -12, n - k - 10)])
+    F = Ul @ np.diag(sig) @ Wr.T + V @ rng.standard_normal((k, m))     # V part is projected out
+    return V, F
+
+
+def test_gram_augmentation_spans_the_qr_subspace():
+    """Sec. 2.1's first approach (Gram matrix, eigenvalues above eps^2) keeps the same
+    subspace as the second (QR of Y^T, SVD of R) when no singular value is near the
+    threshold: same count, principal angles at rounding level."""
+    for seed in range(3):
+        V, F = _augment_case(seed)
+        k = V.shape[1]
+        Vq = rs._augment(V, F, 1e-6, "qr")[:, k:]
+        Vg = rs._augment(V, F, 1e-6, "gram")[:, k:]
+        assert Vq.shape[1] == Vg.shape[1] == 10
+        s = np.linalg.svd(Vq.T @ Vg, compute_uv=False)                  # cosines of the angles
+        assert np.min(s) >= 1 - 1e-10
+        assert np.linalg.norm(V.T @ Vg) <= 1e-12                        # orthogonal to V
+
+
+def test_gram_augmentation_factorises_to_the_same_accuracy():
+    """At a moderate tolerance the Gram variant gives a factor of the same quality."""
+    pb = problem("cov2d", n=1024, leaf=32)
+    A = pb.A.numpy()
+    b = rhs(A.n, 2, seed=12)
+    errs = {}
+    for m in ("qr", "gram"):
+        Z = rs.factorize(A, 1e-6, pb.norm_a, augment=m)
+        x = rs.solve(Z, b)
+        errs[m] = dense.backward_error(A, x, b, pb.norm_a)[0]
+    assert errs["gram"] <= 10 * errs["qr"] + 1e-14 and errs["qr"] <= 1e-5, errs
+
+
+def test_gram_augmentation_loses_what_squaring_hides():
+    """The accuracy trade the paper names: singular values below about
+    sqrt(machine eps) * sigma_max vanish in the Gram matrix, so at a near-zero
+    tolerance the Gram variant keeps fewer vectors than the QR variant."""
+    V, F = _augment_case(0)
+    k = V.shape[1]
+    nq = rs._augment(V, F, 1e-11, "qr").shape[1] - k
+    ng = rs._augment(V, F, 1e-11, "gram").shape[1] - k
+    assert nq >= 11 and ng < nq, (nq, ng)
