@@ -467,9 +467,11 @@ int h2_layout_get(const h2_factor* Z, int32_t level, int64_t* sizes, int64_t* ra
     return H2_OK;
 }
 
-int h2_plan_query_batch(int32_t nsys, const h2_matrix_desc* descs, int32_t level, int64_t* nbox,
-                        int64_t* nblk, int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind,
-                        int32_t* state, int32_t* system) {
+// host-only plan of a batch and the query of one of its levels (skeletonised levels
+// only when only_skel)
+static int plan_query_impl(int32_t nsys, const h2_matrix_desc* descs, int32_t level, bool only_skel,
+                           int64_t* nbox, int64_t* nblk, int32_t* colour, int64_t* row_ptr, int64_t* col,
+                           int32_t* kind, int32_t* state, int32_t* system) {
     return guard([&] {
         H2_REQUIRE(nsys >= 1 && descs != nullptr, H2_ERR_ARG, "need at least one descriptor");
         std::vector<HostStructure> parts(nsys);
@@ -480,7 +482,8 @@ int h2_plan_query_batch(int32_t nsys, const h2_matrix_desc* descs, int32_t level
         merge_forest(parts, H, order, fv);
         Plan P;
         build_plan(H, P);
-        H2_REQUIRE(level >= 0 && level <= (int)P.levels.size(), H2_ERR_ARG, "bad level");
+        const int nlev = (int)P.levels.size() + (only_skel ? 0 : 1);
+        H2_REQUIRE(level >= 0 && level < nlev, H2_ERR_ARG, "bad level");
         const LevelStruct& S = level < (int)P.levels.size() ? P.levels[level] : P.toplev;
         if (nbox) *nbox = S.cnt;
         if (nblk) *nblk = S.nblocks();
@@ -493,20 +496,16 @@ int h2_plan_query_batch(int32_t nsys, const h2_matrix_desc* descs, int32_t level
     });
 }
 
+int h2_plan_query_batch(int32_t nsys, const h2_matrix_desc* descs, int32_t level, int64_t* nbox,
+                        int64_t* nblk, int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind,
+                        int32_t* state, int32_t* system) {
+    return plan_query_impl(nsys, descs, level, false, nbox, nblk, colour, row_ptr, col, kind, state, system);
+}
+
 int h2_plan_query(const h2_matrix_desc* desc, int32_t level, int64_t* nbox, int64_t* nblk,
                   int32_t* colour, int64_t* row_ptr, int64_t* col, int32_t* kind) {
     if (!desc) { set_error("null descriptor"); return H2_ERR_ARG; }
-    // the skeletonised levels only (the batch query also reaches the top-only level)
-    int64_t nb = 0;
-    int rc = h2_plan_query_batch(1, desc, level, &nb, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                 nullptr, nullptr);
-    if (rc != H2_OK) return rc;
-    std::vector<int32_t> st(nb);
-    rc = h2_plan_query_batch(1, desc, level, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                             st.data(), nullptr);
-    if (rc != H2_OK) return rc;
-    if (nb == 0 || st[0] != 1) { set_error("bad level"); return H2_ERR_ARG; }
-    return h2_plan_query_batch(1, desc, level, nbox, nblk, colour, row_ptr, col, kind, nullptr, nullptr);
+    return plan_query_impl(1, desc, level, true, nbox, nblk, colour, row_ptr, col, kind, nullptr, nullptr);
 }
 
 }  // extern "C"

@@ -9,10 +9,28 @@
 // close).  Everything here depends only on the block partition, so it is built once
 // per matrix; box sizes and ranks are applied per level by the driver.
 #include <algorithm>
+#include <thread>
 
 #include "h2rs_internal.h"
 
 namespace h2rs {
+
+// f(lo, hi) over [0, n) in contiguous ranges on the host's cores (the plan of a
+// million-point matrix walks tens of millions of block pairs)
+// (at least `grain` items per thread)
+template <class F>
+static void parallel_for(int64_t n, F f, int64_t grain = 16) {
+    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>(std::min<int64_t>(hw, 32), std::max<int64_t>(1, n / grain));
+    if (nt <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int64_t t = 1; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt);
+    f((int64_t)0, n / nt);
+    for (auto& x : th) x.join();
+}
 
 int LevelStruct::find(int i, int j) const {
     auto b = bcol.begin() + bptr[i];
@@ -74,91 +92,119 @@ static bool is_near(const LevelStruct& L, int i, int j) {
 
 // merged block list = near field U fill pattern (distance-two pairs + carried)
 static void block_list(LevelStruct& L, const std::vector<std::pair<int, int>>& carried) {
-    std::vector<std::vector<int>> rows(L.cnt);
-    for (int i = 0; i < L.cnt; ++i)
-        for (int e = L.nb_ptr[i]; e < L.nb_ptr[i + 1]; ++e) rows[i].push_back(L.nb_col[e]);
+    // fill of row j: k in N(i) outside N(j), for every eliminated i in N(j) (the near
+    // graph is symmetric, so these are the pairs j, k in N(i) of Sec. 2.1 step 3)
     std::vector<std::vector<int>> fill(L.cnt);
-    for (int i : L.skel_boxes)                    // only eliminated boxes create fill
-        for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
-            int j = L.nb_col[a];
-            for (int b = L.nb_ptr[i]; b < L.nb_ptr[i + 1]; ++b) {
-                int k = L.nb_col[b];
-                if (!is_near(L, j, k)) fill[j].push_back(k);
+    parallel_for(L.cnt, [&](int64_t lo, int64_t hi) {
+        for (int j = (int)lo; j < (int)hi; ++j)
+            for (int a = L.nb_ptr[j]; a < L.nb_ptr[j + 1]; ++a) {
+                const int i = L.nb_col[a];
+                if (L.state[i] != 1) continue;        // only eliminated boxes create fill
+                for (int b = L.nb_ptr[i]; b < L.nb_ptr[i + 1]; ++b) {
+                    const int k = L.nb_col[b];
+                    if (!is_near(L, j, k)) fill[j].push_back(k);
+                }
             }
-        }
+    });
     std::vector<std::vector<int>> carr(L.cnt);
     for (auto& pq : carried)
         if (!is_near(L, pq.first, pq.second)) {
             fill[pq.first].push_back(pq.second);
             carr[pq.first].push_back(pq.second);
         }
-    L.bptr.assign(L.cnt + 1, 0);
-    L.bcol.clear();
-    L.bkind.clear();
-    for (int i = 0; i < L.cnt; ++i) {
-        auto& f = fill[i];
-        std::sort(f.begin(), f.end());
-        f.erase(std::unique(f.begin(), f.end()), f.end());
-        std::vector<int> merged;
-        merged.reserve(rows[i].size() + f.size());
-        std::merge(rows[i].begin(), rows[i].end(), f.begin(), f.end(), std::back_inserter(merged));
-        for (int j : merged) {
-            L.bcol.push_back(j);
-            L.bkind.push_back(is_near(L, i, j) ? 0 : 1);
+    // merged rows (near field + fill, columns ascending) and their kinds
+    std::vector<std::vector<int>> merged(L.cnt);
+    std::vector<std::vector<int8_t>> kinds(L.cnt);
+    parallel_for(L.cnt, [&](int64_t lo, int64_t hi) {
+        for (int i = (int)lo; i < (int)hi; ++i) {
+            auto& f = fill[i];
+            std::sort(f.begin(), f.end());
+            f.erase(std::unique(f.begin(), f.end()), f.end());
+            auto& m = merged[i];
+            m.reserve(L.nb_ptr[i + 1] - L.nb_ptr[i] + f.size());
+            std::merge(L.nb_col.begin() + L.nb_ptr[i], L.nb_col.begin() + L.nb_ptr[i + 1], f.begin(), f.end(),
+                       std::back_inserter(m));
+            kinds[i].reserve(m.size());
+            for (int j : m) kinds[i].push_back(is_near(L, i, j) ? 0 : 1);
+            std::sort(carr[i].begin(), carr[i].end());
         }
-        L.bptr[i + 1] = (int)L.bcol.size();
-        std::sort(carr[i].begin(), carr[i].end());
-    }
+    });
+    L.bptr.assign(L.cnt + 1, 0);
+    for (int i = 0; i < L.cnt; ++i) L.bptr[i + 1] = L.bptr[i] + (int)merged[i].size();
+    L.bcol.resize(L.bptr[L.cnt]);
+    L.bkind.resize(L.bptr[L.cnt]);
+    parallel_for(L.cnt, [&](int64_t lo, int64_t hi) {
+        for (int i = (int)lo; i < (int)hi; ++i) {
+            std::copy(merged[i].begin(), merged[i].end(), L.bcol.begin() + L.bptr[i]);
+            std::copy(kinds[i].begin(), kinds[i].end(), L.bkind.begin() + L.bptr[i]);
+        }
+    });
     int nb = L.nblocks();
     L.btr.assign(nb, -1);
     L.first_touch.assign(nb, INT_MAX);
-    for (int i = 0; i < L.cnt; ++i)
-        for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
-            L.btr[b] = L.find(L.bcol[b], i);
-            if (L.bkind[b] == 1 &&
-                std::binary_search(carr[i].begin(), carr[i].end(), L.bcol[b]))
-                L.first_touch[b] = -1;
-        }
+    parallel_for(L.cnt, [&](int64_t lo, int64_t hi) {
+        for (int i = (int)lo; i < (int)hi; ++i)
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
+                L.btr[b] = L.find(L.bcol[b], i);
+                if (L.bkind[b] == 1 && std::binary_search(carr[i].begin(), carr[i].end(), L.bcol[b]))
+                    L.first_touch[b] = -1;
+            }
+    });
 }
 
-// Schur targets per colour (target-owned accumulation) and first touches of fill
+// Schur targets per colour (target-owned accumulation) and first touches of fill;
+// the colours are listed concurrently, then concatenated in colour order
 static void schur_lists(LevelStruct& L) {
+    struct Rec { int t, i, a, kpos; };
+    struct Part {
+        std::vector<int> tblk, tlen, ci, cA, ckpos;
+    };
+    std::vector<Part> parts(L.ncolour);
+    parallel_for(L.ncolour, [&](int64_t lo, int64_t hi) {
+        std::vector<Rec> recs;
+        for (int c = (int)lo; c < (int)hi; ++c) {
+            recs.clear();
+            for (int i : L.cboxes[c]) {
+                int n0 = L.nb_ptr[i], n1 = L.nb_ptr[i + 1];
+                for (int a = n0; a < n1; ++a) {
+                    int j = L.nb_col[a];
+                    int ablk = L.find(j, i);
+                    for (int b = n0; b < n1; ++b) recs.push_back({L.find(j, L.nb_col[b]), i, ablk, b - n0});
+                }
+            }
+            std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) {
+                return x.t != y.t ? x.t < y.t : x.i < y.i;
+            });
+            Part& P = parts[c];
+            for (size_t r = 0; r < recs.size(); ++r) {
+                if (r == 0 || recs[r].t != recs[r - 1].t) {
+                    P.tblk.push_back(recs[r].t);
+                    P.tlen.push_back(0);
+                }
+                ++P.tlen.back();
+                P.ci.push_back(recs[r].i);
+                P.cA.push_back(recs[r].a);
+                P.ckpos.push_back(recs[r].kpos);
+            }
+        }
+    }, 1);
     L.sch_cptr.assign(1, 0);
     L.sch_tblk.clear();
     L.sch_tptr.assign(1, 0);
     L.sch_ci.clear();
     L.sch_cA.clear();
     L.sch_ckpos.clear();
-    struct Rec { int t, i, a, kpos; };
-    std::vector<Rec> recs;
     for (int c = 0; c < L.ncolour; ++c) {
-        recs.clear();
-        for (int i : L.cboxes[c]) {
-            int n0 = L.nb_ptr[i], n1 = L.nb_ptr[i + 1];
-            for (int a = n0; a < n1; ++a) {
-                int j = L.nb_col[a];
-                int ablk = L.find(j, i);
-                for (int b = n0; b < n1; ++b) {
-                    int k = L.nb_col[b];
-                    int t = L.find(j, k);
-                    recs.push_back({t, i, ablk, b - n0});
-                    if (L.bkind[t] == 1 && L.first_touch[t] == INT_MAX) L.first_touch[t] = c;
-                }
-            }
+        const Part& P = parts[c];
+        for (size_t q = 0; q < P.tblk.size(); ++q) {
+            const int t = P.tblk[q];
+            L.sch_tblk.push_back(t);
+            L.sch_tptr.push_back(L.sch_tptr.back() + P.tlen[q]);
+            if (L.bkind[t] == 1 && L.first_touch[t] == INT_MAX) L.first_touch[t] = c;
         }
-        std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) {
-            return x.t != y.t ? x.t < y.t : x.i < y.i;
-        });
-        for (size_t r = 0; r < recs.size(); ++r) {
-            if (r == 0 || recs[r].t != recs[r - 1].t) {
-                if (r) L.sch_tptr.push_back((int)L.sch_ci.size());
-                L.sch_tblk.push_back(recs[r].t);
-            }
-            L.sch_ci.push_back(recs[r].i);
-            L.sch_cA.push_back(recs[r].a);
-            L.sch_ckpos.push_back(recs[r].kpos);
-        }
-        if (!recs.empty()) L.sch_tptr.push_back((int)L.sch_ci.size());
+        L.sch_ci.insert(L.sch_ci.end(), P.ci.begin(), P.ci.end());
+        L.sch_cA.insert(L.sch_cA.end(), P.cA.begin(), P.cA.end());
+        L.sch_ckpos.insert(L.sch_ckpos.end(), P.ckpos.begin(), P.ckpos.end());
         L.sch_cptr.push_back((int)L.sch_tblk.size());
     }
 }
@@ -167,11 +213,13 @@ static void schur_lists(LevelStruct& L) {
 static void solve_lists(LevelStruct& L) {
     L.nb_blk.resize(L.nb_col.size());
     L.nb_blkT.resize(L.nb_col.size());
-    for (int i = 0; i < L.cnt; ++i)
-        for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
-            L.nb_blk[a] = L.find(i, L.nb_col[a]);
-            L.nb_blkT[a] = L.find(L.nb_col[a], i);
-        }
+    parallel_for(L.cnt, [&](int64_t lo, int64_t hi) {
+        for (int i = (int)lo; i < (int)hi; ++i)
+            for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
+                L.nb_blk[a] = L.find(i, L.nb_col[a]);
+                L.nb_blkT[a] = L.find(L.nb_col[a], i);
+            }
+    });
     L.fl_cptr.assign(1, 0);
     L.fl_tbox.clear();
     L.fl_tptr.assign(1, 0);
@@ -257,21 +305,23 @@ static void close_lists(const HostStructure& H, LevelStruct& C, const LevelStruc
     C.cl_dblk.assign(4 * (size_t)nb, -1);
     C.cl_fblk.assign(4 * (size_t)nb, -1);
     C.cl_adm.assign(4 * (size_t)nb, -1);
-    for (int p = 0; p < P.cnt; ++p)
-        for (int b = P.bptr[p]; b < P.bptr[p + 1]; ++b) {
-            int q = P.bcol[b];
-            for (int a = 0; a < 2; ++a)
-                for (int bb = 0; bb < 2; ++bb) {
-                    int c = 2 * p + a, e = 2 * q + bb;
-                    int slot = 4 * b + 2 * a + bb;
-                    int blk = C.find(c, e);
-                    if (blk >= 0) {
-                        if (C.bkind[blk] == 0) C.cl_dblk[slot] = blk;
-                        else C.cl_fblk[slot] = blk;
+    parallel_for(P.cnt, [&](int64_t lo, int64_t hi) {
+        for (int p = (int)lo; p < (int)hi; ++p)
+            for (int b = P.bptr[p]; b < P.bptr[p + 1]; ++b) {
+                int q = P.bcol[b];
+                for (int a = 0; a < 2; ++a)
+                    for (int bb = 0; bb < 2; ++bb) {
+                        int c = 2 * p + a, e = 2 * q + bb;
+                        int slot = 4 * b + 2 * a + bb;
+                        int blk = C.find(c, e);
+                        if (blk >= 0) {
+                            if (C.bkind[blk] == 0) C.cl_dblk[slot] = blk;
+                            else C.cl_fblk[slot] = blk;
+                        }
+                        C.cl_adm[slot] = adm_entry(H, C.first + c, C.first + e);
                     }
-                    C.cl_adm[slot] = adm_entry(H, C.first + c, C.first + e);
-                }
-        }
+            }
+    });
 }
 
 // leaf near blocks come from A's inadmissible leaf entries
