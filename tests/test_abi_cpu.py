@@ -207,3 +207,28 @@ def test_plain_c_caller_builds_and_plans():
     assert "4 boxes, 14 blocks" in lines[1]
     assert lines[2] == "box 0 colour 0: 0 1 2f"          # distance-two fill through box 1
     assert "partition" in lines[-1]
+
+
+def test_binding_rejects_malformed_vectors():
+    """The binding only marshals: non-float64 or row-major right-hand sides are refused
+    before anything reaches the library (no GPU needed)."""
+    import torch
+    from paper_2509_11152_b300 import binding
+    with pytest.raises(TypeError):
+        binding._vec(torch.zeros(8, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        binding._vec(torch.zeros(8, 3, dtype=torch.float64))           # row-major (n, nrhs)
+    p, nrhs, ld, dev = binding._vec(binding.colmajor(torch.zeros(8, 3, dtype=torch.float64)))
+    assert nrhs == 3 and ld == 8 and dev == 0
+    p, nrhs, ld, dev = binding._vec(torch.zeros(8, dtype=torch.float64))
+    assert nrhs == 1 and ld == 8
+
+
+def test_every_declared_entry_point_is_documented():
+    """Each entry point of the header carries a comment block that states its errors or
+    its return value (the boundary's documentation contract)."""
+    txt = open(HEADER).read()
+    for name in _declared():
+        i = txt.index(name + "(")
+        before = txt[max(0, i - 1500):i]
+        assert "/*" in before, name
