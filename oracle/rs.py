@@ -183,21 +183,32 @@ def _project_box(i, Q, r, nbrs, D, F, frow, fcol):
         F[key] = B
 
 
-def _partial_lu(i, n, r, nbrs, sizes, D, F):
+def _partial_lu(i, n, r, nbrs, sizes, D, F, pivot="lu"):
     """Alg. 2 partialLU for box i: LU of D_RR, elementary factors, Schur update of
-    N(i) x N(i) (fill outside the near field goes to F), eliminated rows/cols zeroed."""
+    N(i) x N(i) (fill outside the near field goes to F), eliminated rows/cols zeroed.
+
+    pivot "lu": partial pivoting (the paper's dense LU).  pivot "cholesky" (a symmetric
+    variant for SPD matrices; the paper notes that the method keeps symmetry): D_RR =
+    L L^T and W_L = W_U^T, so only one of the two elementary factors needs storing."""
     WL, WU = {}, {}
     lu = None
     if r > 0:
         DRR = D[(i, i)][:r, :r].copy()
-        lu = sla.lu_factor(DRR, check_finite=True)
 
         def rows_of(j):                   # coordinates of j still in the matrix
             return slice(r, n) if j == i else slice(0, sizes[j])
 
-        for j in nbrs[i]:
-            WU[j] = sla.lu_solve(lu, D[(i, j)][:r, rows_of(j)])
-            WL[j] = sla.lu_solve(lu, D[(j, i)][rows_of(j), :r].T, trans=1).T
+        if pivot == "cholesky":
+            ch = sla.cho_factor(DRR, lower=True, check_finite=True)
+            lu = ("chol", ch[0])
+            for j in nbrs[i]:
+                WU[j] = sla.cho_solve(ch, D[(i, j)][:r, rows_of(j)])
+                WL[j] = WU[j].T
+        else:
+            lu = sla.lu_factor(DRR, check_finite=True)
+            for j in nbrs[i]:
+                WU[j] = sla.lu_solve(lu, D[(i, j)][:r, rows_of(j)])
+                WL[j] = sla.lu_solve(lu, D[(j, i)][rows_of(j), :r].T, trans=1).T
         for j in nbrs[i]:
             Dj = D[(j, i)][rows_of(j), :r]
             for kk in nbrs[i]:
@@ -212,7 +223,7 @@ def _partial_lu(i, n, r, nbrs, sizes, D, F):
     return lu, WL, WU
 
 
-def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None, method="qr"):
+def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None, method="qr", pivot="lu"):
     """Alg. 2 for one colour: augment every box from the same fill matrix, then
     project every box, then the partial LU of every box.  (Boxes of one colour share
     no near-field block, but two of them can share a fill block, so augmenting one
@@ -224,19 +235,20 @@ def _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook=None
     out = {}
     for i in C:
         n, kt = sizes[i], Vt[i].shape[1]
-        lu, WL, WU = _partial_lu(i, n, n - kt, nbrs, sizes, D, F)
+        lu, WL, WU = _partial_lu(i, n, n - kt, nbrs, sizes, D, F, pivot)
         out[i] = BoxFactor(n=n, k=V[i].shape[1], kt=kt, Q=Qs[i], lu=lu, nb=list(nbrs[i]), WL=WL, WU=WU)
     return out
 
 
 # ------------------------------------------------------------------ driver
-def factorize(A, eps_lu: float, norm_a: float, hook=None, augment: str = "qr") -> Factor:
+def factorize(A, eps_lu: float, norm_a: float, hook=None, augment: str = "qr", lu: str = "lu") -> Factor:
     """Alg. 1: factorise the H^2 matrix ``A`` (flat numpy storage) with threshold
     ``eps_lu``; ``norm_a`` is ``||A||_2`` (so ``eps_fill = eps_lu * norm_a``).
     ``hook(event, **state)``, if given, observes intermediate states (tests only).
-    ``augment``: "qr" (truncSVD option 2) or "gram" (Gram matrix + eigendecomposition)."""
-    if augment not in ("qr", "gram"):
-        raise ValueError(augment)
+    ``augment``: "qr" (truncSVD option 2) or "gram" (Gram matrix + eigendecomposition).
+    ``lu``: "lu" (partial pivoting) or "cholesky" (SPD matrices; W_L = W_U^T)."""
+    if augment not in ("qr", "gram") or lu not in ("lu", "cholesky"):
+        raise ValueError((augment, lu))
     eps_fill = eps_lu * norm_a
     d = A.depth
     t = A.top_level()
@@ -264,7 +276,7 @@ def factorize(A, eps_lu: float, norm_a: float, hook=None, augment: str = "qr") -
             hook("level_start", l=l, D=D, F=F, V=V, sizes=sizes)
         for c in range(max(colour) + 1):
             C = [i for i in range(cnt) if colour[i] == c]
-            done = _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook, augment)
+            done = _skeletonise_colour(C, nbrs, sizes, V, D, F, frow, fcol, eps_fill, hook, augment, lu)
             for i in C:
                 boxes[i] = done[i]
                 if hook is not None:
@@ -365,6 +377,9 @@ def solve(Z: Factor, b: np.ndarray) -> np.ndarray:
                     vec[j] -= bx.WL[j] @ vec[i][:r]
         for i, bx in enumerate(lv.boxes):             # diagonal forward (P, L)
             if bx.r:
+                if isinstance(bx.lu[0], str):
+                    vec[i][:bx.r] = sla.solve_triangular(bx.lu[1], vec[i][:bx.r], lower=True)
+                    continue
                 lu, piv = bx.lu
                 y = vec[i][:bx.r].copy()
                 for a, p in enumerate(piv):
@@ -389,6 +404,9 @@ def solve(Z: Factor, b: np.ndarray) -> np.ndarray:
         vec = low
         for i, bx in enumerate(lv.boxes):             # diagonal backward (U)
             if bx.r:
+                if isinstance(bx.lu[0], str):
+                    vec[i][:bx.r] = sla.solve_triangular(bx.lu[1], vec[i][:bx.r], lower=True, trans=1)
+                    continue
                 lu, _ = bx.lu
                 vec[i][:bx.r] = sla.solve_triangular(lu, vec[i][:bx.r], lower=False)
         for i in reversed(lv.order):
@@ -408,7 +426,9 @@ def slogdet(Z: Factor) -> float:
     s = 0.0
     for lv in Z.levels:
         for bx in lv.boxes:
-            if bx.r:
+            if bx.r and isinstance(bx.lu[0], str):               # D_RR = L L^T
+                s += 2.0 * float(np.sum(np.log(np.abs(np.diag(bx.lu[1])))))
+            elif bx.r:
                 s += float(np.sum(np.log(np.abs(np.diag(bx.lu[0])))))
     if Z.top_lu is not None:
         s += float(np.sum(np.log(np.abs(np.diag(Z.top_lu[0])))))

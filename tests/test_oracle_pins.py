@@ -274,3 +274,25 @@ def test_gram_augmentation_loses_what_squaring_hides():
     nq = rs._augment(V, F, 1e-11, "qr").shape[1] - k
     ng = rs._augment(V, F, 1e-11, "gram").shape[1] - k
     assert nq >= 11 and ng < nq, (nq, ng)
+
+
+@pytest.mark.parametrize("name,over", [("cov2d", dict(n=1024, leaf=32)), ("matern3d", dict(n=1024, leaf=32)),
+                                       ("sphere", dict(n=2048, leaf=64))])
+def test_cholesky_variant_equals_lu_on_spd_problems(name, over):
+    """On SPD matrices the redundant blocks stay SPD (they are Schur complements of
+    principal submatrices after an orthogonal change of basis), so D_RR = L L^T and
+    W_L = W_U^T: the symmetric variant gives the same solution and log-determinant as
+    the LU with partial pivoting, storing one elementary factor instead of two."""
+    pb = problem(name, **over)
+    A = pb.A.numpy()
+    b = rhs(A.n, 2, seed=21)
+    Zl = rs.factorize(A, 1e-8, pb.norm_a, lu="lu")
+    Zc = rs.factorize(A, 1e-8, pb.norm_a, lu="cholesky")
+    xl, xc = rs.solve(Zl, b), rs.solve(Zc, b)
+    assert np.linalg.norm(xc - xl) / np.linalg.norm(xl) <= 1e-10
+    assert abs(rs.slogdet(Zc) - rs.slogdet(Zl)) <= 1e-8 * abs(rs.slogdet(Zl))
+    # the LU factor's W_L is (up to rounding) the transpose of its W_U: the premise of
+    # half storage
+    bx = next(b_ for lv in Zl.levels for b_ in lv.boxes if b_.r > 0 and len(b_.nb) > 1)
+    for j in bx.nb:
+        assert np.allclose(bx.WL[j], bx.WU[j].T, rtol=1e-8, atol=1e-12)
