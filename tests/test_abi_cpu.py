@@ -232,3 +232,83 @@ def test_every_declared_entry_point_is_documented():
         i = txt.index(name + "(")
         before = txt[max(0, i - 1500):i]
         assert "/*" in before, name
+
+
+def _structure_only(pts, leaf, eta):
+    """An H^2 descriptor's index arrays from a point set (tree + partition only; rank 1
+    everywhere, values never read by the host planner) and an object the oracle's
+    structure functions accept."""
+    import types
+    from h2gen.tree import build_kdtree, dual_traversal
+    tree = build_kdtree(pts, leaf)
+    part = dual_traversal(tree, eta)
+    d = tree.depth
+    nn = (1 << (d + 1)) - 1
+    rank = np.ones(nn, np.int64)
+    leaves = np.arange((1 << d) - 1, nn)
+    U_off = np.concatenate([[0], np.cumsum(tree.size[leaves])]).astype(np.int64)
+    E_off = np.concatenate([[0, 0], np.arange(1, nn)]).astype(np.int64)
+    adm = np.concatenate([part.adm[l] for l in range(d + 1)], axis=0)
+    inad = np.concatenate([part.inad[l] for l in range(d + 1)], axis=0)
+    S = types.SimpleNamespace(
+        n=int(tree.size[0]), depth=d, node_start=tree.start, node_size=tree.size, rank=rank, U_off=U_off,
+        E_off=E_off, adm_ptr=np.concatenate([[0], np.cumsum(np.bincount(adm[:, 0], minlength=nn))]),
+        adm_col=adm[:, 1], S_off=np.arange(len(adm) + 1),
+        inad_ptr=np.concatenate([[0], np.cumsum(np.bincount(inad[:, 0], minlength=nn))]), inad_col=inad[:, 1],
+        D_off=np.concatenate([[0], np.cumsum(tree.size[part.inad[d][:, 0]] * tree.size[part.inad[d][:, 1]])]),
+        U=np.zeros(1), E=np.zeros(1), S=np.zeros(1), D=np.zeros(1))
+
+    def top_level():
+        for l in range(d + 1):
+            f, c = (1 << l) - 1, 1 << l
+            if S.adm_ptr[f + c] - S.adm_ptr[f] > 0:
+                return l
+        return None
+    S.top_level = top_level
+    return S
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_plan_matches_oracle_on_random_structures(seed):
+    """Random point sets (2D / 3D, uniform or clustered), leaf sizes and admissibility
+    parameters: the library's host plan equals the oracle's level structure bit for
+    bit at every skeletonised level."""
+    import ctypes
+    from paper_2509_11152_b300 import binding
+    rng = np.random.default_rng(1000 + seed)
+    dim = int(rng.integers(2, 4))
+    n = int(rng.integers(200, 3000))
+    pts = rng.random((n, dim))
+    if seed % 2:                                       # clustered: uneven box geometry
+        pts = np.concatenate([pts[: n // 2] * 0.2, pts[n // 2:]])
+    leaf = int(rng.choice([8, 16, 32, 64]))
+    eta = float(rng.choice([0.5, 0.7, 1.0, 2.0]))
+    A = _structure_only(pts, leaf, eta)
+    desc = binding.h2_matrix_desc()
+    desc.n = A.n
+    desc.depth = A.depth
+    keep = {}
+    for name in ("node_start", "node_size", "rank", "U_off", "E_off", "adm_ptr", "adm_col", "S_off",
+                 "inad_ptr", "inad_col", "D_off"):
+        arr = np.ascontiguousarray(np.asarray(getattr(A, name), np.int64))
+        keep[name] = arr
+        setattr(desc, name, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    for name in ("U", "E", "S", "D"):
+        setattr(desc, name, A.U.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    lib = binding.lib()
+    levels = _oracle_levels(A) if A.top_level() is not None else []
+    assert len(levels) >= 1 or A.top_level() is None
+    for li, (colour, lay) in enumerate(levels):
+        nbox, nblk = ctypes.c_int64(), ctypes.c_int64()
+        assert lib.h2_plan_query(ctypes.byref(desc), li, ctypes.byref(nbox), ctypes.byref(nblk),
+                                 None, None, None, None) == 0, binding.lib().h2_last_error()
+        col_ = np.zeros(nbox.value, np.int32)
+        rp = np.zeros(nbox.value + 1, np.int64)
+        cl = np.zeros(nblk.value, np.int64)
+        kd = np.zeros(nblk.value, np.int32)
+        lib.h2_plan_query(ctypes.byref(desc), li, None, None, binding._ptr(col_, ctypes.c_int32),
+                          binding._ptr(rp, ctypes.c_int64), binding._ptr(cl, ctypes.c_int64),
+                          binding._ptr(kd, ctypes.c_int32))
+        assert np.array_equal(col_, np.asarray(colour, np.int32))
+        assert np.array_equal(rp, lay["row_ptr"]) and np.array_equal(cl, lay["col"])
+        assert np.array_equal(kd, lay["kind"].astype(np.int32))
