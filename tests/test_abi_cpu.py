@@ -239,6 +239,7 @@ def _structure_only(pts, leaf, eta):
     everywhere, values never read by the host planner) and an object the oracle's
     structure functions accept."""
     import types
+    import torch
     from h2gen.tree import build_kdtree, dual_traversal
     tree = build_kdtree(pts, leaf)
     part = dual_traversal(tree, eta)
@@ -256,7 +257,8 @@ def _structure_only(pts, leaf, eta):
         adm_col=adm[:, 1], S_off=np.arange(len(adm) + 1),
         inad_ptr=np.concatenate([[0], np.cumsum(np.bincount(inad[:, 0], minlength=nn))]), inad_col=inad[:, 1],
         D_off=np.concatenate([[0], np.cumsum(tree.size[part.inad[d][:, 0]] * tree.size[part.inad[d][:, 1]])]),
-        U=np.zeros(1), E=np.zeros(1), S=np.zeros(1), D=np.zeros(1))
+        U=torch.zeros(1, dtype=torch.float64), E=torch.zeros(1, dtype=torch.float64),
+        S=torch.zeros(1, dtype=torch.float64), D=torch.zeros(1, dtype=torch.float64))
 
     def top_level():
         for l in range(d + 1):
@@ -294,7 +296,7 @@ def test_plan_matches_oracle_on_random_structures(seed):
         keep[name] = arr
         setattr(desc, name, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
     for name in ("U", "E", "S", "D"):
-        setattr(desc, name, A.U.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        setattr(desc, name, ctypes.cast(ctypes.c_void_p(A.U.data_ptr()), ctypes.POINTER(ctypes.c_double)))
     lib = binding.lib()
     levels = _oracle_levels(A) if A.top_level() is not None else []
     assert len(levels) >= 1 or A.top_level() is None
@@ -312,3 +314,34 @@ def test_plan_matches_oracle_on_random_structures(seed):
         assert np.array_equal(col_, np.asarray(colour, np.int32))
         assert np.array_equal(rp, lay["row_ptr"]) and np.array_equal(cl, lay["col"])
         assert np.array_equal(kd, lay["kind"].astype(np.int32))
+
+
+def test_batch_plan_on_random_forests():
+    """Random batches of random structures (different depths and tops): at every forest
+    level each system's boxes, colours, rows and states equal its own plan."""
+    from paper_2509_11152_b300 import h2_plan_query, h2_plan_query_batch
+    rng = np.random.default_rng(77)
+    for trial in range(3):
+        As = []
+        for z in range(int(rng.integers(2, 6))):
+            dim = int(rng.integers(2, 4))
+            pts = rng.random((int(rng.integers(100, 2500)), dim))
+            As.append(_structure_only(pts, int(rng.choice([16, 32])), float(rng.choice([0.7, 1.0]))))
+        nlev = [0 if A.top_level() is None else A.depth - A.top_level() + 1 for A in As]
+        for a in range(max(nlev) + 1):
+            q = h2_plan_query_batch(As, a)
+            for z, A in enumerate(As):
+                boxes = np.flatnonzero(q["system"] == z)
+                if a > A.depth:
+                    assert len(boxes) == 0
+                    continue
+                assert np.array_equal(boxes, np.arange(boxes[0], boxes[0] + len(boxes)))
+                if a < nlev[z]:
+                    s1 = h2_plan_query(A, a)
+                    assert (q["state"][boxes] == 1).all()
+                    assert np.array_equal(q["colour"][boxes], s1["colour"])
+                    for i, bi in enumerate(boxes):
+                        r = q["col"][q["row_ptr"][bi]:q["row_ptr"][bi + 1]] - boxes[0]
+                        assert np.array_equal(r, s1["col"][s1["row_ptr"][i]:s1["row_ptr"][i + 1]])
+                else:
+                    assert (q["state"][boxes] == (2 if a == nlev[z] else 0)).all()
