@@ -15,6 +15,10 @@ Steps (the construction the paper takes from Borm & Garcke, ref. borm07):
    ``sigma_j > eps * sigma_1`` per cluster, with the new bases nested in the new
    child bases; couplings are projected onto the new bases.
 
+A global low-rank update ``W W^T`` (the paper's LRU problem, Sec. 3) enters at step 1
+as ``q`` extra basis columns per cluster (identity transfers and couplings) and in
+the near-field blocks, and is compressed together with the kernel part.
+
 The result is a symmetric H^2 matrix with orthonormal nested bases:
 ``A_st = U_s S_st U_t^T`` on admissible pairs and dense near-field blocks on the
 inadmissible leaf pairs.  Everything is float64 torch on a chosen device.
@@ -150,9 +154,15 @@ class _Clock:
 
 
 def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, kern: Kernel,
-                 p0: int, eps: float, device="cpu", chunk: int = 2048):
+                 p0: int, eps: float, device="cpu", chunk: int = 2048, lowrank: np.ndarray | None = None):
     """Build the H^2 matrix; returns a dict of per-level padded tensors (see
-    ``h2matrix.H2Matrix.from_levels``)."""
+    ``h2matrix.H2Matrix.from_levels``).
+
+    ``lowrank`` (n x q, original point order) adds the update ``W W^T`` to the whole
+    matrix.  Every cluster's interpolation basis is extended by its rows of ``W``
+    (``[L_t, W_t]``), so transfers become ``diag(E, I_q)`` and couplings
+    ``diag(S, I_q)``, and the near-field blocks get ``W_s W_t^T``; the
+    orthogonalisation and compression below then treat it like any other basis."""
     dev = torch.device(device)
     clock = _Clock(dev)
     d = tree.depth
@@ -171,6 +181,21 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
     L0 = _lagrange_nd(xl, centre[leaf_ids], half[leaf_ids], order[d])   # (nl, mmax, k0)
     _, valid = _pad_points(pts, tree, leaf_ids, mmax)
     L0 = L0 * valid.unsqueeze(-1)
+    q = 0
+    if lowrank is not None:
+        Wt = torch.as_tensor(lowrank[tree.perm], dtype=torch.float64, device=dev)   # tree order
+        q = Wt.shape[1]
+        Wl, _ = _pad_points(Wt, tree, leaf_ids, mmax)                              # zero padded
+        L0 = torch.cat([L0, Wl], dim=2)
+
+    def with_identity(X):
+        """``diag(X, I_q)`` for a batch of matrices (X itself when q = 0)."""
+        if q == 0:
+            return X
+        out = torch.zeros(X.shape[:-2] + (X.shape[-2] + q, X.shape[-1] + q), dtype=X.dtype, device=dev)
+        out[..., :X.shape[-2], :X.shape[-1]] = X
+        out[..., X.shape[-2]:, X.shape[-1]:] = torch.eye(q, dtype=X.dtype, device=dev)
+        return out
     Uq, Rr = _qr(L0)
     U = {d: Uq}                   # orthonormal leaf basis (nl, mmax, r_d)
     R = {d: Rr}                   # (cnt, r_l, k0_l)
@@ -181,7 +206,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
         # parent Lagrange polynomials at child Chebyshev nodes
         xi = _cheb_points(centre[ids], half[ids], order[l])             # (cnt, k0_l, dim)
         pidx = torch.as_tensor((ids - 1) // 2, device=dev)
-        E0 = _lagrange_nd(xi, centre[pidx], half[pidx], order[l - 1])   # (cnt, k0_l, k0_{l-1})
+        E0 = with_identity(_lagrange_nd(xi, centre[pidx], half[pidx], order[l - 1]))   # (cnt, k0_l, k0_{l-1})
         RE = R[l] @ E0                                                  # (cnt, r_l, k0_{l-1})
         stacked = torch.cat([RE[0::2], RE[1::2]], dim=1)                # (cntp, 2 r_l, k0_{l-1})
         Qp, Rp = _qr(stacked)
@@ -195,7 +220,7 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
         t = torch.as_tensor(pr[:, 1], device=dev)
         xs = _cheb_points(centre[s], half[s], order[l])
         xt = _cheb_points(centre[t], half[t], order[l])
-        S0 = kern(torch.cdist(xs, xt, compute_mode="donot_use_mm_for_euclid_dist"))
+        S0 = with_identity(kern(torch.cdist(xs, xt, compute_mode="donot_use_mm_for_euclid_dist")))
         first = (1 << l) - 1
         Rs = R[l][s - first]
         Rt = R[l][t - first]
@@ -301,6 +326,10 @@ def construct_h2(points: np.ndarray, tree: ClusterTree, part: BlockPartition, ke
         blk = near_block(kern, xs, xt, same=False)
         blk_same = near_block(kern, xs, xt, same=True)
         blk = torch.where(same.view(-1, 1, 1), blk_same, blk)
+        if q:
+            Ws, _ = _pad_points(Wt, tree, sub[:, 0], mmax)
+            Wu, _ = _pad_points(Wt, tree, sub[:, 1], mmax)
+            blk = blk + Ws @ Wu.transpose(1, 2)
         blk = blk * (vs.unsqueeze(2) & vt.unsqueeze(1))
         Dn.append(blk)
     Dnear = torch.cat(Dn, dim=0) if Dn else torch.zeros((0, mmax, mmax), dtype=torch.float64, device=dev)

@@ -1,6 +1,6 @@
 """The workloads: point set + kernel + tree/admissibility parameters + tolerance.
 
-``WORKLOADS`` holds the five problem families at their full sizes; tests build
+``WORKLOADS`` holds the problem families at their full sizes; tests build
 smaller members of the same families through :func:`make_problem` overrides.
 Construction tolerance is one tenth of the factorisation tolerance, as in the
 paper's Table 1 (``eps = eps_lu / 10``).
@@ -17,7 +17,7 @@ import torch
 from . import points as P
 from .construct import construct_h2, spectral_norm
 from .h2matrix import H2Matrix
-from .kernels import Kernel, laplace2d_cell_average
+from .kernels import Kernel, helmholtz3d_cell_average, laplace2d_cell_average
 from .tree import build_kdtree, dual_traversal
 
 
@@ -45,7 +45,14 @@ WORKLOADS = {
     "sphere": Workload("sphere", 1 << 20, "sphere", 128, 1.0, 1e-5, 1, 4),
     # one system of the uneven batch of Gaussian-kernel problems
     "gauss3d": Workload("gauss3d", 8192, "gauss3d", 64, 1.0, 1e-6, 4, 4),
+    # 3D Helmholtz volume IE cos(3r)/r on a 32^3 cubic lattice (Table 1 parameters)
+    "helmholtz3d": Workload("helmholtz3d", 32768, "helmholtz3d", 64, 0.7, 1e-6, 1, 4),
+    # 3D exponential covariance plus a random rank-32 update (Table 1 "LRU" parameters)
+    "lru3d": Workload("lru3d", 32768, "lru3d", 128, 0.9, 1e-7, 1, 4),
 }
+
+HELMHOLTZ_KAPPA = 3.0     # wavenumber of the Helmholtz IE, fixed as the lattice is refined
+LRU_RANK = 32             # rank of the global update of the LRU problem
 
 
 def family_points_kernel(w: Workload):
@@ -63,6 +70,14 @@ def family_points_kernel(w: Workload):
         h = 1.0 / side
         return (P.jittered_grid_2d(side, 0.25, w.seed),
                 Kernel("laplace2d", 1.0, laplace2d_cell_average(h) + 1e-4))
+    if w.family == "helmholtz3d":
+        side = int(round(n ** (1.0 / 3.0)))
+        assert side ** 3 == n, "helmholtz3d needs a cubic number of points"
+        h = 1.0 / side
+        diag = helmholtz3d_cell_average(h, HELMHOLTZ_KAPPA) + 1e-2
+        return P.cubic_lattice(side), Kernel("helmholtz3d", 1.0, diag, HELMHOLTZ_KAPPA)
+    if w.family == "lru3d":
+        return P.uniform_box(n, 3, w.seed), Kernel("exp", 0.2, 1.0 + 1e-2)
     if w.family == "sphere":
         # regularised diagonal 1/(4 pi h): h = rho/2 with rho the radius of a disk of
         # area 4 pi/n (one point's share of the sphere), so the diagonal equals the
@@ -70,6 +85,14 @@ def family_points_kernel(w: Workload):
         h = 1.0 / math.sqrt(n)
         return P.fibonacci_sphere(n, 1e-3, w.seed), Kernel("laplace3d", 1.0, 1.0 / (4.0 * math.pi * h))
     raise ValueError(w.family)
+
+
+def family_lowrank(w: Workload):
+    """Factor ``W`` (original point order) of the global update ``W W^T`` of a
+    workload, or None."""
+    if w.family == "lru3d":
+        return P.low_rank_factor(w.n, LRU_RANK, w.seed)
+    return None
 
 
 @dataclass
@@ -89,7 +112,7 @@ def make_problem(name: str, device="cpu", **over) -> Problem:
     tree = build_kdtree(pts, w.leaf)
     part = dual_traversal(tree, w.eta)
     t_tree = time.perf_counter() - t0
-    lev = construct_h2(pts, tree, part, kern, w.p0, w.tol / 10.0, device=device)
+    lev = construct_h2(pts, tree, part, kern, w.p0, w.tol / 10.0, device=device, lowrank=family_lowrank(w))
     t1 = time.perf_counter()
     norm_a = spectral_norm(tree, part, lev)
     t_norm = time.perf_counter() - t1

@@ -8,8 +8,8 @@ import scipy.integrate as si
 import torch
 
 from h2gen import points as P
-from h2gen.kernels import Kernel, laplace2d_cell_average, near_block
-from h2gen.problems import WORKLOADS, family_points_kernel, make_problem
+from h2gen.kernels import Kernel, helmholtz3d_cell_average, laplace2d_cell_average, near_block
+from h2gen.problems import WORKLOADS, family_lowrank, family_points_kernel, make_problem
 from h2gen.tree import admissible, build_kdtree, dual_traversal
 from dataclasses import replace
 
@@ -42,12 +42,42 @@ def test_laplace_cell_average_matches_quadrature():
     assert abs(4 * val / h**2 - laplace2d_cell_average(h)) < 1e-9
 
 
+def test_helmholtz_cell_average_matches_quadrature():
+    """The flux form of the cell average against (a) the closed form of the mean of
+    1/r over a cube at kappa = 0 and (b) adaptive cubature of cos(kappa r)/r over one
+    octant (the singularity at its corner), at the lattice spacings of the 3D
+    Helmholtz problem and far outside them."""
+    J = 2 * math.log((1 + math.sqrt(3)) / math.sqrt(2)) - math.pi / 6
+    for h in (1.0, 1 / 32):
+        assert helmholtz3d_cell_average(h, 0.0) == pytest.approx(3 * J / h, rel=1e-14)
+    for h, kappa in ((1 / 16, 3.0), (1 / 64, 3.0), (1.0, 3.0), (0.5, 10.0), (1.0, 1e-4)):
+        def f(z, y, x):
+            r = math.sqrt(x * x + y * y + z * z)
+            return math.cos(kappa * r) / r
+        a = h / 2
+        val, _ = si.tplquad(f, 0, a, 0, a, 0, a, epsabs=1e-14, epsrel=1e-12)
+        assert helmholtz3d_cell_average(h, kappa) == pytest.approx(8 * val / h**3, rel=1e-11)
+
+
 def test_kernel_values():
     r = torch.tensor([0.5], dtype=torch.float64)
     assert float(Kernel("exp", 0.1)(r)) == pytest.approx(math.exp(-5.0))
     s = math.sqrt(3) * 0.5 / 0.2
     assert float(Kernel("matern32", 0.2)(r)) == pytest.approx((1 + s) * math.exp(-s))
     assert float(Kernel("laplace3d")(r)) == pytest.approx(1 / (2 * math.pi))
+    assert float(Kernel("helmholtz3d", kappa=3.0)(r)) == pytest.approx(math.cos(1.5) / 0.5)
+
+
+def test_cubic_lattice_and_low_rank_factor():
+    x = P.cubic_lattice(12)
+    assert x.shape == (1728, 3)
+    for c in range(3):
+        assert np.allclose(np.unique(x[:, c]), (np.arange(12) + 0.5) / 12)
+    W = P.low_rank_factor(4096, 32, seed=3)
+    assert W.shape == (4096, 32)
+    assert np.array_equal(W, P.low_rank_factor(4096, 32, seed=3))
+    assert not np.array_equal(W, P.low_rank_factor(4096, 32, seed=4))
+    assert np.mean(np.sum(W * W, axis=1)) == pytest.approx(1.0, abs=0.02)
 
 
 def test_kdtree_structure():
@@ -89,6 +119,8 @@ def test_partition_covers_matrix_once():
     ("sphere", dict(n=2048, leaf=64), 1e-3),
     ("matern3d", dict(n=2048, leaf=32), 1e-3),
     ("gauss3d", dict(n=2048), 1e-3),
+    ("helmholtz3d", dict(n=1728, leaf=32), 1e-4),
+    ("lru3d", dict(n=2048, leaf=32), 1e-4),
 ])
 def test_h2_matches_dense_kernel(name, over, tol):
     pb = problem(name, **over)
@@ -96,10 +128,13 @@ def test_h2_matches_dense_kernel(name, over, tol):
     w = replace(WORKLOADS[name], **over)
     pts, kern = family_points_kernel(w)
     X = torch.as_tensor(pts[A.perm])
-    K = near_block(kern, X, X, same=True)
+    K = near_block(kern, X, X, same=True).numpy()
+    W = family_lowrank(w)
+    if W is not None:                                  # the global update W W^T
+        K = K + W[A.perm] @ W[A.perm].T
     from oracle.dense import expand
     M = expand(A.numpy())
-    assert np.linalg.norm(M - K.numpy()) / np.linalg.norm(K.numpy()) < tol
+    assert np.linalg.norm(M - K) / np.linalg.norm(K) < tol
     assert np.allclose(M, M.T, atol=1e-12 * np.abs(M).max())
     # spectral norm estimate against the dense symmetric eigenvalues
     ev = np.linalg.eigvalsh(M)

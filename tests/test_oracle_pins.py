@@ -38,6 +38,8 @@ def _dense_solution(A, b):
     ("sphere", dict(n=2048, leaf=64)),
     ("matern3d", dict(n=1024, leaf=32)),
     ("gauss3d", dict(n=1500, leaf=32)),
+    ("helmholtz3d", dict(n=1728, leaf=32)),             # indefinite (oscillatory kernel)
+    ("lru3d", dict(n=2048, leaf=32)),                   # covariance + rank-32 update
 ])
 def test_zero_truncation_equals_dense_solve(name, over):
     pb = problem(name, **over)
@@ -80,6 +82,26 @@ def test_backward_error_tracks_tolerance():
     # once the threshold is below the fill's singular values, lowering it
     # lowers the error (above that no fill basis vector is kept at all)
     assert errs[0] >= errs[1] > errs[2] > errs[3]
+
+
+@pytest.mark.parametrize("name,over,eps", [
+    ("helmholtz3d", dict(n=1728, leaf=32), 1e-6),
+    ("lru3d", dict(n=2048, leaf=32), 1e-7),
+])
+def test_backward_error_tracks_tolerance_on_ie_and_lru(name, over, eps):
+    """The Helmholtz IE and the low-rank-updated covariance at their Table 1
+    tolerances: backward error below 10 eps_lu, and lower at a hundredfold smaller
+    threshold."""
+    pb = problem(name, **over)
+    A = pb.A.numpy()
+    b = rhs(A.n, 1, seed=2)
+    errs = []
+    for e in (eps, eps / 100):
+        Z = rs.factorize(A, e, pb.norm_a)
+        nw, _ = dense.backward_error(A, rs.solve(Z, b), b, pb.norm_a)
+        assert nw < 10 * e
+        errs.append(nw)
+    assert errs[1] < errs[0]
 
 
 def test_projection_identities():
