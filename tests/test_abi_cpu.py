@@ -54,6 +54,8 @@ def _oracle_levels(A):
     ("matern3d", dict(n=2048, leaf=32)),
     ("sphere", dict(n=8192, leaf=64)),
     ("gauss3d", dict(n=1500, leaf=32)),
+    ("helmholtz3d", dict(n=4096, leaf=64)),
+    ("lru3d", dict(n=4096, leaf=64)),
 ])
 def test_plan_matches_oracle_structure(name, over):
     from paper_2509_11152_b300 import h2_plan_query

@@ -50,6 +50,8 @@ CASES = [
     ("matern3d", dict(n=2048, leaf=32), 1e-6),
     ("sphere", dict(n=4096, leaf=64), 1e-5),
     ("gauss3d", dict(n=1500, leaf=32), 1e-6),            # ragged leaves (46/47 points)
+    ("helmholtz3d", dict(n=4096, leaf=64), 1e-6),         # indefinite oscillatory IE, 16^3 lattice
+    ("lru3d", dict(n=4096, leaf=64), 1e-7),               # covariance + rank-32 update
 ]
 IDS = [f"{c[0]}-{c[1].get('n', 'full')}" for c in CASES]
 
