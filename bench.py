@@ -210,12 +210,25 @@ def _rhs(n, nrhs, device):
 
 
 # ------------------------------------------------------------------ oracle timing
+def _lattice_size(workload: str, n: int) -> int:
+    """Largest size <= n that the workload's point set admits (a square number of
+    points for the 2D lattice, a cube for the 3D lattice)."""
+    from h2gen import WORKLOADS
+    dim = {"laplace2d": 2, "helmholtz3d": 3}.get(WORKLOADS[workload].family, 0)
+    if not dim:
+        return n
+    side = int(round(n ** (1.0 / dim)))
+    while side ** dim > n:
+        side -= 1
+    return side ** dim
+
+
 def _oracle_sample(workload: str, n_sample: int):
     """Oracle factor + float64 refined solve on a smaller member of the workload's
     family; returns (seconds, n_sample, iterations, berr)."""
     from h2gen import make_problem, rhs
     from oracle import dense, rs
-    pb = make_problem(workload, n=n_sample)
+    pb = make_problem(workload, n=_lattice_size(workload, n_sample))
     A = pb.A.numpy()
     b = rhs(A.n, pb.workload.nrhs, seed=0)
     t0 = time.perf_counter()
