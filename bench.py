@@ -45,7 +45,9 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sphere")
-    p.add_argument("--n", type=int, default=0, help="override the problem size (testing only)")
+    p.add_argument("--n", "--size", dest="n", type=int, default=0,
+                   help="override the problem size (testing only; spell it --size under torchrun, whose own "
+                        "parser takes --n for an abbreviation of its options)")
     p.add_argument("--nrhs", type=int, default=0, help="override the number of right-hand sides")
     p.add_argument("--fp64-arm", type=int, default=1, help="also time the float64 factor arm once")
     p.add_argument("--e2e-steps", type=int, default=1)
