@@ -88,6 +88,13 @@ void read_structure(const h2_matrix_desc* d, HostStructure& H) {
         }
         H2_REQUIRE(self, H2_ERR_ARG, "every node must be in its own near field");
     }
+    // the matrix is symmetric, so is its near field: (g, t) inadmissible => (t, g)
+    for (int64_t g = 0; g < nn; ++g)
+        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
+            const int64_t t = H.inad_col[e];
+            H2_REQUIRE(std::binary_search(H.inad_col.begin() + H.inad_ptr[t], H.inad_col.begin() + H.inad_ptr[t + 1], g),
+                       H2_ERR_ARG, "the inadmissible pattern is not symmetric");
+        }
 }
 
 // append a chunk, merging it with the previous one when both ranges continue it

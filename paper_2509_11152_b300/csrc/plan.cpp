@@ -9,27 +9,70 @@
 // close).  Everything here depends only on the block partition, so it is built once
 // per matrix; box sizes and ranks are applied per level by the driver.
 #include <algorithm>
+#include <atomic>
+#include <exception>
+#include <mutex>
 #include <thread>
 
 #include "h2rs_internal.h"
 
 namespace h2rs {
 
+// job(t) for t in [0, nt): t = 0 on the calling thread, the others on their own
+// threads (inline when no thread can be had).  An exception thrown by any job (a
+// failed host allocation, an invalid structure) is rethrown here once all have joined.
+template <class J>
+static void run_threads(int64_t nt, J job) {
+    std::exception_ptr err;
+    std::mutex mu;
+    auto guarded = [&](int64_t t) {
+        try {
+            job(t);
+        } catch (...) {
+            std::lock_guard<std::mutex> g(mu);
+            if (!err) err = std::current_exception();
+        }
+    };
+    std::vector<std::thread> th;
+    for (int64_t t = 1; t < nt; ++t) {
+        try {
+            th.emplace_back(guarded, t);
+        } catch (...) {
+            guarded(t);
+        }
+    }
+    guarded(0);
+    for (auto& x : th) x.join();
+    if (err) std::rethrow_exception(err);
+}
+
+static int64_t host_threads() {
+    return std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 32);
+}
+
 // f(lo, hi) over [0, n) in contiguous ranges on the host's cores (the plan of a
-// million-point matrix walks tens of millions of block pairs)
-// (at least `grain` items per thread)
+// million-point matrix walks tens of millions of block pairs), at least `grain` items
+// per thread
 template <class F>
 static void parallel_for(int64_t n, F f, int64_t grain = 16) {
-    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
-    const int64_t nt = std::min<int64_t>(std::min<int64_t>(hw, 32), std::max<int64_t>(1, n / grain));
+    const int64_t nt = std::min<int64_t>(host_threads(), std::max<int64_t>(1, n / grain));
     if (nt <= 1) {
         f((int64_t)0, n);
         return;
     }
-    std::vector<std::thread> th;
-    for (int64_t t = 1; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt);
-    f((int64_t)0, n / nt);
-    for (auto& x : th) x.join();
+    run_threads(nt, [&](int64_t t) { f(n * t / nt, n * (t + 1) / nt); });
+}
+
+// f(item, scratch) for every item in [0, n), handed out one at a time to the host's
+// cores (for items of very different cost, e.g. colours); each thread owns one S
+template <class S, class F>
+static void parallel_items(int64_t n, F f) {
+    const int64_t nt = std::min<int64_t>(host_threads(), n);
+    std::atomic<int64_t> next{0};
+    run_threads(nt, [&](int64_t) {
+        S scratch;
+        for (int64_t c; (c = next.fetch_add(1)) < n;) f(c, scratch);
+    });
 }
 
 int LevelStruct::find(int i, int j) const {
@@ -152,61 +195,105 @@ static void block_list(LevelStruct& L, const std::vector<std::pair<int, int>>& c
     });
 }
 
+static void atomic_min(int* p, int v) {
+    int cur = __atomic_load_n(p, __ATOMIC_RELAXED);
+    while (v < cur && !__atomic_compare_exchange_n(p, &cur, v, true, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+    }
+}
+
 // Schur targets per colour (target-owned accumulation) and first touches of fill;
-// the colours are listed concurrently, then concatenated in colour order
+// the colours are listed concurrently, then concatenated in colour order.  Within a
+// colour the targets are ascending and each target's contributors ascending in i: the
+// contributions are generated box by box (boxes ascending) and bucketed by target.
 static void schur_lists(LevelStruct& L) {
-    struct Rec { int t, i, a, kpos; };
     struct Part {
         std::vector<int> tblk, tlen, ci, cA, ckpos;
     };
+    struct Scratch {
+        std::vector<int> cnt, pos, rt, ri, ra, rk;
+    };
     std::vector<Part> parts(L.ncolour);
-    parallel_for(L.ncolour, [&](int64_t lo, int64_t hi) {
-        std::vector<Rec> recs;
-        for (int c = (int)lo; c < (int)hi; ++c) {
-            recs.clear();
-            for (int i : L.cboxes[c]) {
-                int n0 = L.nb_ptr[i], n1 = L.nb_ptr[i + 1];
-                for (int a = n0; a < n1; ++a) {
-                    int j = L.nb_col[a];
-                    int ablk = L.find(j, i);
-                    for (int b = n0; b < n1; ++b) recs.push_back({L.find(j, L.nb_col[b]), i, ablk, b - n0});
+    const int nb = L.nblocks();
+    parallel_items<Scratch>(L.ncolour, [&](int64_t c, Scratch& s) {
+        if ((int)s.cnt.size() != nb) {
+            s.cnt.assign(nb, 0);
+            s.pos.resize(nb);
+        }
+        s.rt.clear(); s.ri.clear(); s.ra.clear(); s.rk.clear();
+        for (int i : L.cboxes[c]) {
+            const int n0 = L.nb_ptr[i], n1 = L.nb_ptr[i + 1];
+            for (int a = n0; a < n1; ++a) {
+                const int j = L.nb_col[a];
+                const int ablk = L.find(j, i);
+                // every k in N(i) is a block of row j (near field or fill): walk the row
+                int p = L.bptr[j];
+                const int pe = L.bptr[j + 1];
+                for (int b = n0; b < n1; ++b) {
+                    const int k = L.nb_col[b];
+                    while (p < pe && L.bcol[p] < k) ++p;
+                    H2_REQUIRE(p < pe && L.bcol[p] == k && ablk >= 0, H2_ERR_ARG,
+                               "the near field is not symmetric");
+                    ++s.cnt[p];
+                    s.rt.push_back(p);
+                    s.ri.push_back(i);
+                    s.ra.push_back(ablk);
+                    s.rk.push_back(b - n0);
                 }
             }
-            std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) {
-                return x.t != y.t ? x.t < y.t : x.i < y.i;
-            });
-            Part& P = parts[c];
-            for (size_t r = 0; r < recs.size(); ++r) {
-                if (r == 0 || recs[r].t != recs[r - 1].t) {
-                    P.tblk.push_back(recs[r].t);
-                    P.tlen.push_back(0);
-                }
-                ++P.tlen.back();
-                P.ci.push_back(recs[r].i);
-                P.cA.push_back(recs[r].a);
-                P.ckpos.push_back(recs[r].kpos);
+        }
+        Part& P = parts[c];
+        int run = 0;
+        for (int t = 0; t < nb; ++t)
+            if (s.cnt[t]) {
+                P.tblk.push_back(t);
+                P.tlen.push_back(s.cnt[t]);
+                s.pos[t] = run;
+                run += s.cnt[t];
+                s.cnt[t] = 0;
             }
+        P.ci.resize(run);
+        P.cA.resize(run);
+        P.ckpos.resize(run);
+        for (size_t r = 0; r < s.rt.size(); ++r) {
+            const int q = s.pos[s.rt[r]]++;
+            P.ci[q] = s.ri[r];
+            P.cA[q] = s.ra[r];
+            P.ckpos[q] = s.rk[r];
         }
-    }, 1);
-    L.sch_cptr.assign(1, 0);
-    L.sch_tblk.clear();
-    L.sch_tptr.assign(1, 0);
-    L.sch_ci.clear();
-    L.sch_cA.clear();
-    L.sch_ckpos.clear();
-    for (int c = 0; c < L.ncolour; ++c) {
-        const Part& P = parts[c];
-        for (size_t q = 0; q < P.tblk.size(); ++q) {
-            const int t = P.tblk[q];
-            L.sch_tblk.push_back(t);
-            L.sch_tptr.push_back(L.sch_tptr.back() + P.tlen[q]);
-            if (L.bkind[t] == 1 && L.first_touch[t] == INT_MAX) L.first_touch[t] = c;
-        }
-        L.sch_ci.insert(L.sch_ci.end(), P.ci.begin(), P.ci.end());
-        L.sch_cA.insert(L.sch_cA.end(), P.cA.begin(), P.cA.end());
-        L.sch_ckpos.insert(L.sch_ckpos.end(), P.ckpos.begin(), P.ckpos.end());
-        L.sch_cptr.push_back((int)L.sch_tblk.size());
+    });
+    // concatenation in colour order: sizes first, then every colour copied in parallel
+    const int nc = L.ncolour;
+    L.sch_cptr.assign(nc + 1, 0);
+    std::vector<int> coff(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        L.sch_cptr[c + 1] = L.sch_cptr[c] + (int)parts[c].tblk.size();
+        coff[c + 1] = coff[c] + (int)parts[c].ci.size();
     }
+    L.sch_tblk.resize(L.sch_cptr[nc]);
+    L.sch_tptr.resize(L.sch_cptr[nc] + 1);
+    L.sch_tptr[0] = 0;
+    L.sch_ci.resize(coff[nc]);
+    L.sch_cA.resize(coff[nc]);
+    L.sch_ckpos.resize(coff[nc]);
+    parallel_items<int>(nc, [&](int64_t c, int&) {
+        const Part& P = parts[c];
+        const int t0 = L.sch_cptr[c];
+        int run = coff[c];
+        for (size_t q = 0; q < P.tblk.size(); ++q) {
+            L.sch_tblk[t0 + q] = P.tblk[q];
+            run += P.tlen[q];
+            L.sch_tptr[t0 + q + 1] = run;
+        }
+        std::copy(P.ci.begin(), P.ci.end(), L.sch_ci.begin() + coff[c]);
+        std::copy(P.cA.begin(), P.cA.end(), L.sch_cA.begin() + coff[c]);
+        std::copy(P.ckpos.begin(), P.ckpos.end(), L.sch_ckpos.begin() + coff[c]);
+    });
+    // a fill block is first touched by the first (lowest) colour that updates it;
+    // blocks carried from the level below keep -1
+    parallel_items<int>(nc, [&](int64_t c, int&) {
+        for (int t : parts[c].tblk)
+            if (L.bkind[t] == 1) atomic_min(&L.first_touch[t], (int)c);
+    });
 }
 
 // block ids per near-field position and forward-solve target lists
@@ -220,14 +307,13 @@ static void solve_lists(LevelStruct& L) {
                 L.nb_blkT[a] = L.find(L.nb_col[a], i);
             }
     });
-    L.fl_cptr.assign(1, 0);
-    L.fl_tbox.clear();
-    L.fl_tptr.assign(1, 0);
-    L.fl_ci.clear();
-    L.fl_cpos.clear();
+    // per colour: targets j ascending, each with its contributors i ascending
+    struct Part {
+        std::vector<int> tbox, tlen, ci, cpos;
+    };
+    std::vector<Part> parts(L.ncolour);
     struct Rec { int j, i, pos; };
-    std::vector<Rec> recs;
-    for (int c = 0; c < L.ncolour; ++c) {
+    parallel_items<std::vector<Rec>>(L.ncolour, [&](int64_t c, std::vector<Rec>& recs) {
         recs.clear();
         for (int i : L.cboxes[c])
             for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a)
@@ -235,21 +321,70 @@ static void solve_lists(LevelStruct& L) {
         std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) {
             return x.j != y.j ? x.j < y.j : x.i < y.i;
         });
+        Part& P = parts[c];
         for (size_t r = 0; r < recs.size(); ++r) {
             if (r == 0 || recs[r].j != recs[r - 1].j) {
-                if (r) L.fl_tptr.push_back((int)L.fl_ci.size());
-                L.fl_tbox.push_back(recs[r].j);
+                P.tbox.push_back(recs[r].j);
+                P.tlen.push_back(0);
             }
-            L.fl_ci.push_back(recs[r].i);
-            L.fl_cpos.push_back(recs[r].pos);
+            ++P.tlen.back();
+            P.ci.push_back(recs[r].i);
+            P.cpos.push_back(recs[r].pos);
         }
-        if (!recs.empty()) L.fl_tptr.push_back((int)L.fl_ci.size());
+    });
+    L.fl_cptr.assign(1, 0);
+    L.fl_tbox.clear();
+    L.fl_tptr.assign(1, 0);
+    L.fl_ci.clear();
+    L.fl_cpos.clear();
+    for (const Part& P : parts) {
+        for (size_t q = 0; q < P.tbox.size(); ++q) {
+            L.fl_tbox.push_back(P.tbox[q]);
+            L.fl_tptr.push_back(L.fl_tptr.back() + P.tlen[q]);
+        }
+        L.fl_ci.insert(L.fl_ci.end(), P.ci.begin(), P.ci.end());
+        L.fl_cpos.insert(L.fl_cpos.end(), P.cpos.begin(), P.cpos.end());
         L.fl_cptr.push_back((int)L.fl_tbox.size());
     }
 }
 
-// structure-only work lists of every colour (first_touch is final after schur_lists)
+// structure-only work lists of every colour (first_touch is final after schur_lists);
+// built per colour in parallel, then concatenated in colour order
 static void work_lists(LevelStruct& L) {
+    struct Part {
+        std::vector<int> seg_blk, seg_j, seg_slot, seg_end;      // seg_end: local end per box
+        std::vector<int> pj_box, pj_blk, pj_blkT;
+        std::vector<int> zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col;
+    };
+    std::vector<Part> parts(L.ncolour);
+    parallel_items<int>(L.ncolour, [&](int64_t c64, int&) {
+        const int c = (int)c64;
+        Part& P = parts[c];
+        int slot = 0;
+        for (int i : L.cboxes[c]) {
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
+                if (L.bkind[b] != 1 || L.first_touch[b] >= c) continue;
+                P.seg_blk.push_back(b);
+                P.seg_j.push_back(L.bcol[b]);
+                P.seg_slot.push_back(slot);
+            }
+            P.seg_end.push_back((int)P.seg_blk.size());
+            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
+                const bool live = L.bkind[b] == 0 || L.first_touch[b] < c;
+                if (!live) continue;
+                const int bt = L.btr[b];
+                P.pj_box.push_back(i);
+                P.pj_blk.push_back(b);
+                P.pj_blkT.push_back(bt);
+                auto& zb = L.bkind[b] == 1 ? P.zf_box : P.zn_box;
+                auto& zk = L.bkind[b] == 1 ? P.zf_blk : P.zn_blk;
+                auto& zc = L.bkind[b] == 1 ? P.zf_col : P.zn_col;
+                zb.push_back(i); zk.push_back(b); zc.push_back(0);
+                zb.push_back(i); zk.push_back(bt); zc.push_back(1);
+            }
+            ++slot;
+        }
+    });
     L.seg_blk.clear(); L.seg_j.clear(); L.seg_slot.clear();
     L.seg_ptr.assign(1, 0);
     L.seg_cptr.assign(1, 0);
@@ -259,31 +394,14 @@ static void work_lists(LevelStruct& L) {
     L.zn_box.clear(); L.zn_blk.clear(); L.zn_col.clear();
     L.zf_cptr.assign(1, 0);
     L.zn_cptr.assign(1, 0);
-    for (int c = 0; c < L.ncolour; ++c) {
-        int slot = 0;
-        for (int i : L.cboxes[c]) {
-            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
-                if (L.bkind[b] != 1 || L.first_touch[b] >= c) continue;
-                L.seg_blk.push_back(b);
-                L.seg_j.push_back(L.bcol[b]);
-                L.seg_slot.push_back(slot);
-            }
-            L.seg_ptr.push_back((int)L.seg_blk.size());
-            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
-                const bool live = L.bkind[b] == 0 || L.first_touch[b] < c;
-                if (!live) continue;
-                const int bt = L.btr[b];
-                L.pj_box.push_back(i);
-                L.pj_blk.push_back(b);
-                L.pj_blkT.push_back(bt);
-                auto& zb = L.bkind[b] == 1 ? L.zf_box : L.zn_box;
-                auto& zk = L.bkind[b] == 1 ? L.zf_blk : L.zn_blk;
-                auto& zc = L.bkind[b] == 1 ? L.zf_col : L.zn_col;
-                zb.push_back(i); zk.push_back(b); zc.push_back(0);
-                zb.push_back(i); zk.push_back(bt); zc.push_back(1);
-            }
-            ++slot;
-        }
+    auto append = [](std::vector<int>& dst, const std::vector<int>& src) { dst.insert(dst.end(), src.begin(), src.end()); };
+    for (const Part& P : parts) {
+        const int base = (int)L.seg_blk.size();
+        for (int e : P.seg_end) L.seg_ptr.push_back(base + e);
+        append(L.seg_blk, P.seg_blk); append(L.seg_j, P.seg_j); append(L.seg_slot, P.seg_slot);
+        append(L.pj_box, P.pj_box); append(L.pj_blk, P.pj_blk); append(L.pj_blkT, P.pj_blkT);
+        append(L.zf_box, P.zf_box); append(L.zf_blk, P.zf_blk); append(L.zf_col, P.zf_col);
+        append(L.zn_box, P.zn_box); append(L.zn_blk, P.zn_blk); append(L.zn_col, P.zn_col);
         L.seg_cptr.push_back((int)L.seg_blk.size());
         L.pj_cptr.push_back((int)L.pj_box.size());
         L.zf_cptr.push_back((int)L.zf_box.size());
@@ -291,22 +409,23 @@ static void work_lists(LevelStruct& L) {
     }
 }
 
-static int64_t adm_entry(const HostStructure& H, int64_t gs, int64_t gt) {
-    auto b = H.adm_col.begin() + H.adm_ptr[gs];
-    auto e = H.adm_col.begin() + H.adm_ptr[gs + 1];
-    for (auto it = b; it != e; ++it)
-        if (*it == gt) return (int64_t)(it - H.adm_col.begin());
-    return -1;
-}
-
-// sources of each parent block from the four child pairs (level close)
+// sources of each parent block from the four child pairs (level close).  A child
+// pair (c, e) that is admissible takes its coupling from A's admissible CSR: the first
+// entry of row c with column e (each child row's entries are sorted by column once)
 static void close_lists(const HostStructure& H, LevelStruct& C, const LevelStruct& P) {
     int nb = P.nblocks();
     C.cl_dblk.assign(4 * (size_t)nb, -1);
     C.cl_fblk.assign(4 * (size_t)nb, -1);
     C.cl_adm.assign(4 * (size_t)nb, -1);
     parallel_for(P.cnt, [&](int64_t lo, int64_t hi) {
-        for (int p = (int)lo; p < (int)hi; ++p)
+        std::vector<std::pair<int64_t, int64_t>> row[2];      // (column, entry) of rows 2p, 2p+1
+        for (int p = (int)lo; p < (int)hi; ++p) {
+            for (int a = 0; a < 2; ++a) {
+                const int64_t g = C.first + 2 * p + a;
+                row[a].clear();
+                for (int64_t e = H.adm_ptr[g]; e < H.adm_ptr[g + 1]; ++e) row[a].push_back({H.adm_col[e], e});
+                std::sort(row[a].begin(), row[a].end());
+            }
             for (int b = P.bptr[p]; b < P.bptr[p + 1]; ++b) {
                 int q = P.bcol[b];
                 for (int a = 0; a < 2; ++a)
@@ -318,23 +437,48 @@ static void close_lists(const HostStructure& H, LevelStruct& C, const LevelStruc
                             if (C.bkind[blk] == 0) C.cl_dblk[slot] = blk;
                             else C.cl_fblk[slot] = blk;
                         }
-                        C.cl_adm[slot] = adm_entry(H, C.first + c, C.first + e);
+                        const int64_t ge = C.first + e;
+                        auto it = std::lower_bound(row[a].begin(), row[a].end(), std::make_pair(ge, (int64_t)INT64_MIN));
+                        if (it != row[a].end() && it->first == ge) C.cl_adm[slot] = it->second;
                     }
             }
+        }
     });
 }
 
 // leaf near blocks come from A's inadmissible leaf entries
 static void leaf_entries(const HostStructure& H, LevelStruct& L) {
     L.near_entry.assign(L.nblocks(), -1);
-    for (int i = 0; i < L.cnt; ++i) {
-        if (L.state[i] == 0) continue;
-        int64_t g = L.first + i;
-        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
-            int j = (int)(H.inad_col[e] - L.first);
-            L.near_entry[L.find(i, j)] = e - H.inad_ptr[L.first];
+    parallel_for(L.cnt, [&](int64_t lo, int64_t hi) {
+        for (int i = (int)lo; i < (int)hi; ++i) {
+            if (L.state[i] == 0) continue;
+            int64_t g = L.first + i;
+            for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
+                int j = (int)(H.inad_col[e] - L.first);
+                L.near_entry[L.find(i, j)] = e - H.inad_ptr[L.first];
+            }
         }
-    }
+    });
+}
+
+// fill carried to the parent level: the parent pairs (i/2, j/2) of the fill blocks,
+// sorted and distinct (gathered per parent row: its two child rows)
+static void carried_pairs(const LevelStruct& L, std::vector<std::pair<int, int>>& out) {
+    const int np = (L.cnt + 1) / 2;
+    std::vector<std::vector<int>> rows(np);
+    parallel_for(np, [&](int64_t lo, int64_t hi) {
+        for (int p = (int)lo; p < (int)hi; ++p) {
+            auto& r = rows[p];
+            for (int i = 2 * p; i < std::min(2 * p + 2, L.cnt); ++i)
+                for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b)
+                    if (L.bkind[b] == 1) r.push_back(L.bcol[b] / 2);
+            std::sort(r.begin(), r.end());
+            r.erase(std::unique(r.begin(), r.end()), r.end());
+        }
+    });
+    out.clear();
+    for (int p = 0; p < np; ++p)
+        for (int q : rows[p]) out.push_back({p, q});
 }
 
 void build_plan(const HostStructure& H, Plan& P) {
@@ -378,13 +522,7 @@ void build_plan(const HostStructure& H, Plan& P) {
         work_lists(L);
         if (l == H.d) leaf_entries(H, L);
         else L.near_entry.assign(L.nblocks(), -1);
-        // fill carried to the parent level: parents of fill pairs
-        carried.clear();
-        for (int i = 0; i < L.cnt; ++i)
-            for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b)
-                if (L.bkind[b] == 1) carried.push_back({i / 2, L.bcol[b] / 2});
-        std::sort(carried.begin(), carried.end());
-        carried.erase(std::unique(carried.begin(), carried.end()), carried.end());
+        carried_pairs(L, carried);
         P.levels.push_back(std::move(L));
     }
     // the last level: dense top matrices only (t-1, or the leaves when no level is

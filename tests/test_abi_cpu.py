@@ -82,6 +82,17 @@ def test_descriptor_validation_errors():
     rc = binding.lib().h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None)
     assert rc == -1 and b"partition" in binding.lib().h2_last_error()
     d.node_size = keep["node_size"].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    # an inadmissible pattern that is not symmetric: one leaf entry (g, t) moved to
+    # (g, t+1), keeping the row sorted and every block size (all leaves hold 32 points)
+    ptr, col = keep["inad_ptr"], keep["inad_col"].copy()
+    first_leaf = (1 << A.depth) - 1
+    e = next(e for g in range(first_leaf, len(ptr) - 1) for e in range(ptr[g], ptr[g + 1] - 1)
+             if col[e] != g and col[e] + 1 < col[e + 1] and col[e] + 1 != g)
+    col[e] += 1
+    d.inad_col = col.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    rc = binding.lib().h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None)
+    assert rc == -1 and b"not symmetric" in binding.lib().h2_last_error()
+    d.inad_col = keep["inad_col"].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     # a level out of range
     rc = binding.lib().h2_plan_query(ctypes.byref(d), 99, None, None, None, None, None, None)
     assert rc == -1
