@@ -358,3 +358,29 @@ def test_batch_plan_on_random_forests():
                         assert np.array_equal(r, s1["col"][s1["row_ptr"][i]:s1["row_ptr"][i + 1]])
                 else:
                     assert (q["state"][boxes] == (2 if a == nlev[z] else 0)).all()
+
+
+def test_missing_library_fails_loudly():
+    """No fallback: without the built library every entry point raises."""
+    import subprocess
+    import sys
+    code = ("from paper_2509_11152_b300 import binding\n"
+            "binding.LIB_PATH = '/nonexistent/libh2rs.so'\n"
+            "binding._lib = None\n"
+            "try:\n"
+            "    binding.lib()\n"
+            "except RuntimeError as e:\n"
+            "    print('RAISED', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "RAISED" in r.stdout and "missing" in r.stdout, r.stdout + r.stderr
+
+
+def test_product_code_never_touches_the_oracle():
+    """The library package and the input generators import nothing from oracle/."""
+    import re
+    for pkg in ("paper_2509_11152_b300", "h2gen"):
+        for dirpath, _, files in os.walk(os.path.join(ROOT, pkg)):
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h", ".c")):
+                    src = open(os.path.join(dirpath, f)).read()
+                    assert not re.search(r"^\s*(from|import)\s+oracle\b|#include\s+\S*oracle", src, re.M), f
