@@ -19,6 +19,7 @@ Several GPUs run independent replicas (a single system does not shard).
 from __future__ import annotations
 
 import argparse
+import functools
 import json
 import math
 import os
@@ -225,12 +226,19 @@ def _lattice_size(workload: str, n: int) -> int:
     return side ** dim
 
 
+@functools.lru_cache(maxsize=4)
+def _sample_problem(workload: str, n: int):
+    """The input of an oracle sample, built once per size (construction is not timed)."""
+    from h2gen import make_problem
+    return make_problem(workload, n=n)
+
+
 def _oracle_sample(workload: str, n_sample: int):
     """Oracle factor + float64 refined solve on a smaller member of the workload's
     family; returns (seconds, n_sample, iterations, berr)."""
-    from h2gen import make_problem, rhs
+    from h2gen import rhs
     from oracle import dense, rs
-    pb = make_problem(workload, n=_lattice_size(workload, n_sample))
+    pb = _sample_problem(workload, _lattice_size(workload, n_sample))
     A = pb.A.numpy()
     b = rhs(A.n, pb.workload.nrhs, seed=0)
     t0 = time.perf_counter()
