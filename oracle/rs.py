@@ -115,6 +115,16 @@ def _transfer(A, g):
 
 
 # ------------------------------------------------------------------ one box
+def _svd(R):
+    """Thin SVD of R by LAPACK's divide-and-conquer driver; on the rare strongly graded
+    R where that driver does not converge, by its QR-iteration driver (the same
+    decomposition, computed another way)."""
+    try:
+        return np.linalg.svd(R, full_matrices=False)
+    except np.linalg.LinAlgError:
+        return sla.svd(R, full_matrices=False, lapack_driver="gesvd")
+
+
 def _augment(V, Frow, eps_fill, method="qr"):
     """Alg. 2 truncSVD + augment: returns V~ = [V, Vbar].
 
@@ -135,7 +145,7 @@ def _augment(V, Frow, eps_fill, method="qr"):
         Vbar = W[:, :keep]
     else:
         R = np.linalg.qr(Y.T, mode="r")                  # QR of Y^T
-        _, s, Wt = np.linalg.svd(R, full_matrices=False) # R = U_R diag(s) W_R^T
+        _, s, Wt = _svd(R)                               # R = U_R diag(s) W_R^T
         keep = int(np.count_nonzero(s > eps_fill))
         keep = min(keep, n - k)
         Vbar = Wt[:keep].T                               # right sing. vectors of R

@@ -318,3 +318,25 @@ def test_cholesky_variant_equals_lu_on_spd_problems(name, over):
     bx = next(b_ for lv in Zl.levels for b_ in lv.boxes if b_.r > 0 and len(b_.nb) > 1)
     for j in bx.nb:
         assert np.allclose(bx.WL[j], bx.WU[j].T, rtol=1e-8, atol=1e-12)
+
+
+def test_svd_fallback_is_the_same_decomposition(monkeypatch):
+    """The augmentation's SVD of R (Sec. 2.1, second approach) falls back to LAPACK's
+    QR-iteration driver where the divide-and-conquer driver does not converge (seen on
+    a strongly graded 128 x 128 R of the 32,768-point low-rank-updated covariance).
+    Forced onto the fallback, a graded matrix still gets a valid thin SVD with the
+    singular values of the default driver."""
+    rng = np.random.default_rng(5)
+    Q1 = np.linalg.qr(rng.standard_normal((60, 60)))[0]
+    Q2 = np.linalg.qr(rng.standard_normal((60, 60)))[0]
+    R = (Q1 * np.logspace(-3, -19, 60)) @ Q2.T
+    ref = np.linalg.svd(R, compute_uv=False)
+
+    def fail(*a, **k):
+        raise np.linalg.LinAlgError("SVD did not converge")
+    monkeypatch.setattr(rs.np.linalg, "svd", fail)
+    u, s, vt = rs._svd(R)
+    assert np.all(np.diff(s) <= 0)
+    assert np.allclose(s[:20], ref[:20], rtol=1e-10)
+    assert np.linalg.norm((u * s) @ vt - R) <= 1e-14 * np.linalg.norm(R)
+    assert np.allclose(vt @ vt.T, np.eye(60), atol=1e-13)
