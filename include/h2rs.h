@@ -85,7 +85,8 @@ enum {
  *   adm_col[e]      same level (nnodes + 1 / nadm entries), symmetric pattern
  *   S_off[e]        coupling S_st (rank_s x rank_t) of entry e (nadm + 1 entries)
  *   inad_ptr[g]     CSR over all nodes of the inadmissible pairs of the same
- *   inad_col[e]     level, including (g, g), symmetric pattern, columns sorted
+ *   inad_col[e]     level, including (g, g), symmetric pattern (checked),
+ *                   columns sorted (checked)
  *   D_off[j]        dense block (size_s x size_t) of the j-th inadmissible entry of
  *                   a LEAF row, in CSR order (nnear + 1 entries)
  * The library copies everything it needs; the caller keeps ownership of its
