@@ -53,6 +53,8 @@ template <class T> __device__ inline T t_abs(T x) { return x < T(0) ? -x : x; }
 template <class T> __device__ inline bool t_finite(T x) { return isfinite((double)x); }
 
 // ================================================================== leaf load
+// The dense part D of A = H + D on the leaf level (Sec. 2.1), float64 -> working
+// precision, into the level's block buffer.
 template <class T>
 __global__ void k_leaf_load(LevelArgs<T> a, const double* __restrict__ D,
                             const int64_t* __restrict__ D_off,
@@ -70,6 +72,7 @@ __global__ void k_leaf_load(LevelArgs<T> a, const double* __restrict__ D,
     for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) dst[x] = (T)src[x];
 }
 
+// Leaf bases V_i = U_i of the given H^2 matrix (Sec. 1.1) in the working precision.
 template <class T>
 __global__ void k_leaf_basis(LevelArgs<T> a, T* V, const double* __restrict__ U,
                              const int64_t* __restrict__ U_off) {
@@ -219,6 +222,9 @@ __device__ void rfactor_stream(int n, int64_t live, const T* __restrict__ Yt, in
     }
 }
 
+// Alg. 2, first loop, per box: R-factor of Y^T (Householder, streamed), SVD of R by
+// one-sided Jacobi and truncation at eps_fill (Sec. 2.1, the second of its three ways),
+// V~ = [V, Vbar] and its completion Q~ = [V~perp, V~].
 // BIG: boxes up to 256 (one CTA per SM: 64 rows per thread in the R-factor); otherwise
 // boxes up to 128, register-capped so that two boxes share an SM.
 template <class T, bool BIG>
@@ -469,6 +475,7 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
 // ================================================================== projection
 // In-place projection of one 32-wide panel of a block with the box's Q~ (Alg. 2:
 // D <- Q~^T D Q~, F <- Q~^T F Q~), as a register-tiled GEMM:
+// Alg. 2 projection of box i's block row and column by its completed basis (Sec. 2.1):
 //   left  (block in row i):    B[:, c0:c0+32]  <- Q~^T B[:, c0:c0+32]
 //   right (block in column i): B[r0:r0+32, :]  <- B[r0:r0+32, :] Q~
 // Each thread owns RPT coordinates of the box (a = ty + 32u) times 4 panel lines
@@ -548,9 +555,10 @@ k_proj(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_
     }
 }
 
-// F truncation after projection: redundant rows (is_col = 0) or columns (1) of a
-// fill block of box i are dropped (set to zero).  Same kernel zeroes the eliminated
-// rows / columns of near-field blocks after the Schur update.
+// F truncation after projection (Sec. 2.1: fill is kept in the skeleton coordinates
+// only): redundant rows (is_col = 0) or columns (1) of a fill block of box i are
+// dropped (set to zero).  Same kernel zeroes the eliminated rows / columns of
+// near-field blocks after the Schur update.
 template <class T>
 __global__ void k_zero_redundant(LevelArgs<T> a, const int* __restrict__ z_box,
                                  const int* __restrict__ z_blk, const int* __restrict__ z_col) {
@@ -571,7 +579,8 @@ __global__ void k_zero_redundant(LevelArgs<T> a, const int* __restrict__ z_box,
 }
 
 // ================================================================== partial LU
-// LU with partial pivoting of D_RR = D_ii[0:r, 0:r] (first maximal |value| wins).
+// Alg. 2 partial factorisation (Sec. 2.1, Eq. 2.1): LU with partial pivoting of
+// D_RR = D_ii[0:r, 0:r] (first maximal |value| wins) and its explicit inverse.
 template <class T>
 __global__ void __launch_bounds__(256)
 k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
@@ -686,6 +695,7 @@ k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
     }
 }
 
+// The off-diagonal factors of Eq. 2.1 (Sec. 2.1):
 // W_U^i = D_RR^-1 [D_{i_R, j} ..., D_{i_R, i_S}]   (LEFT)  and
 // W_L^i = [D_{j, i_R}; ...; D_{i_S, i_R}] D_RR^-1  (!LEFT), as 64x64-tiled GEMMs with
 // K = r_i; the gathered operand's columns (rows) are located per tile from N(i).
@@ -784,7 +794,8 @@ k_wgemm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w
 }
 
 // ================================================================== Schur update
-// Target-owned accumulation: X_jk -= sum_{i in colour, j,k in N(i)} D_{j,i_R} W_U^i[k]
+// Schur complement of Alg. 2 (Sec. 2.1; fill outside the near field goes to F), with
+// target-owned accumulation: X_jk -= sum_{i in colour, j,k in N(i)} D_{j,i_R} W_U^i[k]
 // as one GEMM per target whose K dimension runs over the contributors.  64x64 tiles,
 // 256 threads, 4x4 outputs per thread.
 template <class T>
@@ -1029,7 +1040,8 @@ __global__ void k_close_blocks(LevelArgs<T> a, T* __restrict__ pblk, const int64
     }
 }
 
-// Parent basis V_p = [T~_c1; T~_c2], T~_c = [E_c; 0] (nested basis after projection).
+// Parent basis V_p = [T~_c1; T~_c2], T~_c = [E_c; 0] (nested basis after projection,
+// Sec. 2.1, level close).
 template <class T>
 __global__ void k_close_basis(LevelArgs<T> a, T* __restrict__ pV, const int64_t* __restrict__ pV_off,
                               const int* __restrict__ pk, const double* __restrict__ E,
@@ -1077,6 +1089,8 @@ __global__ void k_top_assemble(const int* __restrict__ blist, const T* __restric
     }
 }
 
+// Alg. 1, last step: dense LU D_t = L_t U_t of the top level (float64, partial
+// pivoting, blocked).
 // The top LU runs over all systems at once: panel j0 of every top matrix whose order
 // exceeds j0 (blockIdx.x / y / z selects the system, see each kernel).
 

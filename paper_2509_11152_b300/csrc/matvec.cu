@@ -1,5 +1,7 @@
-// Float64 H^2 matrix-vector product y = A x (upsweep, couplings, downsweep, near
-// field) and the vector kernels of iterative refinement.  Coefficient vectors of
+// Float64 H^2 matrix-vector product y = A x in the format of Sec. 1.1 (upsweep through
+// the nested bases, couplings S_st, downsweep, dense near field) and the vector kernels
+// of iterative refinement (not in the paper: it recovers float64 accuracy from a
+// float32 factor).  Coefficient vectors of
 // node g live at coef_off[g]*nrhs, rank_g x nrhs column-major.
 #include "h2rs_internal.h"
 #include "matvec.cuh"
