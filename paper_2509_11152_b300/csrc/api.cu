@@ -137,6 +137,10 @@ int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_matrix*
         place(M.E, H.E_off[nn], fv.E, &h2_matrix_desc::E);
         place(M.S, H.S_off.back(), fv.S, &h2_matrix_desc::S);
         place(M.D, H.D_off.back(), fv.D, &h2_matrix_desc::D);
+        // the level plan is host work: build it while the value copies above are in
+        // flight (from pinned host memory they run asynchronously), before the small
+        // uploads below, whose pageable sources may make them wait for those copies
+        build_plan(H, M.plan);
         upload(M.d_node_start, H.node_start, s);
         upload(M.d_node_size, H.node_size, s);
         upload(M.d_rank, H.rank, s);
@@ -157,11 +161,15 @@ int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_matrix*
         M.coef_off.assign(nn + 1, 0);
         for (int64_t g = 0; g < nn; ++g) M.coef_off[g + 1] = M.coef_off[g] + H.rank[g];
         upload(M.d_coef_off, M.coef_off, s);
-        build_plan(H, M.plan);
         upload_plan(M.plan, s);
         H2_CUDA_CHECK(cudaStreamSynchronize(s));
     });
-    if (rc != H2_OK) { delete A; return rc; }
+    if (rc != H2_OK) {
+        // no copy may still read the caller's arrays once this returns
+        if (nsys >= 1 && descs) cudaStreamSynchronize(static_cast<cudaStream_t>(descs[0].stream));
+        delete A;
+        return rc;
+    }
     *out = A;
     return H2_OK;
 }
