@@ -82,7 +82,8 @@ enum {
  *   E_off[g]        transfer E_g (rank_g x rank_parent), g >= 1; E_off[0] = 0
  *                   (nnodes + 1 entries)
  *   adm_ptr[g]      CSR over all nodes of the admissible pairs (s = g, t) of the
- *   adm_col[e]      same level (nnodes + 1 / nadm entries), symmetric pattern
+ *   adm_col[e]      same level (nnodes + 1 / nadm entries), symmetric pattern,
+ *                   columns sorted, no pair also inadmissible (all checked)
  *   S_off[e]        coupling S_st (rank_s x rank_t) of entry e (nadm + 1 entries)
  *   inad_ptr[g]     CSR over all nodes of the inadmissible pairs of the same
  *   inad_col[e]     level, including (g, g), symmetric pattern (checked),

@@ -72,6 +72,7 @@ void read_structure(const h2_matrix_desc* d, HostStructure& H) {
         for (int64_t e = H.adm_ptr[g]; e < H.adm_ptr[g + 1]; ++e) {
             const int64_t t = H.adm_col[e];
             H2_REQUIRE(t >= lf && t < ll, H2_ERR_ARG, "admissible pair across levels");
+            if (e > H.adm_ptr[g]) H2_REQUIRE(t > H.adm_col[e - 1], H2_ERR_ARG, "adm_col not sorted");
             H2_REQUIRE(H.S_off[e + 1] - H.S_off[e] == H.rank[g] * H.rank[t], H2_ERR_ARG, "S_off size");
         }
         bool self = false;
@@ -88,13 +89,22 @@ void read_structure(const h2_matrix_desc* d, HostStructure& H) {
         }
         H2_REQUIRE(self, H2_ERR_ARG, "every node must be in its own near field");
     }
-    // the matrix is symmetric, so is its near field: (g, t) inadmissible => (t, g)
-    for (int64_t g = 0; g < nn; ++g)
-        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e) {
-            const int64_t t = H.inad_col[e];
-            H2_REQUIRE(std::binary_search(H.inad_col.begin() + H.inad_ptr[t], H.inad_col.begin() + H.inad_ptr[t + 1], g),
-                       H2_ERR_ARG, "the inadmissible pattern is not symmetric");
+    // the matrix is symmetric, so are both patterns: (g, t) in one => (t, g) in the
+    // same one; and no pair is both admissible and inadmissible
+    auto has = [](const std::vector<int64_t>& ptr, const std::vector<int64_t>& col, int64_t g, int64_t t) {
+        return std::binary_search(col.begin() + ptr[g], col.begin() + ptr[g + 1], t);
+    };
+    for (int64_t g = 0; g < nn; ++g) {
+        for (int64_t e = H.inad_ptr[g]; e < H.inad_ptr[g + 1]; ++e)
+            H2_REQUIRE(has(H.inad_ptr, H.inad_col, H.inad_col[e], g), H2_ERR_ARG,
+                       "the inadmissible pattern is not symmetric");
+        for (int64_t e = H.adm_ptr[g]; e < H.adm_ptr[g + 1]; ++e) {
+            H2_REQUIRE(has(H.adm_ptr, H.adm_col, H.adm_col[e], g), H2_ERR_ARG,
+                       "the admissible pattern is not symmetric");
+            H2_REQUIRE(!has(H.inad_ptr, H.inad_col, g, H.adm_col[e]), H2_ERR_ARG,
+                       "a pair is both admissible and inadmissible");
         }
+    }
 }
 
 // append a chunk, merging it with the previous one when both ranges continue it

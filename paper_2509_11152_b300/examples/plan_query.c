@@ -20,7 +20,7 @@ int main(void) {
     int64_t U_off[NLEAF + 1] = {0, 2, 4, 6, 8};             /* 2 x 1 per leaf */
     int64_t E_off[NN + 1] = {0, 0, 1, 2, 3, 4, 5, 6};        /* 1 x 1 per non-root */
     /* admissible pairs: level 2 only, leaves 3..6: (3,5) (3,6) (4,6) + transposes */
-    int64_t adm_ptr[NN + 1] = {0, 0, 0, 0, 2, 3, 5, 6};
+    int64_t adm_ptr[NN + 1] = {0, 0, 0, 0, 2, 3, 4, 6};
     int64_t adm_col[6] = {5, 6, 6, 3, 3, 4};
     int64_t S_off[7] = {0, 1, 2, 3, 4, 5, 6};
     /* inadmissible: root (0,0); level 1 all pairs; leaves: self + (3,4) (4,5) (5,6) */

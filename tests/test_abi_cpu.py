@@ -93,6 +93,27 @@ def test_descriptor_validation_errors():
     rc = binding.lib().h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None)
     assert rc == -1 and b"not symmetric" in binding.lib().h2_last_error()
     d.inad_col = keep["inad_col"].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    # an admissible pattern that is not symmetric: the entry (t, g) of one admissible
+    # pair removed (with its coupling's slot), (g, t) kept
+    aptr, acol, soff = keep["adm_ptr"], keep["adm_col"], keep["S_off"]
+    g = next(g for g in range(len(aptr) - 1) if aptr[g + 1] > aptr[g])
+    t = acol[aptr[g]]
+    e2 = aptr[t] + int(np.searchsorted(acol[aptr[t]:aptr[t + 1]], g))
+    assert acol[e2] == g
+    aptr2 = aptr.copy()
+    aptr2[t + 1:] -= 1
+    acol2 = np.delete(acol, e2)
+    soff2 = np.concatenate([soff[:e2 + 1], soff[e2 + 2:] - (soff[e2 + 1] - soff[e2])])
+    d.adm_ptr = aptr2.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.adm_col = acol2.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.S_off = soff2.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    rc = binding.lib().h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None)
+    assert rc == -1 and b"admissible pattern is not symmetric" in binding.lib().h2_last_error()
+    d.adm_ptr = aptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.adm_col = acol.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.S_off = soff.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    rc = binding.lib().h2_plan_query(ctypes.byref(d), 0, None, None, None, None, None, None)
+    assert rc == 0
     # a level out of range
     rc = binding.lib().h2_plan_query(ctypes.byref(d), 99, None, None, None, None, None, None)
     assert rc == -1
@@ -384,3 +405,67 @@ def test_product_code_never_touches_the_oracle():
                 if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h", ".c")):
                     src = open(os.path.join(dirpath, f)).read()
                     assert not re.search(r"^\s*(from|import)\s+oracle\b|#include\s+\S*oracle", src, re.M), f
+
+
+def _example_matrix():
+    """The H^2 matrix that examples/solve.c builds, mirrored here (same arrays)."""
+    import math
+    import torch
+    from h2gen.h2matrix import H2Matrix
+
+    def kern(i, j):
+        xi, xj = (i + 0.5) / 8, (j + 0.5) / 8
+        return 1.1 if i == j else math.exp(-abs(xi - xj) / 0.5)
+    start = np.array([0, 0, 4, 0, 2, 4, 6])
+    adm_ptr = np.array([0, 0, 0, 0, 2, 3, 4, 6])
+    adm_col = np.array([5, 6, 6, 3, 3, 4])
+    inad_ptr = np.array([0, 1, 3, 5, 7, 10, 13, 15])
+    inad_col = np.array([0, 1, 2, 1, 2, 3, 4, 3, 4, 5, 4, 5, 6, 5, 6])
+    S = [0.5 * sum(kern(start[s] + a, start[t] + b) for a in range(2) for b in range(2))
+         for s in range(3, 7) for t in adm_col[adm_ptr[s]:adm_ptr[s + 1]]]
+    D = [kern(start[s] + r, start[t] + c) for s in range(3, 7) for t in inad_col[inad_ptr[s]:inad_ptr[s + 1]]
+         for c in range(2) for r in range(2)]
+    f = lambda v: torch.tensor(v, dtype=torch.float64)
+    return H2Matrix(n=8, depth=2, node_start=start, node_size=np.array([8, 4, 4, 2, 2, 2, 2]),
+                    rank=np.ones(7, np.int64), U_off=np.array([0, 2, 4, 6, 8]), U=f([2 ** -0.5] * 8),
+                    E_off=np.array([0, 0, 1, 2, 3, 4, 5, 6]), E=f([2 ** -0.5] * 6), adm_ptr=adm_ptr,
+                    adm_col=adm_col, S_off=np.arange(7), S=f(S), inad_ptr=inad_ptr, inad_col=inad_col,
+                    D_off=np.arange(0, 44, 4), D=f(D))
+
+
+def test_c_solve_example_matrix_and_build():
+    """examples/solve.c: its matrix is a valid symmetric positive definite H^2 matrix
+    that the oracle factorises to the dense solution; the program builds with gcc
+    (-Wall -Werror) and, run without a GPU, ends with a status code, not a crash (on
+    a GPU it prints two backward errors and exits 0)."""
+    import shutil
+    import subprocess
+    import tempfile
+    import torch
+    from oracle import dense, rs
+    from paper_2509_11152_b300 import binding
+    A = _example_matrix().numpy()
+    M = dense.expand(A)
+    assert np.allclose(M, M.T) and np.linalg.eigvalsh(M).min() > 0.05
+    b = np.ones((8, 1))
+    norm_a = np.linalg.norm(M, 2)
+    Z = rs.factorize(A, 1e-12, norm_a)
+    assert np.allclose(rs.solve(Z, b), np.linalg.solve(M, b), rtol=1e-12)
+    binding.lib()
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = os.path.join(ROOT, "paper_2509_11152_b300", "examples", "solve.c")
+    libdir = os.path.dirname(binding.LIB_PATH)
+    with tempfile.TemporaryDirectory() as td:
+        exe = os.path.join(td, "solve")
+        r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", src, "-I", os.path.join(ROOT, "include"),
+                            "-L", libdir, "-lh2rs", "-lm", f"-Wl,-rpath,{libdir}", "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    if torch.cuda.is_available():
+        assert r.returncode == 0, r.stdout + r.stderr
+        assert "float64 factor + solve" in r.stdout and "float32 factor" in r.stdout
+    else:
+        assert r.returncode == 2 and "h2_matrix_create failed" in r.stderr, r.stdout + r.stderr
