@@ -1,6 +1,7 @@
 """Input generator checks: point sets, kernels, cluster tree, block partition and the
 H^2 construction (checked against dense kernel matrices)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -148,3 +149,26 @@ def test_bases_orthonormal(cov2d_1k):
     for g in range(A.nnodes):
         if A.rank[g]:
             assert np.allclose(U[g].T @ U[g], np.eye(A.rank[g]), atol=1e-12)
+
+
+def _table1():
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_construction.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows[f[0]] = dict(m=int(f[1]), p0=int(f[2]), dim=int(f[3]), eta=float(f[4]), eps_lu=float(f[7]),
+                              kmax=int(f[8]), csp=int(f[9]))
+    return rows
+
+
+def test_2d_covariance_structure_against_table1():
+    """Table 1 (Sec. 3) as a sanity range: the 2D exponential covariance built with the
+    paper's parameters (m 64, p0 8, eta 0.9, eps 1e-7) at N = 2^14.  Our reading of
+    Eq. 1.1 (box diagonals, box-to-box distance) gives denser near fields than the
+    paper's and, with them, smaller ranks: C_sp between 1x and 4x, k_max between 0.5x
+    and 1.5x the printed values."""
+    t = _table1()["cov2d"]
+    pb = make_problem("cov2d", n=1 << 14, leaf=t["m"], eta=t["eta"], tol=t["eps_lu"], p0=t["p0"])
+    assert t["csp"] <= pb.stats["csp"] <= 4 * t["csp"], pb.stats
+    assert 0.5 * t["kmax"] <= pb.stats["kmax"] <= 1.5 * t["kmax"], pb.stats
