@@ -16,9 +16,9 @@ member of the uneven Gaussian batch (N = 8192, leaf 64, eps_lu 1e-6):
 
 Result (recorded with this script): inv32 stalls at a backward error of 1.7e-6 (no
 convergence in 40 corrections), inv64 and inv32ns need 18 corrections, lu32 needs 9
-(as many as float32 storage with float64 arithmetic).  Multiplying by a rounded inverse costs about
-cond(D_RR) * u, triangular solves do not; this is the float32 path's weak step on
-ill-conditioned problems.
+(as many as float32 storage with float64 arithmetic).  Multiplying by a rounded
+inverse costs about cond(D_RR) * u, triangular solves do not; this is the float32
+path's weak step on ill-conditioned problems.
 """
 import os
 import sys
