@@ -8,7 +8,9 @@ float64 iterative refinement until the normwise backward error
 ``--workload uneven`` instead runs the uneven batch: independent Gaussian-kernel
 systems (3D, leaf 64, eta 1, eps_lu 1e-6, 4 right-hand sides each, sizes
 log-uniform in [--nmin, --nmax]) factorised and refined together as one forest;
-with several GPUs the systems are split over the ranks (LPT by size).
+with several GPUs the systems are split over the ranks (LPT by size).  Any other
+family of ``h2gen.WORKLOADS`` (e.g. ``helmholtz3d``, ``lru3d``) runs as one system,
+its size set by ``--size`` (rounded down to a full lattice where the family has one).
 
 Prints one JSON line (rank 0).  ``value`` is the device time of a step with the
 matrix and right-hand side resident in HBM; ``e2e`` repeats the step through the
@@ -178,7 +180,7 @@ def _traffic(kernel: str, algorithmic_bytes: float, steps: int):
 def _problem(args, device):
     from h2gen import make_problem
     from h2gen.problems import load_problem, save_problem
-    over = {} if not args.n else {"n": args.n}
+    over = {} if not args.n else {"n": _lattice_size(args.workload, args.n)}
     if args.matrix_cache and os.path.exists(args.matrix_cache):
         return load_problem(args.matrix_cache, device)
     pb = make_problem(args.workload, device=device, **over)
@@ -284,7 +286,7 @@ def run_reference(args, dist, rank, ws):
     else:
         family = args.workload
         w = WORKLOADS[family]
-        n_full = args.n or w.n
+        n_full = _lattice_size(family, args.n or w.n)
         n_sample = min(n_full, 16384)
         wdesc = f"{w.name} N={n_full} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs}"
     for _ in range(args.warmup):

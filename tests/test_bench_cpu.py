@@ -51,3 +51,13 @@ def test_reference_arm_under_two_ranks_prints_once():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1, r.stdout
     assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_reference_arm_on_a_lattice_family_rounds_the_size():
+    """A 3D lattice family with a size that is not a cube: the run uses the largest
+    cube below it (17^3 = 4913) and says so."""
+    args = ["--impl", "reference", "--workload", "helmholtz3d", "--size", "5000", "--steps", "1", "--warmup", "1"]
+    r = subprocess.run([sys.executable, "bench.py", *args], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = _json_lines(r.stdout)[-1]
+    assert "helmholtz3d N=4913" in line["config"]["workload"] and "N=4913" in line["cpu_baseline"]["sample"]
