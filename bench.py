@@ -236,8 +236,9 @@ def _sample_problem(workload: str, n: int):
 
 
 def _oracle_sample(workload: str, n_sample: int):
-    """Oracle factor + float64 refined solve on a smaller member of the workload's
-    family; returns (seconds, n_sample, iterations, berr)."""
+    """Oracle factor + float64 refined solve (plain corrections until the backward
+    error is <= 1e-10) of a smaller member of the workload's family, as it stands.
+    Returns (seconds, N, corrections, berr, x, unrefined x, problem, b)."""
     from h2gen import rhs
     from oracle import dense, rs
     pb = _sample_problem(workload, _lattice_size(workload, n_sample))
@@ -246,6 +247,7 @@ def _oracle_sample(workload: str, n_sample: int):
     t0 = time.perf_counter()
     Z = rs.factorize(A, pb.workload.tol, pb.norm_a)
     x = rs.solve(Z, b)
+    x0 = x.copy()
     it = 0
     while True:
         r = b - dense.matvec(A, x)
@@ -254,23 +256,31 @@ def _oracle_sample(workload: str, n_sample: int):
             break
         x = x + rs.solve(Z, r)
         it += 1
-    return time.perf_counter() - t0, A.n, it, berr
+    return time.perf_counter() - t0, A.n, it, berr, x, x0, pb, b
 
 
-def _blas_threads() -> int:
-    try:
-        from threadpoolctl import threadpool_info
-        info = threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] or [1])
-    except Exception:
-        return 1
+def _timed_oracle(workload: str, n_sample: int, threads: int):
+    """_oracle_sample with the BLAS pools limited to `threads` threads (the oracle's
+    own code is one Python thread; its parallelism is inside BLAS/LAPACK calls)."""
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=threads):
+        return _oracle_sample(workload, n_sample)
 
 
-def _cpu_baseline(workload: str, n_full: int, n_sample: int) -> dict:
-    sec, ns, it, berr = _oracle_sample(workload, n_sample)
-    return {"value": sec * n_full / ns, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
-            "sample": f"oracle (float64 numpy) factor + refined solve of the same family at N={ns} "
-                      f"({sec:.1f} s, {it} corrections, berr {berr:.1e}), scaled linearly to N={n_full}"}
+def _cpu_baseline(workload: str, n_full: int, n_sample: int) -> tuple[dict, tuple]:
+    """The oracle timed (not extrapolated) on a bounded sample of the workload, at one
+    BLAS thread and at every host core; value = the all-core time."""
+    ncpu = os.cpu_count() or 1
+    one = _timed_oracle(workload, n_sample, 1)
+    allc = _timed_oracle(workload, n_sample, ncpu)
+    sec1, ns, it, berr = one[:4]
+    secn = allc[0]
+    base = {"value": secn, "unit": "s", "cores": ncpu, "kind": "oracle", "n": ns,
+            "value_1thread": sec1,
+            "sample": f"oracle (float64 numpy, as it stands) factor + refined solve of the same family at "
+                      f"N={ns} (the bench workload has N={n_full}): {secn:.1f} s with BLAS on {ncpu} threads, "
+                      f"{sec1:.1f} s on 1 thread; {it} corrections, berr {berr:.1e}; measured, not scaled"}
+    return base, allc
 
 
 def run_reference(args, dist, rank, ws):
@@ -281,32 +291,56 @@ def run_reference(args, dist, rank, ws):
         sizes = uneven_sizes(args.nsys, args.nmin, args.nmax)
         family, n_full, n_sample = "gauss3d", sum(sizes), 4096
         w = WORKLOADS[family]
-        wdesc = (f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}] "
-                 f"(total {n_full}), leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs} each")
+        full = (f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in [{args.nmin}, {args.nmax}] "
+                f"(total {n_full})")
     else:
         family = args.workload
         w = WORKLOADS[family]
         n_full = _lattice_size(family, args.n or w.n)
         n_sample = min(n_full, 16384)
-        wdesc = f"{w.name} N={n_full} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs}"
+        full = f"{w.name} N={n_full}"
+    ncpu = os.cpu_count() or 1
     for _ in range(args.warmup):
-        _oracle_sample(family, min(n_sample, 4096))
+        _timed_oracle(family, min(n_sample, 4096), ncpu)
     times = []
     info = None
     for _ in range(args.steps):
-        sec, ns, it, berr = _oracle_sample(family, n_sample)
-        times.append(sec * n_full / ns)
-        info = (sec, ns, it, berr)
+        res = _timed_oracle(family, n_sample, ncpu)
+        times.append(res[0])
+        info = res
     v = statistics.mean(times)
+    ns = info[1]
+    wdesc = (f"{w.name} N={ns} leaf={w.leaf} eta={w.eta} eps_lu={w.tol} nrhs={w.nrhs} "
+             f"(the oracle's bounded sample of the {full} workload, timed at the size it ran)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wdesc, "precision": "float64 oracle"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
-                             "sample": f"each step: oracle factor + refined solve at N={info[1]} "
-                                       f"({info[0]:.1f} s), scaled linearly to N={n_full}"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": ncpu, "kind": "oracle", "n": ns,
+                             "sample": f"each step: oracle (as it stands) factor + refined solve at N={ns} "
+                                       f"({info[2]} corrections, berr {info[3]:.1e}), BLAS on {ncpu} threads; "
+                                       f"measured, not scaled"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _oracle_err(h, sample, prec, tol):
+    """The mixed arm against the float64 oracle on the oracle's sample problem: the
+    refined solutions (both at backward error <= 1e-10) and the unrefined solves (the
+    reduced-precision factor against the oracle's float64 factor)."""
+    import torch
+    _, ns, _, _, x_or, x0_or, pb, b = sample
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, tol, pb.norm_a, prec)
+    bt = h.colmajor(torch.from_numpy(b).cuda())
+    x = h.colmajor(torch.zeros_like(bt))
+    it, berr, ok = h.h2_refine_solve(Z, M, bt, x, BERR_TOL, MAXIT)
+    x0 = h.colmajor(torch.from_numpy(b).cuda())
+    h.h2_solve(Z, x0)
+    rel = float(np.linalg.norm(x.cpu().numpy() - x_or) / np.linalg.norm(x_or))
+    rel0 = float(np.linalg.norm(x0.cpu().numpy() - x0_or) / np.linalg.norm(x0_or))
+    return {"n": ns, "refined_vs_oracle_refined": rel, "solve_vs_oracle_solve": rel0, "iters": it,
+            "berr": berr}
 
 
 # ------------------------------------------------------------------ our arm
@@ -376,7 +410,7 @@ def run_ours(args, dist, rank, ws):
     t_step = e0.elapsed_time(e1) / 1e3 / args.steps
     t_step = _max_over_ranks(dist, t_step)
     uneven = args.workload == "uneven"
-    value = t_step if uneven else t_step / ws        # batch: all ranks share one batch
+    value = t_step        # batch: the ranks share one batch; otherwise N independent replicas
 
     # dominant factorisation kernel and its roofline
     peaks, peak_kind = _peaks()
@@ -466,11 +500,13 @@ def run_ours(args, dist, rank, ws):
                          "inad_ptr", "inad_col", "D_off"))
         h2d = sum(A.nbytes() for A in As) + idx_bytes + bh.numel() * 8
         e2e_v = _max_over_ranks(dist, statistics.mean(e2e))
-        line["e2e"] = {"value": e2e_v if uneven else e2e_v / ws, "unit": "s",
+        line["e2e"] = {"value": e2e_v, "unit": "s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(bh.numel() * 8)}
 
     if args.cpu_baseline and rank == 0 and ws == 1:
-        line["cpu_baseline"] = _cpu_baseline(w.name, n_tot, min(n_tot, 4096 if uneven else 16384))
+        base, sample = _cpu_baseline(w.name, n_tot, min(n_tot, 4096 if uneven else 16384))
+        line["cpu_baseline"] = base
+        line["oracle_err"] = _oracle_err(h, sample, prec_mixed, w.tol)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -138,25 +138,29 @@ H2_API int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_
  * either output may be NULL.  Errors: H2_ERR_ARG. */
 H2_API int h2_matrix_batch_info(const h2_matrix* A, int32_t* nsys, int64_t* sys_offset);
 
-/* y = A x in float64 (the H^2 matrix-vector product: upsweep, couplings, downsweep,
- * near field).  x: n x nrhs (ldx >= n), y: n x nrhs (ldy >= n); both device pointers
+/* y = A x in float64: the H^2 matrix-vector product of the format of Sec. 1.1
+ * (Fig. 1-3): upsweep through the nested bases, couplings S_st, downsweep, dense
+ * near field.  x: n x nrhs (ldx >= n), y: n x nrhs (ldy >= n); both device pointers
  * when on_device != 0, else host pointers (copied in and out).  Errors: H2_ERR_ARG,
  * H2_ERR_CUDA. */
 H2_API int h2_matvec(const h2_matrix* A, int32_t nrhs, const double* x, int64_t ldx,
               double* y, int64_t ldy, int32_t on_device);
 
-/* The same product with no device allocation, for callers that may not allocate
- * device memory while it runs (an application that owns all of the GPU's memory and
- * forbids cudaMalloc/cudaFree, or a tight solver loop that cannot pay for an allocator
- * call or the synchronisation of a free).  No counterpart in the paper.
- * The coefficient vectors live in one static device array of H2_MATVEC_STATIC_WORDS
- * doubles (32 MiB) that every GPU loading the library keeps until the process exits.
- * x and y are device pointers (n x nrhs, ldx/ldy >= n).  Calls needing more than the
+/* The same product with no device allocation.  The paper has no counterpart: it is
+ * for callers that may not allocate device memory while it runs, such as an
+ * application that reserves all of the GPU's memory for itself up front and forbids
+ * any further cudaMalloc/cudaFree (or stream-ordered allocation) by the libraries it
+ * calls.  The coefficient vectors live in one static device array of
+ * H2_MATVEC_STATIC_WORDS doubles (32 MiB) that every GPU loading the library keeps
+ * until the process exits.  x and y (n x nrhs, ldx/ldy >= n) must be device (or
+ * managed) memory of the matrix's device, and that device must be current; host or
+ * other-device pointers are rejected with H2_ERR_ARG.  Calls needing more than the
  * array (2 * sum(rank) * nrhs doubles) return H2_ERR_ARG with a message.  The first
  * call on a device looks up the array's device address, so make that first call
- * before any stream capture.  All calls share the array and it keeps the last call's
- * contents (every value read is written first within a call); calls that overlap on
- * the GPU race, so serialise them.  Errors: H2_ERR_ARG, H2_ERR_CUDA. */
+ * before any stream capture.  The call waits for the matrix's stream to finish
+ * before it returns.  All calls share the array and it keeps the last call's contents
+ * (every value read is written first within a call); calls that overlap on the GPU
+ * race, so serialise them.  Errors: H2_ERR_ARG, H2_ERR_CUDA. */
 #define H2_MATVEC_STATIC_WORDS (1 << 22)
 H2_API int h2_matvec_static(const h2_matrix* A, int32_t nrhs, const double* x, int64_t ldx,
                             double* y, int64_t ldy);
@@ -243,6 +247,10 @@ typedef struct {
     double host_ms[4];          /* host time of the factorisation: per-level work lists,
                                    their uploads, level setup + close bookkeeping, and
                                    waits for the per-level rank read-back            */
+    double schur_reread_bytes;  /* Schur operand bytes counted once per target a
+                                   contributor feeds (the kernel's L2 re-reads); the
+                                   Schur entry of phase_bytes counts every operand once
+                                   per colour and every target once (read + write)    */
 } h2_factor_stats;
 
 H2_API int h2_factor_stats_get(const h2_factor* Z, h2_factor_stats* out);

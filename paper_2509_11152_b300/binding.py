@@ -51,7 +51,7 @@ class h2_factor_stats(ctypes.Structure):
                 ("factor_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
                 ("phase_flops", ctypes.c_double * 8), ("phase_bytes", ctypes.c_double * 8),
                 ("kernel_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_int64 * 16),
-                ("host_ms", ctypes.c_double * 4)]
+                ("host_ms", ctypes.c_double * 4), ("schur_reread_bytes", ctypes.c_double)]
 
 
 PHASES = ["augment", "project", "lu_trsm", "schur", "close", "top", "leaf_load", "other"]
@@ -305,7 +305,8 @@ def h2_factor_stats_get(Z: Factor) -> dict:
                 kernel_ms=dict(zip(KERNELS, list(s.kernel_ms))),
                 kernel_launches=dict(zip(KERNELS, list(s.kernel_launches))),
                 host_ms=dict(zip(["work_lists", "uploads", "level_setup_close", "rank_readback"],
-                                 list(s.host_ms))))
+                                 list(s.host_ms))),
+                schur_reread_bytes=s.schur_reread_bytes)
 
 
 def h2_layout_get(Z: Factor, level: int) -> dict:

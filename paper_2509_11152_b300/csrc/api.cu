@@ -59,25 +59,6 @@ static void keep_pool_memory() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
 }
 
-template <class F>
-static int guard(F&& f) {
-    try {
-        f();
-        return H2_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.code;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return H2_ERR_OOM;
-    } catch (const std::exception& e) {
-        set_error(e.what());
-        return H2_ERR_ARG;
-    } catch (...) {
-        set_error("unknown error");
-        return H2_ERR_ARG;
-    }
-}
 
 template <class T>
 static void upload_values(DevBuf& b, const T* p, int64_t n, bool on_dev, cudaStream_t s) {
@@ -120,6 +101,7 @@ int h2_matrix_create_batch(int32_t nsys, const h2_matrix_desc* descs, h2_matrix*
         merge_forest(parts, M.H, order, fv);
         parts.clear();
         M.stream = static_cast<cudaStream_t>(descs[0].stream);
+        H2_CUDA_CHECK(cudaGetDevice(&M.device));
         cudaStream_t s = M.stream;
         const HostStructure& H = M.H;
         const int64_t nn = H.nnodes, nleaf = H.lev_cnt[H.d];

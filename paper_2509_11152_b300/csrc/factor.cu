@@ -81,13 +81,13 @@ static int raise_smem(K kern) {
 }
 
 template <class T, bool RIGHT>
-static void launch_proj(int rpt, int nwork, int npan, int smem, cudaStream_t s, LevelArgs<T> ar, const int* box,
-                        const int* blk) {
+static void launch_proj(int rpt, int nwork, int npan, int smem, cudaStream_t s, LevelArgs<T> ar, int c,
+                        const int* box, const int* blk) {
     const dim3 g(nwork, npan);                        // y: 32-wide panel of the block
-    if (rpt <= 1) k_proj<T, 1, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
-    else if (rpt <= 2) k_proj<T, 2, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
-    else if (rpt <= 4) k_proj<T, 4, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
-    else if (rpt <= 8) k_proj<T, 8, RIGHT><<<g, 256, smem, s>>>(ar, box, blk);
+    if (rpt <= 1) k_proj<T, 1, RIGHT><<<g, 256, smem, s>>>(ar, c, box, blk);
+    else if (rpt <= 2) k_proj<T, 2, RIGHT><<<g, 256, smem, s>>>(ar, c, box, blk);
+    else if (rpt <= 4) k_proj<T, 4, RIGHT><<<g, 256, smem, s>>>(ar, c, box, blk);
+    else if (rpt <= 8) k_proj<T, 8, RIGHT><<<g, 256, smem, s>>>(ar, c, box, blk);
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
 }
 
@@ -524,14 +524,14 @@ void FactorImpl<T>::run_level(size_t a) {
         const int npan = (nmax_level + PW - 1) / PW;        // panels of the other dimension
         if (npj) {
             kbegin(H2_K_PROJ);
-            launch_proj<T, false>(rpt, npj, npan, smp, s, ar, S.dev.pj_box.as<int>() + pj0,
+            launch_proj<T, false>(rpt, npj, npan, smp, s, ar, c, S.dev.pj_box.as<int>() + pj0,
                                   S.dev.pj_blk.as<int>() + pj0);
             kend();
         }
         H2_LAUNCHED();
         if (npj) {
             kbegin(H2_K_PROJ);
-            launch_proj<T, true>(rpt, npj, npan, smp, s, ar, S.dev.pj_box.as<int>() + pj0,
+            launch_proj<T, true>(rpt, npj, npan, smp, s, ar, c, S.dev.pj_box.as<int>() + pj0,
                                  S.dev.pj_blkT.as<int>() + pj0);
             kend();
         }
@@ -624,7 +624,8 @@ void FactorImpl<T>::run_level(size_t a) {
             for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
                 const bool lv_ = S.bkind[b] == 0 || S.first_touch[b] < c;
                 if (!lv_) continue;
-                const double nj = L.n[S.bcol[b]];
+                const int jb = S.bcol[b];
+                const double nj = S.colour[jb] < c ? L.kt[jb] : L.n[jb];   // rectangular fill
                 pbytes += 4.0 * n * nj * w;
                 account(PH_PROJ, 4.0 * n * n * nj, 0);
             }
@@ -634,19 +635,27 @@ void FactorImpl<T>::run_level(size_t a) {
             const double ncol = nsum + kt;
             account(PH_LU, 2.0 / 3.0 * r * r * r + 4.0 * r * r * ncol, w * (4.0 * r * ncol + r * r));
         }
+        // Schur: targets read and written once; each contributor's operands D_{j,i_R}
+        // and W_U^i read once per colour (rows / columns of boxes eliminated before or
+        // in this colour: skeleton part only, rectangular fill)
+        auto live_lines = [&](int j) -> double { return S.colour[j] <= c ? L.kt[j] : L.n[j]; };
         for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
             const int tb = S.sch_tblk[t];
-            const int j = L.brow[tb], kk = S.bcol[tb];
-            const double m = L.n[j] - (S.colour[j] == c ? L.n[j] - L.kt[j] : 0);
-            const double nn = L.n[kk] - (S.colour[kk] == c ? L.n[kk] - L.kt[kk] : 0);
-            double fl = 0, by = 2.0 * m * nn * w;
+            const double m = live_lines(L.brow[tb]), nn = live_lines(S.bcol[tb]);
+            double fl = 0, reread = 0;
             for (int e = S.sch_tptr[t]; e < S.sch_tptr[t + 1]; ++e) {
-                const int i = S.sch_ci[e];
-                const double r = L.n[i] - L.kt[i];
+                const double r = L.n[S.sch_ci[e]] - L.kt[S.sch_ci[e]];
                 fl += 2.0 * m * nn * r;
-                by += w * r * (m + nn);
+                reread += w * r * (m + nn);
             }
-            account(PH_SCHUR, fl, by);
+            account(PH_SCHUR, fl, 2.0 * m * nn * w);
+            stats.schur_reread_bytes += reread;
+        }
+        for (int i : S.cboxes[c]) {
+            const double r = L.n[i] - L.kt[i];
+            double lines = 0;
+            for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p) lines += live_lines(S.nb_col[p]);
+            account(PH_SCHUR, 0, 2.0 * w * r * lines);
         }
     }
 }
@@ -785,6 +794,7 @@ void FactorImpl<T>::factorize() {
     ev.clear();
     ev_phase.clear();
     for (int p = 0; p < 8; ++p) stats.phase_ms[p] = stats.phase_flops[p] = stats.phase_bytes[p] = 0;
+    stats.schur_reread_bytes = 0;
     stats.error_level = stats.error_box = -1;
     H2_CUDA_CHECK(cudaMemsetAsync(status.ptr, 0, sizeof(DevStatus), stream));
     lv.clear();

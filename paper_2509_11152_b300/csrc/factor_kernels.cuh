@@ -483,12 +483,16 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
 // completely into shared memory before anything is written back.
 template <class T, int RPT, bool RIGHT>
 __global__ void __launch_bounds__(256)
-k_proj(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_blk) {
+k_proj(LevelArgs<T> a, int cur, const int* __restrict__ w_box, const int* __restrict__ w_blk) {
     constexpr int PW = 32, KC = 32;
     const int w = blockIdx.x;
-    const int i = w_box[w], b = w_blk[w], p0 = blockIdx.y * PW;
+    const int i = w_box[w], b = w_blk[w];
     const int n = a.n[i];
-    const int nj = RIGHT ? a.n[a.brow[b]] : a.n[a.bcol[b]];   // the block's other dimension
+    const int jb = RIGHT ? a.brow[b] : a.bcol[b];             // the block's other box
+    const int nj = a.n[jb];                                   // ... and dimension
+    // lines of a box eliminated in an earlier colour are zero except its skeleton part
+    // (rectangular fill, Sec. 2.1): only those are projected
+    const int p0 = (a.colour[jb] < cur ? nj - a.kt[jb] : 0) + blockIdx.y * PW;
     if (p0 >= nj) return;                                     // panel beyond the block
     const int pw = min(PW, nj - p0);
     const T* __restrict__ Q = a.Q + a.Q_off[i];
@@ -811,8 +815,10 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
     const int tb = tgt_blk[tt];
     const int j = a.brow[tb], kb = a.bcol[tb];
     const int nj = a.n[j], nk = a.n[kb];
-    const int row_lo = (a.colour[j] == cur) ? nj - a.kt[j] : 0;
-    const int col_lo = (a.colour[kb] == cur) ? nk - a.kt[kb] : 0;
+    // rows / columns of boxes eliminated before (or in) this colour: skeleton part only
+    // (their redundant rows and columns are exact zeros: rectangular fill, Sec. 2.1)
+    const int row_lo = (a.colour[j] <= cur) ? nj - a.kt[j] : 0;
+    const int col_lo = (a.colour[kb] <= cur) ? nk - a.kt[kb] : 0;
     const int m = nj - row_lo, nn = nk - col_lo;
     const int m0 = (mn >> 16) * BM, n0 = (mn & 0xffff) * BN;
     if (m0 >= m || n0 >= nn) return;
@@ -908,8 +914,11 @@ __global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, in
         const int tb = tgt_blk[tt];
         const int j = a.brow[tb], kb = a.bcol[tb];
         const int nj = a.n[j], nk = a.n[kb];
-        const int row_lo = (a.colour[j] == cur) ? nj - a.kt[j] : 0;
-        const int col_lo = (a.colour[kb] == cur) ? nk - a.kt[kb] : 0;
+        // a box eliminated in an earlier colour (or the contributor itself) keeps only
+        // its skeleton rows / columns: the redundant ones are exact zeros once the box is
+        // eliminated, so the update there is zero (rectangular fill, Sec. 2.1)
+        const int row_lo = (a.colour[j] <= cur) ? nj - a.kt[j] : 0;
+        const int col_lo = (a.colour[kb] <= cur) ? nk - a.kt[kb] : 0;
         SchurTgt r;
         r.coff = a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
         r.nj = nj;

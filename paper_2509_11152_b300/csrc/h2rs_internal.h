@@ -5,6 +5,8 @@
 
 #include <climits>
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -35,6 +37,28 @@ void count_launch(int64_t n = 1);
     do {                                                                             \
         if (!(cond)) throw ::h2rs::Error{(code), (msg)};                            \
     } while (0)
+
+// Runs f and turns every exception into a status code (and h2_last_error's message):
+// nothing is thrown across the C-ABI.
+template <class F>
+int guard(F&& f) {
+    try {
+        f();
+        return H2_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_error(e.what());
+        return H2_ERR_ARG;
+    } catch (...) {
+        set_error("unknown error");
+        return H2_ERR_ARG;
+    }
+}
 
 // device status word written by kernels (never trapped on)
 struct DevStatus {
@@ -201,6 +225,7 @@ void merge_forest(const std::vector<HostStructure>& parts, HostStructure& F, std
 struct MatrixObj {
     HostStructure H;
     Plan plan;
+    int device = 0;                           // device current at creation (holds the copies)
     cudaStream_t stream = nullptr;
     DevBuf U, E, S, D;                        // float64 values on the device
     DevBuf d_node_start, d_node_size, d_rank, d_U_off, d_E_off, d_S_off, d_D_off;

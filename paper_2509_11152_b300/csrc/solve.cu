@@ -72,7 +72,8 @@ __global__ void s_fwd_l(const int* __restrict__ tbox, const int* __restrict__ tp
     const int t = blockIdx.x;
     const int j = tbox[t];
     const int nj = n[j];
-    const int lo = (colour[j] == cur) ? nj - kt[j] : 0;
+    // boxes eliminated before (or in) this colour: rows j_R of W_L^i are exact zeros
+    const int lo = (colour[j] <= cur) ? nj - kt[j] : 0;
     const int m = nj - lo;
     T* xj = x + voff[j] * nrhs;
     for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {

@@ -42,6 +42,67 @@ def test_static_scratch_matvec_matches_allocating_matvec(h):
         assert _rel(y_st, y_ref) <= TOL, call
 
 
+def _pool_used(dev):
+    """(used bytes now, used-bytes high watermark) of the device's default memory pool,
+    the pool the library's stream-ordered allocations come from."""
+    from cuda.bindings import runtime as rt
+    err, pool = rt.cudaDeviceGetDefaultMemPool(dev)
+    assert err == rt.cudaError_t.cudaSuccess
+    err, cur = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+    assert err == rt.cudaError_t.cudaSuccess
+    err, high = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh)
+    assert err == rt.cudaError_t.cudaSuccess
+    return int(cur), int(high)
+
+
+def _pool_reset_high(dev):
+    from cuda.bindings import driver
+    from cuda.bindings import runtime as rt
+    err, pool = rt.cudaDeviceGetDefaultMemPool(dev)
+    assert err == rt.cudaError_t.cudaSuccess
+    (err,) = rt.cudaMemPoolSetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh, driver.cuuint64_t(0))
+    assert err == rt.cudaError_t.cudaSuccess
+
+
+def test_static_scratch_takes_nothing_from_the_pool(h):
+    """The point of the entry point: no device allocation during the call.  The
+    allocating h2_matvec raises the pool's used-memory high watermark above the memory
+    in use before the call (this shows the check can see an allocation);
+    h2_matvec_static leaves it there."""
+    pb = problem("cov2d", n=1024, leaf=32)
+    M = h.h2_matrix_create(pb.A)
+    dev = torch.cuda.current_device()
+    x = h.colmajor(torch.randn(pb.A.n, 2, dtype=torch.float64, device="cuda"))
+    y = h.colmajor(torch.zeros_like(x))
+    h.h2_matvec_static(M, x, y)                              # first call: address look-up
+    torch.cuda.synchronize()
+    for fn, allocates in ((h.h2_matvec, True), (h.h2_matvec_static, False), (h.h2_matvec_static, False)):
+        torch.cuda.synchronize()
+        _pool_reset_high(dev)
+        before, _ = _pool_used(dev)
+        fn(M, x, y)
+        torch.cuda.synchronize()
+        _, high = _pool_used(dev)
+        if allocates:
+            assert high > before, (fn.__name__, high, before)
+        else:
+            assert high <= before, (fn.__name__, high, before)
+
+
+def test_static_scratch_rejects_host_vectors(h):
+    """Host memory given to the C entry point is refused before any kernel runs."""
+    import ctypes
+    from paper_2509_11152_b300 import binding
+    pb = problem("cov2d", n=1024, leaf=32)
+    M = h.h2_matrix_create(pb.A)
+    xh = np.zeros((pb.A.n, 1))
+    yh = np.zeros((pb.A.n, 1))
+    rc = binding.lib().h2_matvec_static(M.handle, 1, ctypes.c_void_p(xh.ctypes.data), pb.A.n,
+                                        ctypes.c_void_p(yh.ctypes.data), pb.A.n)
+    assert rc == -1
+    assert b"device memory" in binding.lib().h2_last_error() or b"CUDA pointer" in binding.lib().h2_last_error()
+
+
 def test_static_scratch_rejects_oversize(h):
     pb = problem("cov2d", n=1024, leaf=32)
     M = h.h2_matrix_create(pb.A)
