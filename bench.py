@@ -260,11 +260,30 @@ def _oracle_sample(workload: str, n_sample: int):
 
 
 def _timed_oracle(workload: str, n_sample: int, threads: int):
-    """_oracle_sample with the BLAS pools limited to `threads` threads (the oracle's
-    own code is one Python thread; its parallelism is inside BLAS/LAPACK calls)."""
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(limits=threads):
-        return _oracle_sample(workload, n_sample)
+    """_oracle_sample in a fresh Python process whose BLAS / OpenMP pools have `threads`
+    threads (the oracle's own code is one Python thread; its parallelism is inside the
+    BLAS / LAPACK calls, whose pool size is fixed when numpy loads)."""
+    import tempfile
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    with tempfile.TemporaryDirectory() as d:
+        out = os.path.join(d, "oracle.npz")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", workload, str(n_sample), out],
+                           env=env, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"oracle child failed:\n{r.stderr[-3000:]}")
+        z = np.load(out)
+        sec, ns, it, berr = float(z["sec"]), int(z["n"]), int(z["it"]), float(z["berr"])
+        x, x0 = z["x"], z["x0"]
+    pb = _sample_problem(workload, ns)
+    from h2gen import rhs
+    return sec, ns, it, berr, x, x0, pb, rhs(ns, pb.workload.nrhs, seed=0)
+
+
+def _oracle_child(workload: str, n_sample: int, out: str) -> None:
+    sec, ns, it, berr, x, x0, _, _ = _oracle_sample(workload, n_sample)
+    np.savez(out, sec=sec, n=ns, it=it, berr=berr, x=x, x0=x0)
 
 
 def _cpu_baseline(workload: str, n_full: int, n_sample: int) -> tuple[dict, tuple]:
@@ -512,6 +531,9 @@ def run_ours(args, dist, rank, ws):
 
 
 def main():
+    if len(sys.argv) == 5 and sys.argv[1] == "--oracle-child":
+        _oracle_child(sys.argv[2], int(sys.argv[3]), sys.argv[4])
+        return
     args = _args()
     dist, rank, ws = _dist_init()
     try:

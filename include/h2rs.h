@@ -180,6 +180,12 @@ typedef struct {
 /* h2_factor_opts.flags: time every factorisation kernel launch with CUDA events
  * (h2_factor_stats.kernel_ms / kernel_launches); adds about a microsecond per launch */
 #define H2_FLAG_TIME_KERNELS 1
+/* h2_factor_opts.flags, for testing the failure path only: every wait of the
+ * tensor-core Schur pipeline (H2_PREC_TF32X3) gives up after one SM cycle instead of
+ * about two seconds, so the factorisation fails with H2_ERR_TIMEOUT (the kernel still
+ * waits, with the full budget, for the MMAs it issued before freeing tensor memory);
+ * the library stays usable afterwards */
+#define H2_FLAG_DEBUG_SHORT_WAIT 2
 
 /* kernel ids of h2_factor_stats.kernel_* */
 enum {

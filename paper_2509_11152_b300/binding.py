@@ -57,6 +57,7 @@ class h2_factor_stats(ctypes.Structure):
 PHASES = ["augment", "project", "lu_trsm", "schur", "close", "top", "leaf_load", "other"]
 KERNELS = ["gather", "basis", "proj", "zero", "lu", "trsm", "schur", "close", "top", "load"]
 H2_FLAG_TIME_KERNELS = 1
+H2_FLAG_DEBUG_SHORT_WAIT = 2
 
 # (name, restype, argtypes) of every exported entry point
 _SIGS = [

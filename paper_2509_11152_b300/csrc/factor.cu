@@ -97,29 +97,30 @@ constexpr int kSchurTile = 64;
 
 static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
                          const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
-                         const int* tmn, const SchurTgt*, const SchurCon*, int*) {
+                         const int* tmn, const SchurTgt*, const SchurCon*, int*, long long) {
     k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
 }
 
 static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c,
                          const int* tb, const int* tp, const int* cb, const int* ca, const int* ck,
                          const int* tt, const int* tmn, const SchurTgt* trec, const SchurCon* crec,
-                         int* counter) {
+                         int* counter, long long budget) {
     if (!tensor) {
         k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
         return;
     }
-    // tensor path: ntile = number of targets of the colour, trec offset to the first
+    // tensor path: ntile = number of targets of the colour, trec offset to the first;
+    // one persistent CTA per SM
     static const int nsm = [] {
-        H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
+        H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, ws::kSmem));
         int dev = 0, n = 0;
         H2_CUDA_CHECK(cudaGetDevice(&dev));
         H2_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
         return n;
     }();
-    const int grid = std::min(ntile, 4 * nsm);         // persistent: four CTAs per SM
+    const int grid = std::min(ntile, nsm);
     H2_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), s));
-    k_schur_tc<<<grid, 128, tc::kSmem, s>>>(ar, trec, crec, ntile, counter);
+    k_schur_tc<<<grid, ws::kThreads, ws::kSmem, s>>>(ar, trec, crec, ntile, counter, budget);
 }
 
 template <class T>
@@ -163,6 +164,7 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
             norm_sys[z] = o.sys_norm_a[z];
         }
     time_kernels = (o.flags & H2_FLAG_TIME_KERNELS) != 0;
+    if (o.flags & H2_FLAG_DEBUG_SHORT_WAIT) wait_budget = 1;
     stream = static_cast<cudaStream_t>(o.stream);
     status.alloc(sizeof(DevStatus), stream);
 }
@@ -586,7 +588,7 @@ void FactorImpl<T>::run_level(size_t a) {
             launch_schur(tensor_schur, ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
                          d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
                          d_tile_mn.as<int>() + t0, d_trec.as<SchurTgt>() + tg0, d_crec.as<SchurCon>(),
-                         d_counter.as<int>());
+                         d_counter.as<int>(), wait_budget);
             kend();
         }
         const int zn0 = S.zn_cptr[c], nzn = S.zn_cptr[c + 1] - zn0;

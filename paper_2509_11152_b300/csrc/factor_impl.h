@@ -67,6 +67,7 @@ struct FactorImpl : FactorBase {
     std::vector<int> ev_phase;
     // optional per-launch events (H2_FLAG_TIME_KERNELS)
     bool time_kernels = false;
+    long long wait_budget = 4000000000LL;     // tensor-core Schur pipeline waits (SM cycles)
     std::vector<cudaEvent_t> kev;
     std::vector<int> kev_id;
     void kbegin(int id);

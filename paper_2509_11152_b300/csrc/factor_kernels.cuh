@@ -12,7 +12,7 @@
 #include <cmath>
 
 #include "factor_args.cuh"
-#include "schur_tc.cuh"
+#include "schur_ws.cuh"
 
 namespace h2rs {
 
@@ -849,7 +849,10 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
             ri = a.n[i] - a.kt[i];
             if (ri <= 0) continue;
             A = a.blk + a.blk_off[c_ablk[c]] + row_lo;                        // m x ri, ld nj
-            B = a.WU + a.WU_off[i] + (int64_t)a.nbofs[a.nb_ptr[i] + c_kpos[c]] * ri;   // ri x nn, ld ri
+            // W_U^i holds all n_k columns of a neighbour k (col_lo: skip the zero ones of
+            // an eliminated k) but only the skeleton columns of i itself
+            B = a.WU + a.WU_off[i] +
+                (int64_t)(a.nbofs[a.nb_ptr[i] + c_kpos[c]] + (kb == i ? 0 : col_lo)) * ri;   // ri x nn, ld ri
             k0 = 0;
             return true;
         }
@@ -932,84 +935,198 @@ __global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, in
         const int e = e0 + (x - nt);
         const int i = c_box[e];
         const int ri = a.n[i] - a.kt[i];
+        const int p = a.nb_ptr[i] + c_kpos[e];
+        const int kb = a.nb_col[p];                  // the target's column box
+        // W_U^i holds all n_k columns of a neighbour k, of which an eliminated k's first
+        // n_k - kt_k are zero (skipped); of i itself it holds the skeleton columns only
+        const int cl = (kb != i && a.colour[kb] < cur) ? a.n[kb] - a.kt[kb] : 0;
         SchurCon r;
         r.aoff = a.blk_off[c_ablk[e]];
-        r.boff = a.WU_off[i] + (int64_t)a.nbofs[a.nb_ptr[i] + c_kpos[e]] * ri;
+        r.boff = a.WU_off[i] + (int64_t)(a.nbofs[p] + cl) * ri;
         r.ri = ri > 0 ? ri : 0;
         r.pad = 0;
         crec[e] = r;
     }
 }
 
-// Float32 factor: the same target-owned update on the tcgen05 tensor cores.  A
-// persistent grid (a few CTAs of 128 threads per SM) takes the colour's targets one at
-// a time from a counter (zero before the launch), so that long and short targets
-// balance, and walks each target's 128 x 64 tiles in turn; a tile's K runs over its
-// contributors in 16-wide slices; split-TF32 products, see schur_tc.cuh.
-__global__ void __launch_bounds__(128, 4)
+// Float32 factor: the same target-owned update on the tcgen05 tensor cores, one
+// persistent warp-specialised CTA per SM (schur_ws.cuh).  Targets come from a counter
+// (zero before the launch); `budget` bounds every pipeline wait (SM cycles).
+__global__ void __launch_bounds__(ws::kThreads, 1)
 k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon* __restrict__ crec, int ntgt,
-           int* __restrict__ counter) {
+           int* __restrict__ counter, long long budget) {
+    using namespace ws;
     extern __shared__ __align__(1024) unsigned char sm_tc[];
-    __shared__ int next_tgt;
-    bool active = false;                             // a target is being walked
-    int first = 0;
-    SchurTgt tg{};
-    SchurCon cr{};
-    int c = 0, k0 = 0, tm = 0, tn = 0, ntm = 0, ntn = 0;
-    tc::TileOut out{};
-    auto start_tile = [&]() {
-        const int m0 = tm * tc::TBM, n0 = tn * tc::TBN;
-        out.C = a.blk + tg.coff + m0 + (int64_t)n0 * tg.nj;
-        out.ldc = tg.nj;
-        out.mv = min(tc::TBM, tg.m - m0);
-        out.nv = min(tc::TBN, tg.nn - n0);
-        c = tg.cb;
-        k0 = 0;
-        if (c < tg.ce) cr = crec[c];
-        first = 1;
-    };
-    auto gen = [&](tc::SliceT& st) -> bool {
-        for (;;) {
-            if (!active) {
-                __syncthreads();                         // every thread calls gen in step
-                if (threadIdx.x == 0) next_tgt = atomicAdd(counter, 1);
-                __syncthreads();
-                const int t = next_tgt;
-                if (t >= ntgt) return false;
-                tg = trec[t];
-                ntm = (tg.m + tc::TBM - 1) / tc::TBM;
-                ntn = (tg.nn + tc::TBN - 1) / tc::TBN;
-                if (ntm <= 0 || ntn <= 0) continue;
-                tm = tn = 0;
-                start_tile();
-                active = true;
-            }
-            while (c < tg.ce) {
-                if (k0 < cr.ri) {
-                    // D_{j, i_R}: m x ri (ld nj); W_U^i columns of the target: ri x nn (ld ri)
-                    const int m0 = tm * tc::TBM, n0 = tn * tc::TBN;
-                    st.sl.A = a.blk + cr.aoff + tg.row_lo + m0 + (int64_t)k0 * tg.nj;
-                    st.sl.lda = tg.nj;
-                    st.sl.B = a.WU + cr.boff + (int64_t)n0 * cr.ri + k0;
-                    st.sl.ldb = cr.ri;
-                    st.sl.kv = min(tc::TBK, cr.ri - k0);
-                    st.out = out;
-                    st.first = first;
-                    first = 0;
-                    k0 += tc::TBK;
-                    return true;
-                }
-                ++c;
-                k0 = 0;
-                if (c < tg.ce) cr = crec[c];
-            }
-            // tile done (no slice: nothing to add); next tile of the target, or next target
-            if (++tn == ntn) { tn = 0; ++tm; }
-            if (tm < ntm) start_tile();
-            else active = false;
+    unsigned char* ring = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(sm_tc) + 1023) & ~static_cast<uintptr_t>(1023));
+    float* Cs = reinterpret_cast<float*>(ring + (size_t)kStages * kStageBytes);   // BM x BN, ld BM
+    Ctrl* ctl = reinterpret_cast<Ctrl*>(ring + (size_t)kStages * kStageBytes + kCBytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort = &ctl->abort;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            tc::mbar_init(&ctl->full[st], kProdWarps);
+            tc::mbar_init(&ctl->empty[st], 1);
         }
-    };
-    if (!tc::tiles_sub(gen, sm_tc) && threadIdx.x == 0) dev_fail(a.status, H2_ERR_TIMEOUT, a.level, -1);
+        for (int q = 0; q < 2; ++q) {
+            tc::mbar_init(&ctl->accfull[q], 1);
+            tc::mbar_init(&ctl->accempty[q], kEpiWarps);
+        }
+        for (int q = 0; q < kTrec; ++q) {
+            tc::mbar_init(&ctl->tfull[q], 1);
+            tc::mbar_init(&ctl->tempty[q], kEpiWarps);
+        }
+        tc::mbar_init(&ctl->drain, 1);
+        *abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == kMmaWarp) {
+        tc::tmem_alloc(&ctl->tmem, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp < kProdWarps) {
+        // ---------------- producers
+        Walk w{trec, crec, ntgt, counter, a.blk, a.WU, ctl, tid, budget};
+        float ra[kPrefetch][8], rb[kPrefetch][8];
+        int hf[kPrefetch], hn[kPrefetch];
+        bool have[kPrefetch];
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) have[j] = false;
+        // slot j holds slice s + j of the ring order: it is stored, then refilled with
+        // the slice kPrefetch further on
+        bool more = true;
+        int s = 0;
+        do {
+#pragma unroll
+            for (int j = 0; j < kPrefetch; ++j) {
+                if (have[j]) put_stage(ctl, ring, s++, tid, hf[j], hn[j], ra[j], rb[j], budget);
+                have[j] = false;
+                if (more) {
+                    SliceMeta m;
+                    more = w.next(m);
+                    if (more) {
+                        load_slice(m, tid, ra[j], rb[j]);
+                        hf[j] = m.flags;
+                        hn[j] = m.n;
+                        have[j] = true;
+                    }
+                }
+            }
+        } while (more || have[0] || have[1] || have[2]);
+        static_assert(kPrefetch == 3, "the loop condition names every slot");
+        // end markers: a stage for the MMA thread, a tile record for the epilogue
+        if (!*abort) {
+            const int st = s % kStages, use = s / kStages;
+            if (use >= 1 && lane == 0) wait_phase(&ctl->empty[st], (use - 1) & 1, abort, budget);
+            __syncwarp();
+            if (tid == 0) ctl->hdr[st] = StageHdr{F_END, 0};
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->full[st]);
+        }
+        if (tid == 0) {
+            TileRec r{};
+            r.end = 1;
+            w.publish(r);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue (one thread)
+        if (lane == 0) {
+            int s = 0, tile = 0;
+            bool issued = false;
+            for (;;) {
+                const int st = s % kStages, use = s / kStages;
+                if (!wait_phase(&ctl->full[st], use & 1, abort, budget)) break;
+                const StageHdr h = ctl->hdr[st];
+                if (h.flags & F_END) break;
+                const int acc = tile & 1, accuse = tile >> 1;
+                if ((h.flags & F_FIRST) && accuse >= 1 &&
+                    !wait_phase(&ctl->accempty[acc], (accuse - 1) & 1, abort, budget))
+                    break;
+                tc::fence_after();
+                const uint32_t base = tc::smem_u32(ring + (size_t)st * kStageBytes);
+                const uint32_t d = tmem + (uint32_t)acc * kAccCols;
+                const uint32_t idesc = tc::idesc_tf32(BM, h.n);
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    const uint32_t o = kk * 2 * tc::kLBO;          // two core matrices per 8 k
+                    const uint64_t aH = tc::sdesc(base + o, tc::kLBO, kSBO);
+                    const uint64_t aL = tc::sdesc(base + kPart + o, tc::kLBO, kSBO);
+                    const uint64_t bH = tc::sdesc(base + 2 * kPart + o, tc::kLBO, kSBO);
+                    const uint64_t bL = tc::sdesc(base + 3 * kPart + o, tc::kLBO, kSBO);
+                    tc::mma_tf32(d, aL, bH, idesc, ((h.flags & F_FIRST) && kk == 0) ? 0 : 1);   // small terms first
+                    tc::mma_tf32(d, aH, bL, idesc, 1);
+                    tc::mma_tf32(d, aH, bH, idesc, 1);
+                }
+                issued = true;
+                tc::mma_commit(&ctl->empty[st]);                    // frees the stage
+                if (h.flags & F_LAST) {
+                    tc::mma_commit(&ctl->accfull[acc]);             // the tile's sum is final
+                    ++tile;
+                }
+                ++s;
+            }
+            // every MMA issued has completed before tensor memory is freed (full budget)
+            if (issued) {
+                tc::mma_commit(&ctl->drain);
+                if (!tc::mbar_wait(&ctl->drain, 0, kWaitCycles)) *abort = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: C -= accumulator
+        const int q = warp & 3;                                      // tensor-memory lane quadrant
+        const int row = 32 * q + lane;
+        float* Cr = Cs + row;                                        // this thread's row, stride BM
+        int tile = 0;
+        for (;;) {
+            const int slot = tile % kTrec;
+            if (!wait_phase(&ctl->tfull[slot], (tile / kTrec) & 1, abort, budget)) break;
+            const TileRec r = ctl->trec[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->tempty[slot]);
+            if (r.end) break;
+            const bool rok = row < r.mv;
+            float* Crow = r.C + row;
+            if (rok)
+                for (int col = 0; col < r.nv; ++col) cp_async4(Cr + col * BM, Crow + (int64_t)col * r.ldc);
+            cp_async_commit();
+            const int acc = tile & 1;
+            if (!wait_phase(&ctl->accfull[acc], (tile >> 1) & 1, abort, budget)) break;
+            tc::fence_after();
+            cp_async_wait_all();
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * kAccCols;
+            const int ncc = (r.nv + 15) / 16;                        // warp-uniform
+            for (int cc = 0; cc < ncc; ++cc) {
+                float v[16];
+                tc::tmem_ld16(taddr + 16 * cc, v);
+                if (rok) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = 16 * cc + j;
+                        if (col < r.nv) Crow[(int64_t)col * r.ldc] = Cr[col * BM] - v[j];
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->accempty[acc]);
+            ++tile;
+        }
+        cp_async_wait_all();                                         // none left in flight
+    }
+    // every role is done (or has given up): free tensor memory
+    tc::fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+    if (tid == 0 && *abort) dev_fail(a.status, H2_ERR_TIMEOUT, a.level, -1);
 }
 
 // ================================================================== level close

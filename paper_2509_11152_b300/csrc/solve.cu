@@ -83,7 +83,9 @@ __global__ void s_fwd_l(const int* __restrict__ tbox, const int* __restrict__ tp
             const int i = ci[q];
             const int ri = n[i] - kt[i];
             if (ri <= 0) continue;
-            const int row = nbofs[nb_ptr[i] + cpos[q]] + a;
+            // W_L^i holds all n_j rows of a neighbour j (skip the zero rows of an
+            // eliminated j) but only the skeleton rows of i itself
+            const int row = nbofs[nb_ptr[i] + cpos[q]] + (j == i ? 0 : lo) + a;
             const T* W = WL + WL_off[i] + row;
             const int64_t ld = WLld[i];
             const T* xr = x + voff[i] * nrhs + (int64_t)c * n[i];

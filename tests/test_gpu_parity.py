@@ -35,6 +35,15 @@ def h():
 
 
 @functools.lru_cache(maxsize=None)
+def dense_solution(name, nrhs, seed, **over):
+    """A^-1 b of the expanded H^2 matrix (float64 LAPACK): the exact solution the
+    refined results are compared with."""
+    pb = problem(name, **over)
+    A = pb.A.numpy()
+    return np.linalg.solve(dense.expand(A), rhs(A.n, nrhs, seed=seed))
+
+
+@functools.lru_cache(maxsize=None)
 def oracle_solution(name, eps, nrhs, seed, **over):
     pb = problem(name, **over)
     A = pb.A.numpy()
@@ -52,6 +61,8 @@ CASES = [
     ("gauss3d", dict(n=1500, leaf=32), 1e-6),            # ragged leaves (46/47 points)
     ("helmholtz3d", dict(n=4096, leaf=64), 1e-6),         # indefinite oscillatory IE, 16^3 lattice
     ("lru3d", dict(n=4096, leaf=64), 1e-7),               # covariance + rank-32 update
+    ("sphere", dict(n=8192), 1e-5),                       # the benchmark's leaf size (128)
+    ("lru3d", dict(n=8192, leaf=128), 1e-7),              # level-2 boxes of up to 200 points
 ]
 IDS = [f"{c[0]}-{c[1].get('n', 'full')}" for c in CASES]
 
@@ -93,10 +104,21 @@ def test_fp32_factor_with_refinement(h, name, over, eps, prec):
     bt = h.colmajor(torch.from_numpy(b).cuda())
     xt = h.colmajor(torch.zeros_like(bt))
     it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
-    assert ok and berr <= BERR_TOL
     x = xt.cpu().numpy()
+    # the error against the float64 oracle, stated for every result: the unrefined
+    # solve against the oracle's (same algorithm and eps_lu, float64), the refined
+    # solution against the exact solve of the H^2 matrix
+    x1 = h.colmajor(torch.from_numpy(b).cuda())
+    h.h2_solve(Z, x1)
+    e_solve = np.linalg.norm(x1.cpu().numpy() - x0) / np.linalg.norm(x0)
+    xd = dense_solution(name, 2, 1, **over)
+    e_ref = np.linalg.norm(x - xd) / np.linalg.norm(xd)
+    msg = (f"{name} {prec}: {it} corrections, berr {berr:.2e}; solve vs oracle solve {e_solve:.2e}, "
+           f"refined vs exact {e_ref:.2e}")
+    print(msg)
+    assert ok and berr <= BERR_TOL, msg
     nw, _ = dense.backward_error(A, x, b, pb.norm_a)       # the oracle's own matvec
-    assert nw <= BERR_TOL, nw
+    assert nw <= BERR_TOL, (nw, msg)
     # ranks of the float32 factor stay those of the float64 oracle almost everywhere
     lay = h.h2_layout_get(Z, 0)
     r0 = np.asarray([bx.kt for bx in Z0.levels[0].boxes])
@@ -201,3 +223,22 @@ def test_gmres_refinement_when_plain_corrections_stall(h):
     assert ok and berr <= BERR_TOL and it > 3
     nw, _ = dense.backward_error(A, xt.cpu().numpy(), b, pb.norm_a)
     assert nw <= BERR_TOL
+
+
+def test_schur_pipeline_timeout_is_reported_and_context_survives(h):
+    """The tensor-core Schur kernel's bounded waits: with H2_FLAG_DEBUG_SHORT_WAIT every
+    pipeline wait gives up after one cycle (the wait for the MMAs already issued keeps
+    its full budget), so the factorisation fails with H2_ERR_TIMEOUT instead of hanging,
+    and the library and the CUDA context stay usable."""
+    name, over, eps = "sphere", dict(n=4096, leaf=64), 1e-5
+    pb, A, b, Z0, x0 = oracle_solution(name, eps, 2, 1, **over)
+    M = h.h2_matrix_create(pb.A)
+    from paper_2509_11152_b300 import binding
+    with pytest.raises(h.H2Error) as e:
+        h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_TF32X3, flags=binding.H2_FLAG_DEBUG_SHORT_WAIT)
+    assert e.value.code == -7                       # H2_ERR_TIMEOUT
+    Z = h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_TF32X3)
+    bt = h.colmajor(torch.from_numpy(b).cuda())
+    xt = h.colmajor(torch.zeros_like(bt))
+    it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
+    assert ok and berr <= BERR_TOL
