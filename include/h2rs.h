@@ -199,7 +199,8 @@ enum {
     H2_K_CLOSE = 7,             /* level close (blocks and bases)                      */
     H2_K_TOP = 8,               /* top-level assembly and float64 LU                   */
     H2_K_LOAD = 9,              /* leaf near-field and basis load                      */
-    H2_K_COUNT = 10
+    H2_K_PACK = 10,             /* TF32 hi / lo packing of the tensor-core Schur operands */
+    H2_K_COUNT = 11
 };
 
 /* Factorise A (Alg. 1): levels d..t, greedy colours in order, per colour the

@@ -55,7 +55,7 @@ class h2_factor_stats(ctypes.Structure):
 
 
 PHASES = ["augment", "project", "lu_trsm", "schur", "close", "top", "leaf_load", "other"]
-KERNELS = ["gather", "basis", "proj", "zero", "lu", "trsm", "schur", "close", "top", "load"]
+KERNELS = ["gather", "basis", "proj", "zero", "lu", "trsm", "schur", "close", "top", "load", "pack"]
 H2_FLAG_TIME_KERNELS = 1
 H2_FLAG_DEBUG_SHORT_WAIT = 2
 

@@ -97,20 +97,21 @@ constexpr int kSchurTile = 64;
 
 static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
                          const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
-                         const int* tmn, const SchurTgt*, const SchurCon*, int*, long long) {
+                         const int* tmn, const SchurTgt*, const SchurCon*, const unsigned char*,
+                         const unsigned char*, long long) {
     k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
 }
 
 static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c,
                          const int* tb, const int* tp, const int* cb, const int* ca, const int* ck,
                          const int* tt, const int* tmn, const SchurTgt* trec, const SchurCon* crec,
-                         int* counter, long long budget) {
+                         const unsigned char* pA, const unsigned char* pB, long long budget) {
     if (!tensor) {
         k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
         return;
     }
     // tensor path: ntile = number of targets of the colour, trec offset to the first;
-    // one persistent CTA per SM
+    // persistent CTAs, two per SM
     static const int nsm = [] {
         H2_CUDA_CHECK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, ws::kSmem));
         int dev = 0, n = 0;
@@ -118,9 +119,16 @@ static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs
         H2_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
         return n;
     }();
-    const int grid = std::min(ntile, nsm);
-    H2_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), s));
-    k_schur_tc<<<grid, ws::kThreads, ws::kSmem, s>>>(ar, trec, crec, ntile, counter, budget);
+    const int grid = std::min(ntile, ws::kCtasPerSm * nsm);
+    k_schur_tc<<<grid, ws::kThreads, ws::kSmem, s>>>(ar, trec, crec, ntile, pA, pB, budget);
+}
+
+// operand packing of the tensor-core Schur update (float32 factors only)
+static void launch_pack(int, int, cudaStream_t, const LevelArgs<double>&, const int*, const int*, const int64_t*,
+                        unsigned char*, unsigned char*) {}
+static void launch_pack(int npk, int c, cudaStream_t s, const LevelArgs<float>& ar, const int* box,
+                        const int* pos, const int64_t* off, unsigned char* pA, unsigned char* pB) {
+    k_schur_pack<<<dim3(npk, 2), 256, 0, s>>>(ar, c, box, pos, off, pA, pB);
 }
 
 template <class T>
@@ -474,9 +482,28 @@ void FactorImpl<T>::run_level(size_t a) {
     upload(d_tile_mn, W.tile_mn, s);
     const DevBuf &d_tgt_blk = S.dev.sch_tblk, &d_tgt_ptr = S.dev.sch_tptr, &d_c_box = S.dev.sch_ci,
                  &d_c_ablk = S.dev.sch_cA, &d_c_kpos = S.dev.sch_ckpos;
-    DevBuf d_trec, d_crec, d_counter;                      // Schur records (tensor-core path)
+    DevBuf d_trec, d_crec;                                 // Schur records (tensor-core path)
+    // packed operands of the tensor-core Schur update: one region per near-field
+    // position of every box, offsets restarting in every colour and bounded by the box
+    // sizes (the ranks are not known here); the buffers fit the largest colour
+    DevBuf d_pk_off, packA, packB;
     if (tensor_schur) {
-        d_counter.alloc(sizeof(int), s);
+        std::vector<int64_t> pk(S.nb_col.size() + 1, 0);
+        int64_t mx = 256;
+        for (int c = 0; c < nc; ++c) {
+            int64_t off = 0;
+            for (int q = S.pk_cptr[c]; q < S.pk_cptr[c + 1]; ++q) {
+                const int p = S.pk_pos[q];
+                pk[p] = off;
+                off += ws::pack_region_bytes(L.n[S.pk_box[q]], L.n[S.nb_col[p]]);
+            }
+            mx = std::max(mx, off);
+        }
+        upload(d_pk_off, pk, s);
+        track(this, packA, mx, s);
+        track(this, packB, mx, s);
+    }
+    if (tensor_schur) {
         d_trec.alloc(std::max<size_t>(1, S.sch_tblk.size()) * sizeof(SchurTgt), s);
         d_crec.alloc(std::max<size_t>(1, S.sch_ci.size()) * sizeof(SchurCon), s);
     }
@@ -571,6 +598,16 @@ void FactorImpl<T>::run_level(size_t a) {
         H2_LAUNCHED();
         H2_CUDA_CHECK(cudaGetLastError());
         mark(PH_LU);
+        if (tensor_schur) {
+            const int q0 = S.pk_cptr[c], nq = S.pk_cptr[c + 1] - q0;
+            if (nq) {
+                kbegin(H2_K_PACK);
+                launch_pack(nq, c, s, ar, S.dev.pk_box.as<int>() + q0, S.dev.pk_pos.as<int>() + q0,
+                            d_pk_off.as<int64_t>(), packA.as<unsigned char>(), packB.as<unsigned char>());
+                kend();
+                H2_LAUNCHED();
+            }
+        }
         // ---- Schur update and zeroing of the eliminated rows / columns
         const int t0 = W.tile_cptr[c];
         const int tg0 = S.sch_cptr[c], ntg = S.sch_cptr[c + 1] - tg0;
@@ -581,14 +618,15 @@ void FactorImpl<T>::run_level(size_t a) {
                 const int e0 = S.sch_tptr[tg0], ne = S.sch_tptr[tg0 + ntg] - e0;
                 k_schur_prep<T><<<(unsigned)((ntg + ne + 255) / 256), 256, 0, s>>>(
                     ar, c, tg0, ntg, e0, ne, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
-                    d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_trec.as<SchurTgt>(), d_crec.as<SchurCon>());
+                    S.dev.sch_cjpos.as<int>(), d_c_kpos.as<int>(), d_pk_off.as<int64_t>(), d_trec.as<SchurTgt>(),
+                    d_crec.as<SchurCon>());
                 H2_LAUNCHED();
                 count_launch();
             }
             launch_schur(tensor_schur, ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
                          d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
                          d_tile_mn.as<int>() + t0, d_trec.as<SchurTgt>() + tg0, d_crec.as<SchurCon>(),
-                         d_counter.as<int>(), wait_budget);
+                         packA.as<unsigned char>(), packB.as<unsigned char>(), wait_budget);
             kend();
         }
         const int zn0 = S.zn_cptr[c], nzn = S.zn_cptr[c + 1] - zn0;
@@ -609,6 +647,10 @@ void FactorImpl<T>::run_level(size_t a) {
     H2_CUDA_CHECK(cudaStreamSynchronize(s));
     stats.host_ms[3] += ht.lap();
     untrack(this, scratch);
+    if (tensor_schur) {
+        untrack(this, packA);
+        untrack(this, packB);
+    }
     // ---------------- algorithmic counts of this level (for roofline fractions)
     const double w = sizeof(T);
     for (int c = 0; c < nc; ++c) {

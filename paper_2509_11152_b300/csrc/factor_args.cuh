@@ -61,18 +61,21 @@ struct TopSys {
 
 // Schur update records, filled per colour once the colour's ranks and W_U are known
 // (so that a tile walks one record per contributor instead of a chain of index loads).
+struct SchurCon {
+    int64_t aoff;          // byte offset of the packed D_{j,i_R} region (A operand)
+    int64_t boff;          // byte offset of the packed W_U^i[k] region (B operand)
+    int ri;                // redundant size of contributor i (0: nothing to add)
+    int pad;
+};
 struct SchurTgt {
     int64_t coff;          // element offset of the target's first updated entry in blk
     int nj;                // leading dimension (rows of the target block)
     int m, nn;             // updated rows / columns
-    int row_lo;            // first updated row (A operands start there too)
+    int row_lo;            // first updated row
     int cb, ce;            // contributor records cb .. ce-1
-};
-struct SchurCon {
-    int64_t aoff;          // block (j, i): D_{j, i_R} starts at blk + aoff (+ row_lo)
-    int64_t boff;          // W_U^i columns of the target's column box: WU + boff (ld ri)
-    int ri;                // redundant size of contributor i (0: nothing to add)
-    int pad;
+    int nsl;               // K slices of 16 over all contributors
+    int ga, gb;            // row groups per part of a packed slice: ceil(n_j / 8), ceil(n_k / 8)
+    SchurCon c0;           // copy of record cb (read with the target: one load less)
 };
 
 // Per-colour work lists of the basis kernels (device pointers).

@@ -904,13 +904,94 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
         }
 }
 
+// ---- tensor-core path: operand packing, records, update (see schur_ws.cuh)
+
+// Live lines of neighbour b of a box of colour `cur`: all n_b of a box eliminated
+// later, the skeleton part of one eliminated before (or in) this colour.
+template <class T>
+__device__ inline int live_lo(const LevelArgs<T>& a, int cur, int b) {
+    return a.colour[b] <= cur ? a.n[b] - a.kt[b] : 0;
+}
+
+// 16 bytes of hi and lo TF32 parts of four values
+__device__ inline void split_store(unsigned char* hi, unsigned char* lo, const float (&x)[4]) {
+    float4 h, l;
+    h.x = tc::to_tf32(x[0]); l.x = tc::to_tf32(x[0] - h.x);
+    h.y = tc::to_tf32(x[1]); l.y = tc::to_tf32(x[1] - h.y);
+    h.z = tc::to_tf32(x[2]); l.z = tc::to_tf32(x[2] - h.z);
+    h.w = tc::to_tf32(x[3]); l.w = tc::to_tf32(x[3] - h.w);
+    *reinterpret_cast<float4*>(hi) = h;
+    *reinterpret_cast<float4*>(lo) = l;
+}
+
+// Packs one (box i, neighbour position p) pair of the colour (blockIdx.y = 0: A region
+// D_{b,i_R}; 1: B region W_U^i[b]) in the layout of schur_ws.cuh.
+__global__ void __launch_bounds__(256)
+k_schur_pack(LevelArgs<float> a, int cur, const int* __restrict__ pk_box, const int* __restrict__ pk_pos,
+             const int64_t* __restrict__ pk_off, unsigned char* __restrict__ pA, unsigned char* __restrict__ pB) {
+    const int i = pk_box[blockIdx.x], p = pk_pos[blockIdx.x];
+    const int r = a.n[i] - a.kt[i];
+    if (r <= 0) return;
+    const int b = a.nb_col[p], nb = a.n[b];
+    const int G = (nb + 7) / 8;
+    const bool isB = blockIdx.y == 1;
+    const float* src;
+    int64_t ls, ks;                                   // strides of line and k in the source
+    int lines;
+    if (!isB) {                                       // D_{b,i_R}: block (b, i), live rows of b
+        const int lo = live_lo(a, cur, b);
+        src = a.blk + a.blk_off[a.nb_blkT[p]] + lo;
+        ls = 1;
+        ks = nb;
+        lines = nb - lo;
+    } else {                                          // W_U^i columns of b (ld r)
+        const int lo = b == i ? 0 : (a.colour[b] < cur ? nb - a.kt[b] : 0);
+        src = a.WU + a.WU_off[i] + (int64_t)(a.nbofs[p] + lo) * r;
+        ls = r;
+        ks = 1;
+        lines = b == i ? a.kt[i] : nb - lo;
+    }
+    unsigned char* dst = (isB ? pB : pA) + pk_off[p];
+    const int gv = (lines + 7) / 8, ns = (r + ws::BK - 1) / ws::BK;
+    const int items = ns * 4 * gv * 8;                // (slice, k group, row group, line in group)
+    for (int x = threadIdx.x; x < items; x += blockDim.x) {
+        const int l8 = x & 7;
+        int rest = x >> 3;
+        const int g = rest % gv;
+        rest /= gv;
+        const int q = rest & 3, sl = rest >> 2;
+        const int line = 8 * g + l8, k0 = ws::BK * sl + 4 * q;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            v[e] = (line < lines && k0 + e < r) ? __ldg(src + line * ls + (int64_t)(k0 + e) * ks) : 0.f;
+        unsigned char* o = dst + (int64_t)sl * 2 * G * ws::kGroup + g * ws::kGroup + q * 128 + l8 * 16;
+        split_store(o, o + (int64_t)G * ws::kGroup, v);
+    }
+}
+
 // Records of one colour's Schur targets and contributors (one thread per record).
+// Contributor record e of the tensor-core path: the packed A and B regions.
+template <class T>
+__device__ inline SchurCon schur_con(const LevelArgs<T>& a, int e, const int* __restrict__ c_box,
+                                     const int* __restrict__ c_jpos, const int* __restrict__ c_kpos,
+                                     const int64_t* __restrict__ pk_off) {
+    const int i = c_box[e];
+    const int ri = a.n[i] - a.kt[i];
+    SchurCon r;
+    r.aoff = pk_off[a.nb_ptr[i] + c_jpos[e]];
+    r.boff = pk_off[a.nb_ptr[i] + c_kpos[e]];
+    r.ri = ri > 0 ? ri : 0;
+    r.pad = 0;
+    return r;
+}
+
 template <class T>
 __global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, int ne,
                              const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
-                             const int* __restrict__ c_box, const int* __restrict__ c_ablk,
-                             const int* __restrict__ c_kpos, SchurTgt* __restrict__ trec,
-                             SchurCon* __restrict__ crec) {
+                             const int* __restrict__ c_box, const int* __restrict__ c_jpos,
+                             const int* __restrict__ c_kpos, const int64_t* __restrict__ pk_off,
+                             SchurTgt* __restrict__ trec, SchurCon* __restrict__ crec) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x < nt) {
         const int tt = t0 + x;
@@ -920,8 +1001,8 @@ __global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, in
         // a box eliminated in an earlier colour (or the contributor itself) keeps only
         // its skeleton rows / columns: the redundant ones are exact zeros once the box is
         // eliminated, so the update there is zero (rectangular fill, Sec. 2.1)
-        const int row_lo = (a.colour[j] <= cur) ? nj - a.kt[j] : 0;
-        const int col_lo = (a.colour[kb] <= cur) ? nk - a.kt[kb] : 0;
+        const int row_lo = live_lo(a, cur, j);
+        const int col_lo = live_lo(a, cur, kb);
         SchurTgt r;
         r.coff = a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
         r.nj = nj;
@@ -930,42 +1011,38 @@ __global__ void k_schur_prep(LevelArgs<T> a, int cur, int t0, int nt, int e0, in
         r.row_lo = row_lo;
         r.cb = tgt_ptr[tt];
         r.ce = tgt_ptr[tt + 1];
+        int nsl = 0;
+        for (int e = r.cb; e < r.ce; ++e) {
+            const int ri = a.n[c_box[e]] - a.kt[c_box[e]];
+            if (ri > 0) nsl += (ri + ws::BK - 1) / ws::BK;
+        }
+        r.nsl = nsl;
+        r.ga = (nj + 7) / 8;
+        r.gb = (nk + 7) / 8;
+        r.c0 = r.cb < r.ce ? schur_con(a, r.cb, c_box, c_jpos, c_kpos, pk_off) : SchurCon{0, 0, 0, 0};
         trec[tt] = r;
     } else if (x < nt + ne) {
         const int e = e0 + (x - nt);
-        const int i = c_box[e];
-        const int ri = a.n[i] - a.kt[i];
-        const int p = a.nb_ptr[i] + c_kpos[e];
-        const int kb = a.nb_col[p];                  // the target's column box
-        // W_U^i holds all n_k columns of a neighbour k, of which an eliminated k's first
-        // n_k - kt_k are zero (skipped); of i itself it holds the skeleton columns only
-        const int cl = (kb != i && a.colour[kb] < cur) ? a.n[kb] - a.kt[kb] : 0;
-        SchurCon r;
-        r.aoff = a.blk_off[c_ablk[e]];
-        r.boff = a.WU_off[i] + (int64_t)(a.nbofs[p] + cl) * ri;
-        r.ri = ri > 0 ? ri : 0;
-        r.pad = 0;
-        crec[e] = r;
+        crec[e] = schur_con(a, e, c_box, c_jpos, c_kpos, pk_off);
     }
 }
 
-// Float32 factor: the same target-owned update on the tcgen05 tensor cores, one
-// persistent warp-specialised CTA per SM (schur_ws.cuh).  Targets come from a counter
-// (zero before the launch); `budget` bounds every pipeline wait (SM cycles).
-__global__ void __launch_bounds__(ws::kThreads, 1)
+// Float32 factor: the same target-owned update on the tcgen05 tensor cores, persistent
+// warp-specialised CTAs (two per SM) over the packed operands (schur_ws.cuh); CTA b
+// takes targets b, b + gridDim.x, ...; `budget` bounds every pipeline wait (SM cycles).
+__global__ void __launch_bounds__(ws::kThreads, ws::kCtasPerSm)
 k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon* __restrict__ crec, int ntgt,
-           int* __restrict__ counter, long long budget) {
+           const unsigned char* __restrict__ pA, const unsigned char* __restrict__ pB, long long budget) {
     using namespace ws;
     extern __shared__ __align__(1024) unsigned char sm_tc[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(sm_tc) + 1023) & ~static_cast<uintptr_t>(1023));
-    float* Cs = reinterpret_cast<float*>(ring + (size_t)kStages * kStageBytes);   // BM x BN, ld BM
-    Ctrl* ctl = reinterpret_cast<Ctrl*>(ring + (size_t)kStages * kStageBytes + kCBytes);
+    Ctrl* ctl = reinterpret_cast<Ctrl*>(ring + (size_t)kStages * kStageBytes);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort = &ctl->abort;
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) {
-            tc::mbar_init(&ctl->full[st], kProdWarps);
+            tc::mbar_init(&ctl->full[st], 1);
             tc::mbar_init(&ctl->empty[st], 1);
         }
         for (int q = 0; q < 2; ++q) {
@@ -989,50 +1066,52 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
     tc::fence_after();
     const uint32_t tmem = ctl->tmem;
 
-    if (warp < kProdWarps) {
-        // ---------------- producers
-        Walk w{trec, crec, ntgt, counter, a.blk, a.WU, ctl, tid, budget};
-        float ra[kPrefetch][8], rb[kPrefetch][8];
-        int hf[kPrefetch], hn[kPrefetch];
-        bool have[kPrefetch];
-#pragma unroll
-        for (int j = 0; j < kPrefetch; ++j) have[j] = false;
-        // slot j holds slice s + j of the ring order: it is stored, then refilled with
-        // the slice kPrefetch further on
-        bool more = true;
-        int s = 0;
-        do {
-#pragma unroll
-            for (int j = 0; j < kPrefetch; ++j) {
-                if (have[j]) put_stage(ctl, ring, s++, tid, hf[j], hn[j], ra[j], rb[j], budget);
-                have[j] = false;
-                if (more) {
-                    SliceMeta m;
-                    more = w.next(m);
-                    if (more) {
-                        load_slice(m, tid, ra[j], rb[j]);
-                        hf[j] = m.flags;
-                        hn[j] = m.n;
-                        have[j] = true;
-                    }
+    if (warp == kProdWarp) {
+        // ---------------- producer (one thread): bulk copies of packed slices
+        if (lane == 0) {
+            Walk w{trec, crec, ntgt, a.blk, pA, pB, ctl, budget};
+            w.init();
+            int s = 0;
+            bool copied = false;
+            const unsigned char* sa;
+            const unsigned char* sb;
+            int flags;
+            while (w.next(sa, sb, flags)) {
+                if (*abort) continue;                                // drain: walk, copy nothing
+                const int st = s % kStages, use = s / kStages;
+                if (use >= 1 && !wait_phase(&ctl->empty[st], (use - 1) & 1, abort, budget)) continue;
+                unsigned char* d = ring + (size_t)st * kStageBytes;
+                ctl->hdr[st] = StageHdr{flags, w.nmma};
+                mbar_arrive_tx(&ctl->full[st], 2 * (w.abytes + w.bbytes));
+                bulk_g2s(d, sa, w.abytes, &ctl->full[st]);
+                bulk_g2s(d + kPart, sa + (int64_t)w.tg.ga * kGroup, w.abytes, &ctl->full[st]);
+                bulk_g2s(d + 2 * kPart, sb, w.bbytes, &ctl->full[st]);
+                bulk_g2s(d + 3 * kPart, sb + (int64_t)w.tg.gb * kGroup, w.bbytes, &ctl->full[st]);
+                copied = true;
+                ++s;
+            }
+            // end markers: a stage for the MMA thread, a tile record for the epilogue
+            if (!*abort) {
+                const int st = s % kStages, use = s / kStages;
+                if (use < 1 || wait_phase(&ctl->empty[st], (use - 1) & 1, abort, budget)) {
+                    ctl->hdr[st] = StageHdr{F_END, 0};
+                    mbar_arrive(&ctl->full[st]);
                 }
             }
-        } while (more || have[0] || have[1] || have[2]);
-        static_assert(kPrefetch == 3, "the loop condition names every slot");
-        // end markers: a stage for the MMA thread, a tile record for the epilogue
-        if (!*abort) {
-            const int st = s % kStages, use = s / kStages;
-            if (use >= 1 && lane == 0) wait_phase(&ctl->empty[st], (use - 1) & 1, abort, budget);
-            __syncwarp();
-            if (tid == 0) ctl->hdr[st] = StageHdr{F_END, 0};
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->full[st]);
-        }
-        if (tid == 0) {
             TileRec r{};
             r.end = 1;
             w.publish(r);
+            // the copies issued have landed before the CTA may exit (full budget): the
+            // last stage filled completes once all of them have
+            if (copied && *abort) {
+                for (int q = 0; q < kStages; ++q) {
+                    const int sq = s - 1 - q;
+                    if (sq < 0) break;
+                    tc::mbar_wait(&ctl->full[sq % kStages], (sq / kStages) & 1, kWaitCycles);
+                }
+            }
         }
+        __syncwarp();
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
@@ -1078,10 +1157,9 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: C -= accumulator
+        // ---------------- epilogue: C -= accumulator, as reductions in L2
         const int q = warp & 3;                                      // tensor-memory lane quadrant
         const int row = 32 * q + lane;
-        float* Cr = Cs + row;                                        // this thread's row, stride BM
         int tile = 0;
         for (;;) {
             const int slot = tile % kTrec;
@@ -1090,15 +1168,11 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->tempty[slot]);
             if (r.end) break;
-            const bool rok = row < r.mv;
-            float* Crow = r.C + row;
-            if (rok)
-                for (int col = 0; col < r.nv; ++col) cp_async4(Cr + col * BM, Crow + (int64_t)col * r.ldc);
-            cp_async_commit();
             const int acc = tile & 1;
             if (!wait_phase(&ctl->accfull[acc], (tile >> 1) & 1, abort, budget)) break;
             tc::fence_after();
-            cp_async_wait_all();
+            const bool rok = row < r.mv;
+            float* Crow = r.C + row;
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * kAccCols;
             const int ncc = (r.nv + 15) / 16;                        // warp-uniform
             for (int cc = 0; cc < ncc; ++cc) {
@@ -1108,7 +1182,7 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int col = 16 * cc + j;
-                        if (col < r.nv) Crow[(int64_t)col * r.ldc] = Cr[col * BM] - v[j];
+                        if (col < r.nv) red_add(Crow + (int64_t)col * r.ldc, -v[j]);
                     }
                 }
             }
@@ -1117,7 +1191,6 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
             if (lane == 0) mbar_arrive(&ctl->accempty[acc]);
             ++tile;
         }
-        cp_async_wait_all();                                         // none left in flight
     }
     // every role is done (or has given up): free tensor memory
     tc::fence_before();

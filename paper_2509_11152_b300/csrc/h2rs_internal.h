@@ -157,6 +157,7 @@ struct LevelStruct {
     std::vector<int> sch_ci;                  // contributor box i
     std::vector<int> sch_cA;                  // block (j, i)  (A operand)
     std::vector<int> sch_ckpos;               // position of k in N(i)
+    std::vector<int> sch_cjpos;               // position of j in N(i)
     // per near-field position (nb_ptr order): block ids of (i, j) and (j, i)
     std::vector<int> nb_blk, nb_blkT;
     // per-colour work lists (boxes in cboxes order): fill segments of the basis
@@ -165,6 +166,9 @@ struct LevelStruct {
     std::vector<int> seg_blk, seg_j, seg_slot, seg_ptr, seg_cptr;
     std::vector<int> pj_box, pj_blk, pj_blkT, pj_cptr;
     std::vector<int> zf_box, zf_blk, zf_col, zf_cptr, zn_box, zn_blk, zn_col, zn_cptr;
+    // operand packing of the tensor-core Schur update: every near-field position p of
+    // every box i of the colour (box, position), per colour
+    std::vector<int> pk_box, pk_pos, pk_cptr;
     // forward-solve L updates, per colour: target boxes j and contributors i
     std::vector<int> fl_cptr;                 // ncolour+1 -> ranges of targets
     std::vector<int> fl_tbox;                 // target box j
@@ -183,10 +187,10 @@ struct LevelStruct {
     struct Dev {
         DevBuf colour, brow, bcol, top_boxes, skel_boxes, nb_ptr, nb_col, nb_blk, nb_blkT, diag_blk;
         DevBuf fl_tbox, fl_tptr, fl_ci, fl_cpos, near_entry;
-        DevBuf sch_tblk, sch_tptr, sch_ci, sch_cA, sch_ckpos, cl_dblk, cl_fblk, cl_adm;
+        DevBuf sch_tblk, sch_tptr, sch_ci, sch_cA, sch_ckpos, sch_cjpos, cl_dblk, cl_fblk, cl_adm;
         DevBuf cboxes;                        // boxes of every colour, in colour order
         DevBuf seg_blk, seg_j, seg_slot, seg_ptr, pj_box, pj_blk, pj_blkT;
-        DevBuf zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col;
+        DevBuf zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col, pk_box, pk_pos;
     } dev;
     std::vector<int> cbox_ptr;                // ncolour+1 offsets into dev.cboxes
 };

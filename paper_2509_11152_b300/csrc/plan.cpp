@@ -207,10 +207,10 @@ static void atomic_min(int* p, int v) {
 // contributions are generated box by box (boxes ascending) and bucketed by target.
 static void schur_lists(LevelStruct& L) {
     struct Part {
-        std::vector<int> tblk, tlen, ci, cA, ckpos;
+        std::vector<int> tblk, tlen, ci, cA, ckpos, cjpos;
     };
     struct Scratch {
-        std::vector<int> cnt, pos, rt, ri, ra, rk;
+        std::vector<int> cnt, pos, rt, ri, ra, rk, rj;
     };
     std::vector<Part> parts(L.ncolour);
     const int nb = L.nblocks();
@@ -219,7 +219,7 @@ static void schur_lists(LevelStruct& L) {
             s.cnt.assign(nb, 0);
             s.pos.resize(nb);
         }
-        s.rt.clear(); s.ri.clear(); s.ra.clear(); s.rk.clear();
+        s.rt.clear(); s.ri.clear(); s.ra.clear(); s.rk.clear(); s.rj.clear();
         for (int i : L.cboxes[c]) {
             const int n0 = L.nb_ptr[i], n1 = L.nb_ptr[i + 1];
             for (int a = n0; a < n1; ++a) {
@@ -238,6 +238,7 @@ static void schur_lists(LevelStruct& L) {
                     s.ri.push_back(i);
                     s.ra.push_back(ablk);
                     s.rk.push_back(b - n0);
+                    s.rj.push_back(a - n0);
                 }
             }
         }
@@ -254,11 +255,13 @@ static void schur_lists(LevelStruct& L) {
         P.ci.resize(run);
         P.cA.resize(run);
         P.ckpos.resize(run);
+        P.cjpos.resize(run);
         for (size_t r = 0; r < s.rt.size(); ++r) {
             const int q = s.pos[s.rt[r]]++;
             P.ci[q] = s.ri[r];
             P.cA[q] = s.ra[r];
             P.ckpos[q] = s.rk[r];
+            P.cjpos[q] = s.rj[r];
         }
     });
     // concatenation in colour order: sizes first, then every colour copied in parallel
@@ -275,6 +278,7 @@ static void schur_lists(LevelStruct& L) {
     L.sch_ci.resize(coff[nc]);
     L.sch_cA.resize(coff[nc]);
     L.sch_ckpos.resize(coff[nc]);
+    L.sch_cjpos.resize(coff[nc]);
     parallel_items<int>(nc, [&](int64_t c, int&) {
         const Part& P = parts[c];
         const int t0 = L.sch_cptr[c];
@@ -287,6 +291,7 @@ static void schur_lists(LevelStruct& L) {
         std::copy(P.ci.begin(), P.ci.end(), L.sch_ci.begin() + coff[c]);
         std::copy(P.cA.begin(), P.cA.end(), L.sch_cA.begin() + coff[c]);
         std::copy(P.ckpos.begin(), P.ckpos.end(), L.sch_ckpos.begin() + coff[c]);
+        std::copy(P.cjpos.begin(), P.cjpos.end(), L.sch_cjpos.begin() + coff[c]);
     });
     // a fill block is first touched by the first (lowest) colour that updates it;
     // blocks carried from the level below keep -1
@@ -355,6 +360,7 @@ static void work_lists(LevelStruct& L) {
         std::vector<int> seg_blk, seg_j, seg_slot, seg_end;      // seg_end: local end per box
         std::vector<int> pj_box, pj_blk, pj_blkT;
         std::vector<int> zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col;
+        std::vector<int> pk_box, pk_pos;
     };
     std::vector<Part> parts(L.ncolour);
     parallel_items<int>(L.ncolour, [&](int64_t c64, int&) {
@@ -369,6 +375,10 @@ static void work_lists(LevelStruct& L) {
                 P.seg_slot.push_back(slot);
             }
             P.seg_end.push_back((int)P.seg_blk.size());
+            for (int a = L.nb_ptr[i]; a < L.nb_ptr[i + 1]; ++a) {
+                P.pk_box.push_back(i);
+                P.pk_pos.push_back(a);
+            }
             for (int b = L.bptr[i]; b < L.bptr[i + 1]; ++b) {
                 const bool live = L.bkind[b] == 0 || L.first_touch[b] < c;
                 if (!live) continue;
@@ -394,6 +404,8 @@ static void work_lists(LevelStruct& L) {
     L.zn_box.clear(); L.zn_blk.clear(); L.zn_col.clear();
     L.zf_cptr.assign(1, 0);
     L.zn_cptr.assign(1, 0);
+    L.pk_box.clear(); L.pk_pos.clear();
+    L.pk_cptr.assign(1, 0);
     auto append = [](std::vector<int>& dst, const std::vector<int>& src) { dst.insert(dst.end(), src.begin(), src.end()); };
     for (const Part& P : parts) {
         const int base = (int)L.seg_blk.size();
@@ -402,6 +414,8 @@ static void work_lists(LevelStruct& L) {
         append(L.pj_box, P.pj_box); append(L.pj_blk, P.pj_blk); append(L.pj_blkT, P.pj_blkT);
         append(L.zf_box, P.zf_box); append(L.zf_blk, P.zf_blk); append(L.zf_col, P.zf_col);
         append(L.zn_box, P.zn_box); append(L.zn_blk, P.zn_blk); append(L.zn_col, P.zn_col);
+        append(L.pk_box, P.pk_box); append(L.pk_pos, P.pk_pos);
+        L.pk_cptr.push_back((int)L.pk_box.size());
         L.seg_cptr.push_back((int)L.seg_blk.size());
         L.pj_cptr.push_back((int)L.pj_box.size());
         L.zf_cptr.push_back((int)L.zf_box.size());
@@ -576,6 +590,7 @@ static void upload_level(LevelStruct& L, cudaStream_t s) {
     upload(d.sch_ci, L.sch_ci, s);
     upload(d.sch_cA, L.sch_cA, s);
     upload(d.sch_ckpos, L.sch_ckpos, s);
+    upload(d.sch_cjpos, L.sch_cjpos, s);
     upload(d.cl_dblk, L.cl_dblk, s);
     upload(d.cl_fblk, L.cl_fblk, s);
     upload(d.cl_adm, L.cl_adm, s);
@@ -593,6 +608,8 @@ static void upload_level(LevelStruct& L, cudaStream_t s) {
     upload(d.zn_box, L.zn_box, s);
     upload(d.zn_blk, L.zn_blk, s);
     upload(d.zn_col, L.zn_col, s);
+    upload(d.pk_box, L.pk_box, s);
+    upload(d.pk_pos, L.pk_pos, s);
 }
 
 void upload_plan(Plan& P, cudaStream_t s) {
