@@ -469,8 +469,10 @@ void FactorImpl<T>::run_level(size_t a) {
     for (auto v : W.scratch_need) scratch_max = std::max(scratch_max, v);
     DevBuf scratch;
     track(this, scratch, scratch_max * sizeof(T), s);
-    DevBuf d_ybase, d_ylead, d_wbase, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn;
+    DevBuf d_ybase, d_ylead, d_wbase, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn, d_ynorm2;
     DevBuf d_tile_tgt, d_tile_mn;
+    d_ynorm2.alloc(std::max(1, nbox_all) * sizeof(double), s);
+    H2_CUDA_CHECK(cudaMemsetAsync(d_ynorm2.ptr, 0, std::max(1, nbox_all) * sizeof(double), s));
     upload(d_ybase, W.ybase, s);
     upload(d_ylead, W.ylead, s);
     upload(d_wbase, W.wbase, s);
@@ -519,6 +521,7 @@ void FactorImpl<T>::run_level(size_t a) {
         CL.ybase = d_ybase.as<int64_t>() + b0;
         CL.ylead = d_ylead.as<int64_t>() + b0;
         CL.wbase = d_wbase.as<int64_t>() + b0;
+        CL.ynorm2 = d_ynorm2.as<double>() + b0;
         const int s0 = S.seg_cptr[c], ns = S.seg_cptr[c + 1] - s0;
         // ---- augmentation
         if (ns > 0) {

@@ -87,6 +87,7 @@ struct ColourLists {
     const int64_t* ybase;      // scratch offset of the box's Y^T
     const int64_t* ylead;      // leading dimension (total rows) of the box's Y^T
     const int64_t* wbase;      // scratch offset of the box's n x n work matrix
+    double* ynorm2;            // ||Y||_F^2 of the box's fill rows (zero before the gather)
 };
 
 }  // namespace h2rs

@@ -120,6 +120,7 @@ __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* 
     }
     const T* V = VS ? Vs : Vg;
     const int lv = VS ? lf : n;
+    double y2 = 0;                                   // this thread's part of ||Y||_F^2
     for (int c0 = skip; c0 < nj; c0 += PC) {
         const int pc = min(PC, nj - c0);
         for (int x = tid; x < n * pc; x += bs) {
@@ -142,17 +143,24 @@ __global__ void k_aug_gather(LevelArgs<T> a, ColourLists L, int cur, const int* 
             const T* pcol = Ps + c * lq;
             for (int q = 0; q < k; ++q) acc -= V[r + (int64_t)q * lv] * pcol[q];
             Yt[(c0 + c) + (int64_t)r * ld] = acc;
+            y2 += (double)acc * (double)acc;
         }
         __syncthreads();
     }
+    __shared__ double red[33];
+    const double tot = block_sum(y2, red);
+    if (tid == 0) atomicAdd(&L.ynorm2[slot], tot);
 }
 
 // R-factor of the live rows of Y^T (stored back to back, `live` rows) accumulated in W
-// (row-major n x n, row stride ldw), streamed in chunks of CH rows.  Each thread keeps
-// RPT rows of one column of the chunk in registers (TPC = CH / RPT threads per
-// column); per Householder step only the reflector column and its partial norms go
-// through shared memory (double buffered, one barrier per step).  Requires
-// n * TPC <= blockDim.x.
+// (row-major n x n, row stride ldw), streamed in chunks of 64 rows (Householder QR of
+// [R; chunk] per chunk).  256 threads: 32 column groups of CPT consecutive columns x 8
+// row groups; thread (g, h) keeps rows h + 8q (q < 8) of its CPT columns in registers,
+// so one broadcast reflector value serves CPT columns, and the 8 row groups of a
+// column group are 8 consecutive lanes (partial dot products reduced by shuffles).
+// Per column the owning lanes publish the reflector and its scalars (computed once)
+// through shared memory (double buffered, one barrier per column).  Requires
+// n <= 32 * CPT and blockDim.x == 256.
 // elements of the chunk buffer of k_basis (also holds rfactor_stream's broadcasts)
 __host__ __device__ inline int basis_chunk_elems(int n) {
     const int ch = n <= 192 ? 64 : 32;
@@ -160,62 +168,80 @@ __host__ __device__ inline int basis_chunk_elems(int n) {
     return e > 288 ? e : 288;
 }
 
-template <class T, int RPT, int CH>
+template <class T, int CPT>
 __device__ void rfactor_stream(int n, int64_t live, const T* __restrict__ Yt, int64_t ld, T* W, int ldw, T* vb) {
-    constexpr int TPC = CH / RPT;
+    constexpr int CH = 64, RG = 8, RPT = CH / RG;
     const int tid = threadIdx.x;
-    const int part = tid % TPC, col = tid / TPC;
-    const bool own = col < n;
-    // vb layout: 2 buffers of [CH reflector values | TPC partial norms | x0]
-    const int bufsz = CH + TPC + 1;
-    T x[RPT];
+    const int h = tid & (RG - 1);                    // row group: rows h + RG q
+    const int g = tid >> 3;                          // column group: columns CPT g + cc
+    // vb: 2 buffers of [CH reflector values | tw | inv]
+    constexpr int bufsz = CH + 2;
+    T x[RPT][CPT];
     for (int64_t r0 = 0; r0 < live; r0 += CH) {
         const int rows = (int)min((int64_t)CH, live - r0);
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-            const int rr = part * RPT + q;
-            x[q] = (own && rr < rows) ? Yt[(r0 + rr) + (int64_t)col * ld] : T(0);
-        }
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc) {
+                const int rr = h + RG * q, col = CPT * g + cc;
+                x[q][cc] = (rr < rows && col < n) ? Yt[(r0 + rr) + (int64_t)col * ld] : T(0);
+            }
         for (int jj = 0; jj < n; ++jj) {
             T* buf = vb + (jj & 1) * bufsz;
-            if (col == jj) {
+            if (g == jj / CPT) {                         // the 8 lanes owning column jj
+                const int c0 = jj % CPT;
                 T p2 = 0;
 #pragma unroll
                 for (int q = 0; q < RPT; ++q) {
-                    buf[part * RPT + q] = x[q];
-                    p2 += x[q] * x[q];
+                    T v = x[q][0];
+#pragma unroll
+                    for (int cc = 1; cc < CPT; ++cc)
+                        if (cc == c0) v = x[q][cc];
+                    buf[h + RG * q] = v;
+                    p2 += v * v;
                 }
-                buf[CH + part] = p2;
-                if (part == 0) buf[CH + TPC] = W[(int64_t)jj * ldw + jj];
+                // only these 8 lanes of the warp take part: the mask names exactly them
+                const unsigned grp = 0xffu << (8 * ((threadIdx.x & 31) >> 3));
+#pragma unroll
+                for (int o = 1; o < RG; o <<= 1) p2 += __shfl_xor_sync(grp, p2, o);
+                if (h == 0) {
+                    T tw = 0, inv = 0;
+                    if (p2 != T(0)) {
+                        const T x0 = W[(int64_t)jj * ldw + jj];
+                        const T nrm = sqrt(x0 * x0 + p2);
+                        const T beta = x0 > T(0) ? -nrm : nrm;
+                        const T v0 = x0 - beta;
+                        tw = -v0 / beta;
+                        inv = T(1) / v0;
+                        W[(int64_t)jj * ldw + jj] = beta;
+                    }
+                    buf[CH] = tw;
+                    buf[CH + 1] = inv;
+                }
             }
             __syncthreads();
-            T ss = 0;
+            const T tw = buf[CH];
+            if (tw == T(0)) continue;                    // uniform; buffers alternate
+            const T inv = buf[CH + 1];
+            T vr[RPT];
 #pragma unroll
-            for (int p = 0; p < TPC; ++p) ss += buf[CH + p];
-            if (ss == T(0)) continue;                         // uniform; buffers alternate
-            const T x0 = buf[CH + TPC];
-            const T nrm = sqrt(x0 * x0 + ss);
-            const T beta = x0 > T(0) ? -nrm : nrm;
-            const T v0 = x0 - beta;
-            const T tw = -v0 / beta;
-            const T inv = T(1) / v0;
-            const bool act = own && col > jj;
-            T d = 0;
-            if (act) {
+            for (int q = 0; q < RPT; ++q) vr[q] = buf[h + RG * q];
 #pragma unroll
-                for (int q = 0; q < RPT; ++q) d += buf[part * RPT + q] * x[q];
-            }
+            for (int cc = 0; cc < CPT; ++cc) {
+                const int col = CPT * g + cc;
+                T d = 0;
 #pragma unroll
-            for (int o = 1; o < TPC; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (act) {
-                const T w = W[(int64_t)jj * ldw + col] + d * inv;
-                const T tww = tw * w;
-                const T f = tww * inv;
+                for (int q = 0; q < RPT; ++q) d += vr[q] * x[q][cc];
 #pragma unroll
-                for (int q = 0; q < RPT; ++q) x[q] -= f * buf[part * RPT + q];
-                if (part == 0) W[(int64_t)jj * ldw + col] -= tww;
-            } else if (col == jj && part == 0) {
-                W[(int64_t)jj * ldw + jj] = beta;
+                for (int o = 1; o < RG; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (col > jj && col < n) {
+                    const T w = W[(int64_t)jj * ldw + col] + d * inv;
+                    const T tww = tw * w;
+                    const T f = tww * inv;
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) x[q][cc] -= f * vr[q];
+                    if (h == 0) W[(int64_t)jj * ldw + col] -= tww;
+                }
             }
         }
         __syncthreads();
@@ -261,14 +287,20 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
         live += nj - ((a.colour[j] < cur) ? (nj - a.kt[j]) : 0);
     }
     int keep = 0;
-    if (live > 0 && k < n) {
+    // sigma_max(Y) <= ||Y||_F: when the Frobenius norm (accumulated in float64 by the
+    // gather) is below eps_fill, no singular value exceeds it and the truncated SVD
+    // keeps nothing, so the R-factor and the SVD are skipped (the margin covers the
+    // rounding of the norm itself)
+    const double yn2 = L.ynorm2[slot];
+    const bool below = yn2 <= (double)eps_fill * (double)eps_fill * (1.0 - 4e-6);
+    if (live > 0 && k < n && !below) {
         // ---------------- R-factor of Y^T (R row-major in W, row stride ldw)
         for (int x = tid; x < n * ldw; x += blockDim.x) W[x] = T(0);
         __syncthreads();
-        if (n <= 32) rfactor_stream<T, 16, 128>(n, live, Yt, ld, W, ldw, C);
-        else if (n <= 64) rfactor_stream<T, 32, 128>(n, live, Yt, ld, W, ldw, C);
-        else if (!BIG || n <= 128) rfactor_stream<T, 32, 64>(n, live, Yt, ld, W, ldw, C);
-        else rfactor_stream<T, BIG ? 64 : 32, 64>(n, live, Yt, ld, W, ldw, C);   // n <= 256
+        if (n <= 32) rfactor_stream<T, 1>(n, live, Yt, ld, W, ldw, C);
+        else if (n <= 64) rfactor_stream<T, 2>(n, live, Yt, ld, W, ldw, C);
+        else if (!BIG || n <= 128) rfactor_stream<T, 4>(n, live, Yt, ld, W, ldw, C);
+        else rfactor_stream<T, BIG ? 8 : 4>(n, live, Yt, ld, W, ldw, C);   // n <= 256
         __syncthreads();
         // ---------------- one-sided Jacobi on M = R^T (column p of M = row p of R)
         // Round-robin pairs over the active columns, tpp threads per pair (rows
@@ -1161,15 +1193,17 @@ k_schur_tc(LevelArgs<float> a, const SchurTgt* __restrict__ trec, const SchurCon
         const int q = warp & 3;                                      // tensor-memory lane quadrant
         const int row = 32 * q + lane;
         int tile = 0;
+        // every lane waits, and the warp leaves together if any lane gave up (the
+        // warp-wide tcgen05.ld and __syncwarp below need all 32 lanes)
         for (;;) {
             const int slot = tile % kTrec;
-            if (!wait_phase(&ctl->tfull[slot], (tile / kTrec) & 1, abort, budget)) break;
+            if (!__all_sync(0xffffffffu, wait_phase(&ctl->tfull[slot], (tile / kTrec) & 1, abort, budget))) break;
             const TileRec r = ctl->trec[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->tempty[slot]);
             if (r.end) break;
             const int acc = tile & 1;
-            if (!wait_phase(&ctl->accfull[acc], (tile >> 1) & 1, abort, budget)) break;
+            if (!__all_sync(0xffffffffu, wait_phase(&ctl->accfull[acc], (tile >> 1) & 1, abort, budget))) break;
             tc::fence_after();
             const bool rok = row < r.mv;
             float* Crow = r.C + row;
