@@ -4,6 +4,8 @@
 // which fix the sizes (and prefix-sum offsets) of the parent level.
 #include <algorithm>
 #include <chrono>
+#include <functional>
+#include <future>
 #include <numeric>
 #include <string>
 
@@ -89,6 +91,31 @@ static void launch_proj(int rpt, int nwork, int npan, int smem, cudaStream_t s, 
     else if (rpt <= 4) k_proj<T, 4, RIGHT><<<g, 256, smem, s>>>(ar, c, box, blk);
     else if (rpt <= 8) k_proj<T, 8, RIGHT><<<g, 256, smem, s>>>(ar, c, box, blk);
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the projection kernel"};
+}
+
+static int num_sms() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        H2_CUDA_CHECK(cudaGetDevice(&dev));
+        H2_CUDA_CHECK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        return v;
+    }();
+    return n;
+}
+
+// tensor-core projection (float32 factors only): one CTA per box of the colour
+static void launch_proj_tc(bool, int, cudaStream_t, const LevelArgs<double>&, int, const int*, const int*,
+                           const int*, long long) {}
+static void launch_proj_tc(bool right, int nbx, cudaStream_t s, const LevelArgs<float>& ar, int c,
+                           const int* boxes, const int* pj_ptr, const int* blks, long long budget) {
+    static const bool ready = [] {
+        H2_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pj::kSmem));
+        H2_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pj::kSmem));
+        return true;
+    }();
+    (void)ready;
+    if (right) k_proj_tc<true><<<nbx, pj::kThreads, pj::kSmem, s>>>(ar, c, boxes, pj_ptr, blks, budget);
+    else k_proj_tc<false><<<nbx, pj::kThreads, pj::kSmem, s>>>(ar, c, boxes, pj_ptr, blks, budget);
 }
 
 // Schur tiles of the FMA kernel: 64 x 64 (the tensor-core kernel walks each target's
@@ -358,6 +385,64 @@ struct ColourWork {
     std::vector<int> tile_tgt, tile_mn, tile_cptr;         // FMA Schur tiles
 };
 
+// Algorithmic flops and bytes of one level's phases (the roofline definitions of the
+// kernels' work units), from the plan and the level's sizes and ranks.
+LevelCounts level_counts(const LevelStruct& S, const LevelRT& L, double w) {
+    LevelCounts R{};
+    auto account = [&](int ph, double f, double b) { R.flops[ph] += f; R.bytes[ph] += b; };
+    const int nc = S.ncolour;
+    for (int c = 0; c < nc; ++c) {
+        for (int i : S.cboxes[c]) {
+            const double n = L.n[i], kt = L.kt[i], r = n - kt;
+            double live = 0;
+            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b)
+                if (S.bkind[b] == 1 && S.first_touch[b] < c) {
+                    const int j = S.bcol[b];
+                    live += (S.colour[j] < c) ? L.kt[j] : L.n[j];
+                }
+            account(PH_AUG, 4.0 * n * L.k[i] * live + 2.0 * live * n * n + 4.0 * n * n * kt,
+                    w * (live * n + n * n));
+            double nsum = 0, pbytes = 0;
+            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
+                const bool lv_ = S.bkind[b] == 0 || S.first_touch[b] < c;
+                if (!lv_) continue;
+                const int jb = S.bcol[b];
+                const double nj = S.colour[jb] < c ? L.kt[jb] : L.n[jb];   // rectangular fill
+                pbytes += 4.0 * n * nj * w;
+                account(PH_PROJ, 4.0 * n * n * nj, 0);
+            }
+            account(PH_PROJ, 0, pbytes + n * n * w);
+            for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
+                if (S.nb_col[p] != i) nsum += L.n[S.nb_col[p]];
+            const double ncol = nsum + kt;
+            account(PH_LU, 2.0 / 3.0 * r * r * r + 4.0 * r * r * ncol, w * (4.0 * r * ncol + r * r));
+        }
+        // Schur: targets read and written once; each contributor's operands D_{j,i_R}
+        // and W_U^i read once per colour (rows / columns of boxes eliminated before or
+        // in this colour: skeleton part only, rectangular fill)
+        auto live_lines = [&](int j) -> double { return S.colour[j] <= c ? L.kt[j] : L.n[j]; };
+        for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
+            const int tb = S.sch_tblk[t];
+            const double m = live_lines(L.brow[tb]), nn = live_lines(S.bcol[tb]);
+            double fl = 0, reread = 0;
+            for (int e = S.sch_tptr[t]; e < S.sch_tptr[t + 1]; ++e) {
+                const double r = L.n[S.sch_ci[e]] - L.kt[S.sch_ci[e]];
+                fl += 2.0 * m * nn * r;
+                reread += w * r * (m + nn);
+            }
+            account(PH_SCHUR, fl, 2.0 * m * nn * w);
+            R.schur_reread += reread;
+        }
+        for (int i : S.cboxes[c]) {
+            const double r = L.n[i] - L.kt[i];
+            double lines = 0;
+            for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p) lines += live_lines(S.nb_col[p]);
+            account(PH_SCHUR, 0, 2.0 * w * r * lines);
+        }
+    }
+    return R;
+}
+
 template <class T>
 void FactorImpl<T>::run_level(size_t a) {
     LevelRT& L = lv[a];
@@ -554,20 +639,24 @@ void FactorImpl<T>::run_level(size_t a) {
         const int smp = 2 * PW * ((W.nmax[c] + 31) / 32 * 32 + 1) * (int)sizeof(T);
         const int rpt = (W.nmax[c] + 31) / 32;
         const int npan = (nmax_level + PW - 1) / PW;        // panels of the other dimension
-        if (npj) {
+        // tensor cores for the float32 factor with split-TF32 products on colours with at
+        // least one box per SM whose boxes all have 65..128 points (one CTA per box: it
+        // pays where every SM has a box of full-width tiles), the FMA pipes otherwise
+        const bool proj_tc = tensor_schur && W.nmax[c] <= pj::BM && W.nmax[c] > pj::BM / 2 && nbx >= num_sms();
+        for (int side = 0; side < 2 && npj; ++side) {
             kbegin(H2_K_PROJ);
-            launch_proj<T, false>(rpt, npj, npan, smp, s, ar, c, S.dev.pj_box.as<int>() + pj0,
-                                  S.dev.pj_blk.as<int>() + pj0);
+            if (proj_tc)
+                launch_proj_tc(side == 1, nbx, s, ar, c, S.dev.cboxes.as<int>() + b0, S.dev.pj_ptr.as<int>() + b0,
+                               side == 0 ? S.dev.pj_blk.as<int>() : S.dev.pj_blkT.as<int>(), wait_budget);
+            else if (side == 0)
+                launch_proj<T, false>(rpt, npj, npan, smp, s, ar, c, S.dev.pj_box.as<int>() + pj0,
+                                      S.dev.pj_blk.as<int>() + pj0);
+            else
+                launch_proj<T, true>(rpt, npj, npan, smp, s, ar, c, S.dev.pj_box.as<int>() + pj0,
+                                     S.dev.pj_blkT.as<int>() + pj0);
             kend();
+            H2_LAUNCHED();
         }
-        H2_LAUNCHED();
-        if (npj) {
-            kbegin(H2_K_PROJ);
-            launch_proj<T, true>(rpt, npj, npan, smp, s, ar, c, S.dev.pj_box.as<int>() + pj0,
-                                 S.dev.pj_blkT.as<int>() + pj0);
-            kend();
-        }
-        H2_LAUNCHED();
         const int zf0 = S.zf_cptr[c], nzf = S.zf_cptr[c + 1] - zf0;
         if (nzf) {
             kbegin(H2_K_ZERO);
@@ -654,57 +743,10 @@ void FactorImpl<T>::run_level(size_t a) {
         untrack(this, packA);
         untrack(this, packB);
     }
-    // ---------------- algorithmic counts of this level (for roofline fractions)
-    const double w = sizeof(T);
-    for (int c = 0; c < nc; ++c) {
-        for (int i : S.cboxes[c]) {
-            const double n = L.n[i], kt = L.kt[i], r = n - kt;
-            double live = 0;
-            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b)
-                if (S.bkind[b] == 1 && S.first_touch[b] < c) {
-                    const int j = S.bcol[b];
-                    live += (S.colour[j] < c) ? L.kt[j] : L.n[j];
-                }
-            account(PH_AUG, 4.0 * n * L.k[i] * live + 2.0 * live * n * n + 4.0 * n * n * kt,
-                    w * (live * n + n * n));
-            double nsum = 0, pbytes = 0;
-            for (int b = S.bptr[i]; b < S.bptr[i + 1]; ++b) {
-                const bool lv_ = S.bkind[b] == 0 || S.first_touch[b] < c;
-                if (!lv_) continue;
-                const int jb = S.bcol[b];
-                const double nj = S.colour[jb] < c ? L.kt[jb] : L.n[jb];   // rectangular fill
-                pbytes += 4.0 * n * nj * w;
-                account(PH_PROJ, 4.0 * n * n * nj, 0);
-            }
-            account(PH_PROJ, 0, pbytes + n * n * w);
-            for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p)
-                if (S.nb_col[p] != i) nsum += L.n[S.nb_col[p]];
-            const double ncol = nsum + kt;
-            account(PH_LU, 2.0 / 3.0 * r * r * r + 4.0 * r * r * ncol, w * (4.0 * r * ncol + r * r));
-        }
-        // Schur: targets read and written once; each contributor's operands D_{j,i_R}
-        // and W_U^i read once per colour (rows / columns of boxes eliminated before or
-        // in this colour: skeleton part only, rectangular fill)
-        auto live_lines = [&](int j) -> double { return S.colour[j] <= c ? L.kt[j] : L.n[j]; };
-        for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
-            const int tb = S.sch_tblk[t];
-            const double m = live_lines(L.brow[tb]), nn = live_lines(S.bcol[tb]);
-            double fl = 0, reread = 0;
-            for (int e = S.sch_tptr[t]; e < S.sch_tptr[t + 1]; ++e) {
-                const double r = L.n[S.sch_ci[e]] - L.kt[S.sch_ci[e]];
-                fl += 2.0 * m * nn * r;
-                reread += w * r * (m + nn);
-            }
-            account(PH_SCHUR, fl, 2.0 * m * nn * w);
-            stats.schur_reread_bytes += reread;
-        }
-        for (int i : S.cboxes[c]) {
-            const double r = L.n[i] - L.kt[i];
-            double lines = 0;
-            for (int p = S.nb_ptr[i]; p < S.nb_ptr[i + 1]; ++p) lines += live_lines(S.nb_col[p]);
-            account(PH_SCHUR, 0, 2.0 * w * r * lines);
-        }
-    }
+    // ---------------- algorithmic counts of this level (for roofline fractions): a host
+    // loop over every box and Schur target, run on a worker thread so that the GPU goes
+    // on with the next level meanwhile (summed at the end of the factorisation)
+    counts.push_back(std::async(std::launch::async, level_counts, std::cref(S), std::cref(L), (double)sizeof(T)));
 }
 
 // ------------------------------------------------------------------ level close
@@ -842,6 +884,7 @@ void FactorImpl<T>::factorize() {
     ev_phase.clear();
     for (int p = 0; p < 8; ++p) stats.phase_ms[p] = stats.phase_flops[p] = stats.phase_bytes[p] = 0;
     stats.schur_reread_bytes = 0;
+    counts.clear();
     stats.error_level = stats.error_box = -1;
     H2_CUDA_CHECK(cudaMemsetAsync(status.ptr, 0, sizeof(DevStatus), stream));
     lv.clear();
@@ -868,6 +911,12 @@ void FactorImpl<T>::factorize() {
     }
     top_factor();
     H2_CUDA_CHECK(cudaStreamSynchronize(stream));
+    for (auto& f : counts) {
+        const LevelCounts R = f.get();
+        for (int p = 0; p < 8; ++p) account(p, R.flops[p], R.bytes[p]);
+        stats.schur_reread_bytes += R.schur_reread;
+    }
+    counts.clear();
     float total = 0;
     for (size_t e = 1; e < ev.size(); ++e) {
         float ms = 0;

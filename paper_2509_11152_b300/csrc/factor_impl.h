@@ -2,6 +2,7 @@
 // factorisation (factor.cu) and of the solve / refinement (solve.cu).
 #pragma once
 
+#include <future>
 #include <memory>
 
 #include "factor_args.cuh"
@@ -32,6 +33,12 @@ struct LevelRT {
     // device: working data (freed after the level close)
     DevBuf blk, V;
 };
+
+// algorithmic flops / bytes of one level's phases (h2_factor_stats)
+struct LevelCounts {
+    double flops[8], bytes[8], schur_reread;
+};
+LevelCounts level_counts(const LevelStruct& S, const LevelRT& L, double w);
 
 struct FactorBase {
     virtual ~FactorBase() = default;
@@ -65,6 +72,7 @@ struct FactorImpl : FactorBase {
     // events for phase timing
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_phase;
+    std::vector<std::future<LevelCounts>> counts;   // per level, computed on worker threads
     // optional per-launch events (H2_FLAG_TIME_KERNELS)
     bool time_kernels = false;
     long long wait_budget = 4000000000LL;     // tensor-core Schur pipeline waits (SM cycles)

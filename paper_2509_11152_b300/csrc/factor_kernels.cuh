@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "factor_args.cuh"
+#include "proj_tc.cuh"
 #include "schur_ws.cuh"
 
 namespace h2rs {
@@ -589,6 +590,288 @@ k_proj(LevelArgs<T> a, int cur, const int* __restrict__ w_box, const int* __rest
             else B[(p0 + c) + (int64_t)aa * nj] = acc[u][v];
         }
     }
+}
+
+// ---- the same projection on the tensor cores (float32 factors, boxes <= 128; see
+// proj_tc.cuh).  blockIdx.x = box of the colour; its entries pj_ptr[q] .. pj_ptr[q+1]-1
+// of `blks` (row i's blocks on the left, their transposes on the right).
+template <bool RIGHT>
+__global__ void __launch_bounds__(pj::kThreads, 1)
+k_proj_tc(LevelArgs<float> a, int cur, const int* __restrict__ boxes, const int* __restrict__ pj_ptr,
+          const int* __restrict__ blks, long long budget) {
+    using namespace pj;
+    extern __shared__ __align__(1024) unsigned char sm_pj[];
+    unsigned char* As = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(sm_pj) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char* ring = As + kABytes;
+    Ctrl* ctl = reinterpret_cast<Ctrl*>(ring + (size_t)kStages * kStageBytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort = &ctl->abort;
+    const int q = blockIdx.x;
+    const int i = boxes[q];
+    const int ni = a.n[i];
+    const int ks = (ni + BK - 1) / BK;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            tc::mbar_init(&ctl->full[st], kProdWarps);
+            tc::mbar_init(&ctl->empty[st], 1);
+        }
+        for (int x = 0; x < 2; ++x) {
+            tc::mbar_init(&ctl->accfull[x], 1);
+            tc::mbar_init(&ctl->accempty[x], kEpiWarps);
+        }
+        for (int x = 0; x < kTrec; ++x) {
+            tc::mbar_init(&ctl->tfull[x], 1);
+            tc::mbar_init(&ctl->tempty[x], kEpiWarps);
+        }
+        tc::mbar_init(&ctl->aready, kProdWarps);
+        tc::mbar_init(&ctl->drain, 1);
+        *abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == kMmaWarp) {
+        tc::tmem_alloc(&ctl->tmem, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp < kProdWarps) {
+        // ---------------- producers
+        const int line = tid & 127, h = tid >> 7;
+        // Q~^T: A[m][k] = Q~[k][m], K-contiguous; zero beyond n_i
+        {
+            const float* Q = a.Q + a.Q_off[i];
+            for (int sl = 0; sl < ks; ++sl) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int k = BK * sl + 8 * h + e;
+                    v[e] = (line < ni && k < ni) ? Q[k + (int64_t)line * ni] : 0.f;
+                }
+                unsigned char* d = As + (size_t)sl * 2 * kPart;
+                store8(d, d + kPart, tid, v);
+            }
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->aready);
+        }
+        // walk: blocks of the box, 128-line tiles, K slices
+        const int e1 = pj_ptr[q + 1];
+        int e = pj_ptr[q];
+        bool active = false;
+        int tn = 0, ntn = 0, sl = 0, nv = 0, nmma = 16, tiles = 0, N = 0, lo = 0, nj = 0;
+        int64_t boff = 0;
+        auto publish = [&](const TileRec& r) {      // thread 0
+            const int slot = tiles % kTrec;
+            if (tiles >= kTrec && !*abort) wait_phase(&ctl->tempty[slot], ((tiles / kTrec) - 1) & 1, abort, budget);
+            ctl->trec[slot] = r;
+            mbar_arrive(&ctl->tfull[slot]);
+            ++tiles;
+        };
+        auto start_tile = [&]() {
+            const int n0 = tn * BN;
+            nv = min(BN, N - n0);
+            nmma = (nv + 15) / 16 * 16;
+            sl = 0;
+            if (tid == 0) {
+                TileRec r;
+                if (!RIGHT) { r.C = a.blk + boff + (int64_t)(lo + n0) * ni; r.ls = 1; r.cs = ni; }
+                else { r.C = a.blk + boff + lo + n0; r.ls = nj; r.cs = 1; }
+                r.mv = ni;
+                r.nv = nv;
+                r.end = 0;
+                r.pad = 0;
+                publish(r);
+            }
+        };
+        // next slice: base of its first line and k, strides, header; false when done
+        auto next = [&](const float*& base, int64_t& kst, int64_t& lst, int& vlines, int& hdr) -> bool {
+            for (;;) {
+                if (!active) {
+                    if (e >= e1) return false;
+                    const int b = blks[e++];
+                    const int jb = RIGHT ? a.brow[b] : a.bcol[b];
+                    nj = a.n[jb];
+                    // lines of a box eliminated in an earlier colour are zero except its
+                    // skeleton part (rectangular fill, Sec. 2.1)
+                    lo = a.colour[jb] < cur ? nj - a.kt[jb] : 0;
+                    N = nj - lo;
+                    if (N <= 0) continue;
+                    boff = a.blk_off[b];
+                    ntn = (N + BN - 1) / BN;
+                    tn = 0;
+                    start_tile();
+                    active = true;
+                }
+                if (sl < ks) {
+                    const int n0 = tn * BN;
+                    if (!RIGHT) { base = a.blk + boff + (int64_t)(lo + n0) * ni + BK * sl; kst = 1; lst = ni; }
+                    else { base = a.blk + boff + lo + n0 + (int64_t)(BK * sl) * nj; kst = nj; lst = 1; }
+                    vlines = nv;
+                    hdr = (sl == 0 ? F_FIRST : 0) | (sl == ks - 1 ? F_LAST : 0) | (nmma << 3) | (sl << 12);
+                    ++sl;
+                    return true;
+                }
+                if (++tn < ntn) start_tile();
+                else active = false;
+            }
+        };
+        auto load = [&](const float* base, int64_t kst, int64_t lst, int vlines, int kmax, float (&v)[8]) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int k = 8 * h + x;
+                v[x] = (line < vlines && k < kmax) ? base[(int64_t)k * kst + (int64_t)line * lst] : 0.f;
+            }
+        };
+        float rv[kPre][8];
+        int hd[kPre];
+        bool have[kPre];
+#pragma unroll
+        for (int j = 0; j < kPre; ++j) { hd[j] = 0; have[j] = false; }
+        bool more = true;
+        int s = 0;
+        auto put = [&](int hdr, const float (&v)[8]) {
+            const int st = s % kStages, use = s / kStages;
+            ++s;
+            if (*abort) return;
+            if (use >= 1 && lane == 0) wait_phase(&ctl->empty[st], (use - 1) & 1, abort, budget);
+            __syncwarp();
+            if (*abort) return;
+            unsigned char* d = ring + (size_t)st * kStageBytes;
+            store8(d, d + kPart, tid, v);
+            if (tid == 0) ctl->hdr[st] = hdr;
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->full[st]);
+        };
+        bool pending;
+        do {
+#pragma unroll
+            for (int j = 0; j < kPre; ++j) {
+                if (have[j]) put(hd[j], rv[j]);
+                have[j] = false;
+                if (more) {
+                    const float* base;
+                    int64_t kst, lst;
+                    int vlines;
+                    more = next(base, kst, lst, vlines, hd[j]);
+                    if (more) {
+                        const int kmax = ni - BK * ((hd[j] >> 12) & 7);
+                        load(base, kst, lst, vlines, kmax, rv[j]);
+                        have[j] = true;
+                    }
+                }
+            }
+            pending = false;
+#pragma unroll
+            for (int j = 0; j < kPre; ++j) pending |= have[j];
+        } while (more || pending);
+        // end markers: a stage for the MMA thread, a tile record for the epilogue
+        if (!*abort) {
+            const int st = s % kStages, use = s / kStages;
+            if (use >= 1 && lane == 0) wait_phase(&ctl->empty[st], (use - 1) & 1, abort, budget);
+            __syncwarp();
+            if (tid == 0) ctl->hdr[st] = F_END;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->full[st]);
+        }
+        if (tid == 0) {
+            TileRec r{};
+            r.end = 1;
+            publish(r);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue (one thread)
+        if (lane == 0) {
+            bool issued = false;
+            if (wait_phase(&ctl->aready, 0, abort, budget)) {
+                int s = 0, tile = 0;
+                for (;;) {
+                    const int st = s % kStages, use = s / kStages;
+                    if (!wait_phase(&ctl->full[st], use & 1, abort, budget)) break;
+                    const int hdr = ctl->hdr[st];
+                    if (hdr & F_END) break;
+                    const int acc = tile & 1, accuse = tile >> 1;
+                    if ((hdr & F_FIRST) && accuse >= 1 &&
+                        !wait_phase(&ctl->accempty[acc], (accuse - 1) & 1, abort, budget))
+                        break;
+                    tc::fence_after();
+                    const uint32_t ab = tc::smem_u32(As + (size_t)((hdr >> 12) & 7) * 2 * kPart);
+                    const uint32_t bb = tc::smem_u32(ring + (size_t)st * kStageBytes);
+                    const uint32_t d = tmem + (uint32_t)acc * kAccCols;
+                    const uint32_t idesc = tc::idesc_tf32(BM, (hdr >> 3) & 0x1ff);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint32_t o = kk * 2 * tc::kLBO;
+                        const uint64_t aH = tc::sdesc(ab + o, tc::kLBO, kSBO);
+                        const uint64_t aL = tc::sdesc(ab + kPart + o, tc::kLBO, kSBO);
+                        const uint64_t bH = tc::sdesc(bb + o, tc::kLBO, kSBO);
+                        const uint64_t bL = tc::sdesc(bb + kPart + o, tc::kLBO, kSBO);
+                        tc::mma_tf32(d, aL, bH, idesc, ((hdr & F_FIRST) && kk == 0) ? 0 : 1);
+                        tc::mma_tf32(d, aH, bL, idesc, 1);
+                        tc::mma_tf32(d, aH, bH, idesc, 1);
+                    }
+                    issued = true;
+                    tc::mma_commit(&ctl->empty[st]);
+                    if (hdr & F_LAST) {
+                        tc::mma_commit(&ctl->accfull[acc]);
+                        ++tile;
+                    }
+                    ++s;
+                }
+            }
+            if (issued) {
+                tc::mma_commit(&ctl->drain);
+                if (!tc::mbar_wait(&ctl->drain, 0, kWaitCycles)) *abort = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: the tile over the block
+        const int qd = warp & 3;
+        const int row = 32 * qd + lane;
+        int tile = 0;
+        for (;;) {
+            const int slot = tile % kTrec;
+            if (!__all_sync(0xffffffffu, wait_phase(&ctl->tfull[slot], (tile / kTrec) & 1, abort, budget))) break;
+            const TileRec r = ctl->trec[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->tempty[slot]);
+            if (r.end) break;
+            const int acc = tile & 1;
+            if (!__all_sync(0xffffffffu, wait_phase(&ctl->accfull[acc], (tile >> 1) & 1, abort, budget))) break;
+            tc::fence_after();
+            const bool rok = row < r.mv;
+            float* Crow = r.C + (int64_t)row * r.ls;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)acc * kAccCols;
+            const int ncc = (r.nv + 15) / 16;
+            for (int cc = 0; cc < ncc; ++cc) {
+                float v[16];
+                tc::tmem_ld16(taddr + 16 * cc, v);
+                if (rok) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = 16 * cc + j;
+                        if (col < r.nv) Crow[(int64_t)col * r.cs] = v[j];
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->accempty[acc]);
+            ++tile;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+    if (tid == 0 && *abort) dev_fail(a.status, H2_ERR_TIMEOUT, a.level, i);
 }
 
 // F truncation after projection (Sec. 2.1: fill is kept in the skeleton coordinates

@@ -165,6 +165,7 @@ struct LevelStruct {
     // live blocks to project (row block b and its transpose), blocks to zero
     std::vector<int> seg_blk, seg_j, seg_slot, seg_ptr, seg_cptr;
     std::vector<int> pj_box, pj_blk, pj_blkT, pj_cptr;
+    std::vector<int> pj_ptr;                  // per box (cboxes order): its first pj entry (+ end)
     std::vector<int> zf_box, zf_blk, zf_col, zf_cptr, zn_box, zn_blk, zn_col, zn_cptr;
     // operand packing of the tensor-core Schur update: every near-field position p of
     // every box i of the colour (box, position), per colour
@@ -189,7 +190,7 @@ struct LevelStruct {
         DevBuf fl_tbox, fl_tptr, fl_ci, fl_cpos, near_entry;
         DevBuf sch_tblk, sch_tptr, sch_ci, sch_cA, sch_ckpos, sch_cjpos, cl_dblk, cl_fblk, cl_adm;
         DevBuf cboxes;                        // boxes of every colour, in colour order
-        DevBuf seg_blk, seg_j, seg_slot, seg_ptr, pj_box, pj_blk, pj_blkT;
+        DevBuf seg_blk, seg_j, seg_slot, seg_ptr, pj_box, pj_blk, pj_blkT, pj_ptr;
         DevBuf zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col, pk_box, pk_pos;
     } dev;
     std::vector<int> cbox_ptr;                // ncolour+1 offsets into dev.cboxes

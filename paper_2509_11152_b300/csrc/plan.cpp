@@ -361,6 +361,7 @@ static void work_lists(LevelStruct& L) {
         std::vector<int> pj_box, pj_blk, pj_blkT;
         std::vector<int> zf_box, zf_blk, zf_col, zn_box, zn_blk, zn_col;
         std::vector<int> pk_box, pk_pos;
+        std::vector<int> pj_end;                                 // local end of each box's entries
     };
     std::vector<Part> parts(L.ncolour);
     parallel_items<int>(L.ncolour, [&](int64_t c64, int&) {
@@ -392,6 +393,7 @@ static void work_lists(LevelStruct& L) {
                 zb.push_back(i); zk.push_back(b); zc.push_back(0);
                 zb.push_back(i); zk.push_back(bt); zc.push_back(1);
             }
+            P.pj_end.push_back((int)P.pj_box.size());
             ++slot;
         }
     });
@@ -406,10 +408,13 @@ static void work_lists(LevelStruct& L) {
     L.zn_cptr.assign(1, 0);
     L.pk_box.clear(); L.pk_pos.clear();
     L.pk_cptr.assign(1, 0);
+    L.pj_ptr.assign(1, 0);
     auto append = [](std::vector<int>& dst, const std::vector<int>& src) { dst.insert(dst.end(), src.begin(), src.end()); };
     for (const Part& P : parts) {
         const int base = (int)L.seg_blk.size();
         for (int e : P.seg_end) L.seg_ptr.push_back(base + e);
+        const int pbase = (int)L.pj_box.size();
+        for (int e : P.pj_end) L.pj_ptr.push_back(pbase + e);
         append(L.seg_blk, P.seg_blk); append(L.seg_j, P.seg_j); append(L.seg_slot, P.seg_slot);
         append(L.pj_box, P.pj_box); append(L.pj_blk, P.pj_blk); append(L.pj_blkT, P.pj_blkT);
         append(L.zf_box, P.zf_box); append(L.zf_blk, P.zf_blk); append(L.zf_col, P.zf_col);
@@ -602,6 +607,7 @@ static void upload_level(LevelStruct& L, cudaStream_t s) {
     upload(d.pj_box, L.pj_box, s);
     upload(d.pj_blk, L.pj_blk, s);
     upload(d.pj_blkT, L.pj_blkT, s);
+    upload(d.pj_ptr, L.pj_ptr, s);
     upload(d.zf_box, L.zf_box, s);
     upload(d.zf_blk, L.zf_blk, s);
     upload(d.zf_col, L.zf_col, s);
