@@ -175,6 +175,16 @@ typedef struct {
     const double* sys_norm_a;   /* batch: ||A_s||_2 of every system (host, nsys values,
                                    copied); NULL = norm_a for all.  Each system's
                                    eps_fill and backward error use its own norm       */
+    const int32_t* force_ranks; /* debug (host, copied; NULL = off): the augmented rank
+                                   k~_i of every box of every skeletonised level, levels
+                                   0 (leaves) .. nlevels-1 concatenated in the box order
+                                   of h2_layout_get / h2_plan_query (the box counts of
+                                   those levels, summed).  The factorisation then keeps
+                                   k~_i - k_i fill vectors (the largest singular values,
+                                   clamped to what the box can hold) instead of
+                                   truncating at eps_fill, so that its layouts can be
+                                   compared entry by entry with another factorisation
+                                   of the same matrix (e.g. float32 against float64).  */
 } h2_factor_opts;
 
 /* h2_factor_opts.flags: time every factorisation kernel launch with CUDA events
@@ -219,9 +229,9 @@ H2_API int h2_solve(const h2_factor* Z, int32_t nrhs, double* b, int64_t ldb, in
 
 /* Iterative refinement in float64: x0 = solve(b), then corrections
  * x_{k+1} = x_k + solve(b - A x_k); once a correction fails to halve the backward
- * error (eps_lu * cond(A) near 1) the remaining corrections are restarted GMRES(30)
- * cycles on A d = b - A x_k right-preconditioned by the factor (GMRES-based
- * refinement).  Stops when the max over columns (and, for a batch, over systems s) of
+ * error (eps_lu * cond(A) near 1) the remaining corrections are restarted flexible
+ * GMRES(30) cycles on A d = b - A x_k right-preconditioned by the factor (the
+ * preconditioned basis is kept, so a reduced-precision solve need not be linear).  Stops when the max over columns (and, for a batch, over systems s) of
  * ||b_s - A_s x_s|| / (||A_s|| ||x_s||) <= tol or after maxit corrections (plain steps
  * plus GMRES iterations).  b, x: n x nrhs (device
  * when on_device != 0).  *iters receives the number of corrections, *berr the final

@@ -41,7 +41,8 @@ class h2_matrix_desc(ctypes.Structure):
 
 class h2_factor_opts(ctypes.Structure):
     _fields_ = [("eps_lu", ctypes.c_double), ("norm_a", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p), ("sys_norm_a", _dp)]
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p), ("sys_norm_a", _dp),
+                ("force_ranks", ctypes.POINTER(ctypes.c_int32))]
 
 
 class h2_factor_stats(ctypes.Structure):
@@ -234,8 +235,10 @@ def h2_matrix_batch_info(M: Matrix) -> np.ndarray:
 
 
 def h2_factor_create(M: Matrix, eps_lu: float, norm_a, precision: int = H2_PREC_FP64,
-                     stream=None, flags: int = 0) -> Factor:
-    """``norm_a``: ||A||_2, or for a batch one norm per system (a sequence)."""
+                     stream=None, flags: int = 0, force_ranks=None) -> Factor:
+    """``norm_a``: ||A||_2, or for a batch one norm per system (a sequence).
+    ``force_ranks``: debug, the augmented ranks of every level (a sequence of arrays,
+    leaves first) that the factorisation must use instead of truncating."""
     o = h2_factor_opts()
     o.eps_lu = float(eps_lu)
     keep = None
@@ -247,6 +250,11 @@ def h2_factor_create(M: Matrix, eps_lu: float, norm_a, precision: int = H2_PREC_
         o.sys_norm_a = _ptr(keep, ctypes.c_double)
     o.precision = int(precision)
     o.flags = int(flags)
+    if force_ranks is not None:
+        fr = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.int32).ravel() for r in force_ranks])
+                                  if len(force_ranks) else np.zeros(0, np.int32))
+        o.force_ranks = fr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        keep = (keep, fr)
     o.stream = ctypes.c_void_p(stream) if stream else None
     h = ctypes.c_void_p()
     _check(lib().h2_factor_create(M.handle, ctypes.byref(o), ctypes.byref(h)))

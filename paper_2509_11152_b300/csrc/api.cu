@@ -7,6 +7,11 @@
 #include "factor_impl.h"
 #include "matvec.cuh"
 
+// Krylov vectors per restarted flexible-GMRES cycle of the refinement
+#ifndef H2_GMRES_RESTART
+#define H2_GMRES_RESTART 30
+#endif
+
 namespace h2rs {
 
 static thread_local std::string g_err;
@@ -306,16 +311,20 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
             H2_REQUIRE(std::isfinite(be), H2_ERR_NONFINITE, "non-finite residual in refinement");
             return be;
         };
-        // One restarted-GMRES cycle on A d = r, right-preconditioned by the factor
-        // (A M^-1 u = r, d = M^-1 u), classical Gram-Schmidt applied twice; float64.
+        // One restarted flexible-GMRES cycle on A d = r, right-preconditioned by the
+        // factor, classical Gram-Schmidt applied twice; float64.  The preconditioned
+        // vectors z_j = M^-1 v_j are kept and d = Z y, so A Z = V H holds to float64
+        // rounding and the cycle's residual estimate is the true residual even though a
+        // reduced-precision solve is not exactly linear (forming d = M^-1 V y with a
+        // fresh solve instead would cap each cycle's gain at the solve's accuracy).
         // Every channel (right-hand side of one system) has its own Krylov basis and
         // Hessenberg matrix, so a batch converges like its slowest system.  Used once
         // plain correction steps stop contracting (eps_lu * cond(A) near 1).
-        DevBuf Vb, hb, tb;
+        DevBuf Vb, Zb, hb;
         auto gmres_cycle = [&](int m, double target_rel) -> int {
             Vb.alloc((size_t)(m + 1) * vbytes, s);
+            Zb.alloc((size_t)m * vbytes, s);
             hb.alloc((size_t)(m + 1) * nq * sizeof(double), s);
-            tb.alloc(vbytes, s);
             double* V = Vb.as<double>();
             double* hd = hb.as<double>();
             std::vector<double> beta(nq), sc(nq);
@@ -336,9 +345,10 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
             for (int j = 0; j < m; ++j) {
                 double* vj = V + (size_t)j * n * nrhs;
                 double* w = V + (size_t)(j + 1) * n * nrhs;
-                H2_CUDA_CHECK(cudaMemcpyAsync(tb.ptr, vj, vbytes, cudaMemcpyDeviceToDevice, s));
-                F.solve_dev(tb.as<double>(), nrhs, n);                       // M^-1 v_j
-                matvec_dev(A->m, nrhs, tb.as<double>(), n, w, n, s);          // A M^-1 v_j
+                double* zj = Zb.as<double>() + (size_t)j * n * nrhs;
+                H2_CUDA_CHECK(cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, s));
+                F.solve_dev(zj, nrhs, n);                                    // z_j = M^-1 v_j
+                matvec_dev(A->m, nrhs, zj, n, w, n, s);                       // A z_j
                 for (int pass = 0; pass < 2; ++pass) {
                     multidot_dev(V, w, j + 1, n, nrhs, seg, nseg, hd, s);
                     H2_CUDA_CHECK(cudaMemcpyAsync(h2.data(), hd, (size_t)(j + 1) * nq * sizeof(double),
@@ -382,7 +392,7 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
                 k = j + 1;
                 if (done) break;
             }
-            // y = R^-1 g per channel; u = V y; d = M^-1 u (left in dr)
+            // y = R^-1 g per channel; d = Z y (left in dr)
             std::vector<double> y((size_t)k * nq, 0.0);
             for (int q = 0; q < nq; ++q)
                 for (int i = k - 1; i >= 0; --i) {
@@ -392,8 +402,7 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
                 }
             H2_CUDA_CHECK(cudaMemcpyAsync(hd, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
             H2_CUDA_CHECK(cudaMemsetAsync(dr.ptr, 0, vbytes, s));
-            combine_dev(V, hd, k, n, nrhs, seg, nseg, dr.as<double>(), s);
-            F.solve_dev(dr.as<double>(), nrhs, n);
+            combine_dev(Zb.as<double>(), hd, k, n, nrhs, seg, nseg, dr.as<double>(), s);
             return k;
         };
         int it = 0;
@@ -406,7 +415,7 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
                 F.solve_dev(dr.as<double>(), nrhs, n);
                 ++it;
             } else {
-                it += gmres_cycle(std::max(1, std::min(30, maxit - it)), 0.5 * tol);
+                it += gmres_cycle(std::max(1, std::min(H2_GMRES_RESTART, maxit - it)), 0.5 * tol);
             }
             add_dev(xd, lx, dr.as<double>(), n, n, nrhs, s);
             be = residual();

@@ -64,6 +64,7 @@ static LevelArgs<T> args_of(LevelRT& L, DevStatus* st) {
     a.nb_blkT = L.d_nb_blkT.as<int>();
     a.diag_blk = L.d_diag_blk.as<int>();
     a.eps_fill = L.d_eps.as<T>();
+    a.force_kt = L.d_force.ptr ? L.d_force.as<int>() : nullptr;
     a.status = st;
     return a;
 }
@@ -118,23 +119,19 @@ static void launch_proj_tc(bool right, int nbx, cudaStream_t s, const LevelArgs<
     else k_proj_tc<false><<<nbx, pj::kThreads, pj::kSmem, s>>>(ar, c, boxes, pj_ptr, blks, budget);
 }
 
-// Schur tiles of the FMA kernel: 64 x 64 (the tensor-core kernel walks each target's
-// 128 x 64 tiles itself)
-constexpr int kSchurTile = 64;
 
-static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, const int* tb,
-                         const int* tp, const int* cb, const int* ca, const int* ck, const int* tt,
-                         const int* tmn, const SchurTgt*, const SchurCon*, const unsigned char*,
-                         const unsigned char*, long long) {
-    k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+static void launch_schur(bool, int ntile, cudaStream_t s, const LevelArgs<double>& ar, int c, int tg0,
+                         const int* tb, const int* tp, const int* cb, const int* ca, const int* ck, const SchurTgt*,
+                         const SchurCon*, const unsigned char*, const unsigned char*, long long) {
+    k_schur<double><<<ntile, 256, 0, s>>>(ar, c, tg0, tb, tp, cb, ca, ck);
 }
 
-static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c,
+static void launch_schur(bool tensor, int ntile, cudaStream_t s, const LevelArgs<float>& ar, int c, int tg0,
                          const int* tb, const int* tp, const int* cb, const int* ca, const int* ck,
-                         const int* tt, const int* tmn, const SchurTgt* trec, const SchurCon* crec,
-                         const unsigned char* pA, const unsigned char* pB, long long budget) {
+                         const SchurTgt* trec, const SchurCon* crec, const unsigned char* pA,
+                         const unsigned char* pB, long long budget) {
     if (!tensor) {
-        k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tb, tp, cb, ca, ck, tt, tmn);
+        k_schur<float><<<ntile, 256, 0, s>>>(ar, c, tg0, tb, tp, cb, ca, ck);
         return;
     }
     // tensor path: ntile = number of targets of the colour, trec offset to the first;
@@ -156,6 +153,25 @@ static void launch_pack(int, int, cudaStream_t, const LevelArgs<double>&, const 
 static void launch_pack(int npk, int c, cudaStream_t s, const LevelArgs<float>& ar, const int* box,
                         const int* pos, const int64_t* off, unsigned char* pA, unsigned char* pB) {
     k_schur_pack<<<dim3(npk, 2), 256, 0, s>>>(ar, c, box, pos, off, pA, pB);
+}
+
+// W_U (left) / W_L by triangular solves, one CTA per (box, 64-line chunk)
+template <class T>
+static void launch_wtrsm(bool left, int nmax, int nblk, cudaStream_t s, const LevelArgs<T>& ar, const int* box,
+                         const int* chunk) {
+    if (left) {
+        if (nmax <= 32) k_wtrsm<T, true, 1><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else if (nmax <= 64) k_wtrsm<T, true, 2><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else if (nmax <= 128) k_wtrsm<T, true, 4><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else if (nmax <= 256) k_wtrsm<T, true, 8><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the triangular solves"};
+    } else {
+        if (nmax <= 32) k_wtrsm<T, false, 1><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else if (nmax <= 64) k_wtrsm<T, false, 2><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else if (nmax <= 128) k_wtrsm<T, false, 4><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else if (nmax <= 256) k_wtrsm<T, false, 8><<<nblk, 256, 0, s>>>(ar, box, chunk);
+        else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the triangular solves"};
+    }
 }
 
 template <class T>
@@ -199,6 +215,19 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
             norm_sys[z] = o.sys_norm_a[z];
         }
     time_kernels = (o.flags & H2_FLAG_TIME_KERNELS) != 0;
+    if (o.force_ranks) {
+        const Plan& P = A->plan;
+        force_off.assign(P.levels.size() + 1, 0);
+        for (size_t a = 0; a < P.levels.size(); ++a) force_off[a + 1] = force_off[a] + P.levels[a].cnt;
+        force.assign(o.force_ranks, o.force_ranks + force_off.back());
+        for (size_t a = 0; a < P.levels.size(); ++a)
+            for (int i = 0; i < P.levels[a].cnt; ++i) {
+                const int64_t g = P.levels[a].first + i;
+                const int v = force[force_off[a] + i];
+                H2_REQUIRE(v >= 0 && (a > 0 || v <= A->H.node_size[g]), H2_ERR_ARG,
+                           "force_ranks: negative rank or rank above the box size");
+            }
+    }
     if (o.flags & H2_FLAG_DEBUG_SHORT_WAIT) wait_budget = 1;
     stream = static_cast<cudaStream_t>(o.stream);
     status.alloc(sizeof(DevStatus), stream);
@@ -336,6 +365,10 @@ void FactorImpl<T>::setup_level(size_t a) {
     upload(L.d_ttoff, L.ttoff, s);
     upload(L.d_tsys, L.tsys, s);
     upload(L.d_eps, eps, s);
+    if (!force.empty() && !is_top) {
+        const std::vector<int> fk(force.begin() + force_off[a], force.begin() + force_off[a + 1]);
+        upload(L.d_force, fk, s);
+    }
     L.kt.assign(S.cnt, 0);
     upload(L.d_kt, L.kt, s);
     track(this, L.blk, std::max<int64_t>(1, L.blk_off[nb]) * sizeof(T), s);
@@ -381,8 +414,9 @@ struct ColourWork {
     std::vector<int64_t> ybase, ylead, wbase;             // basis: per box
     std::vector<int64_t> scratch_need;                     // per colour (elements)
     std::vector<int> smem_basis, w_in_smem, smem_gather, gather_pc, gather_vs, nmax;
-    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;   // W_U / W_L GEMM tiles
-    std::vector<int> tile_tgt, tile_mn, tile_cptr;         // FMA Schur tiles
+    // W_U / W_L: GEMM tiles (box, 64 x 64 tile; explicit inverse) or, for the triangular
+    // solves, (box, 64-line chunk) in wu_box / wu_mn
+    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;
 };
 
 // Algorithmic flops and bytes of one level's phases (the roofline definitions of the
@@ -481,7 +515,6 @@ void FactorImpl<T>::run_level(size_t a) {
     W.wbase.resize(nbox_all);
     W.wu_cptr.push_back(0);
     W.wl_cptr.push_back(0);
-    W.tile_cptr.push_back(0);
     int nmax_level = 1;
     for (int v : L.n) nmax_level = std::max(nmax_level, v);
     for (int c = 0; c < nc; ++c) {
@@ -500,30 +533,25 @@ void FactorImpl<T>::run_level(size_t a) {
             wsum += (int64_t)n * (n + 1);
             kmax = std::max(kmax, L.k[i]);
             csz = std::max(csz, basis_chunk_elems(n));
-            const int wide = L.Nsum[i] + n;
-            for (int tm = 0; tm * 64 < n; ++tm)
-                for (int tn = 0; tn * 64 < wide; ++tn) {
+            const int wide = L.Nsum[i] + n;          // bound of the width sum n_j + k~_i
+            if (!tensor_schur) {
+                for (int ch = 0; ch * 64 < wide; ++ch) {
                     W.wu_box.push_back(i);
-                    W.wu_mn.push_back((tm << 16) | tn);
-                    W.wl_box.push_back(i);
-                    W.wl_mn.push_back((tn << 16) | tm);
+                    W.wu_mn.push_back(ch);
                 }
+            } else {
+                for (int tm = 0; tm * 64 < n; ++tm)
+                    for (int tn = 0; tn * 64 < wide; ++tn) {
+                        W.wu_box.push_back(i);
+                        W.wu_mn.push_back((tm << 16) | tn);
+                        W.wl_box.push_back(i);
+                        W.wl_mn.push_back((tn << 16) | tm);
+                    }
+            }
         }
         for (int q = S.cbox_ptr[c]; q < S.cbox_ptr[c + 1]; ++q) W.wbase[q] += ysum;   // after the Y^T rows
         W.wu_cptr.push_back((int)W.wu_box.size());
         W.wl_cptr.push_back((int)W.wl_box.size());
-        // schur tiles of the FMA kernel (the tensor-core kernel walks targets' tiles itself)
-        if (!tensor_schur)
-            for (int t = S.sch_cptr[c]; t < S.sch_cptr[c + 1]; ++t) {
-                const int tb = S.sch_tblk[t];
-                const int m = L.n[L.brow[tb]], nn = L.n[S.bcol[tb]];
-                for (int tm = 0; tm * kSchurTile < m; ++tm)
-                    for (int tn = 0; tn * kSchurTile < nn; ++tn) {
-                        W.tile_tgt.push_back(t);
-                        W.tile_mn.push_back((tm << 16) | tn);
-                    }
-            }
-        W.tile_cptr.push_back((int)W.tile_tgt.size());
         const size_t base = (size_t)(csz + 2 * nmax + 33) * sizeof(T) + 16;
         const size_t wsm = (size_t)nmax * (nmax + 1) * sizeof(T);
         const auto& lim = smem_limits<T>();
@@ -555,7 +583,6 @@ void FactorImpl<T>::run_level(size_t a) {
     DevBuf scratch;
     track(this, scratch, scratch_max * sizeof(T), s);
     DevBuf d_ybase, d_ylead, d_wbase, d_wu_box, d_wu_mn, d_wl_box, d_wl_mn, d_ynorm2;
-    DevBuf d_tile_tgt, d_tile_mn;
     d_ynorm2.alloc(std::max(1, nbox_all) * sizeof(double), s);
     H2_CUDA_CHECK(cudaMemsetAsync(d_ynorm2.ptr, 0, std::max(1, nbox_all) * sizeof(double), s));
     upload(d_ybase, W.ybase, s);
@@ -565,8 +592,6 @@ void FactorImpl<T>::run_level(size_t a) {
     upload(d_wu_mn, W.wu_mn, s);
     upload(d_wl_box, W.wl_box, s);
     upload(d_wl_mn, W.wl_mn, s);
-    upload(d_tile_tgt, W.tile_tgt, s);
-    upload(d_tile_mn, W.tile_mn, s);
     const DevBuf &d_tgt_blk = S.dev.sch_tblk, &d_tgt_ptr = S.dev.sch_tptr, &d_c_box = S.dev.sch_ci,
                  &d_c_ablk = S.dev.sch_cA, &d_c_kpos = S.dev.sch_ckpos;
     DevBuf d_trec, d_crec;                                 // Schur records (tensor-core path)
@@ -671,11 +696,19 @@ void FactorImpl<T>::run_level(size_t a) {
         const size_t lu_sm = (size_t)W.nmax[c] * W.nmax[c] * sizeof(T);
         const int lu_in = lu_sm <= (size_t)smem_limits<T>().lu;
         kbegin(H2_K_LU);
-        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, S.dev.cboxes.as<int>() + b0, lu_in);
+        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, S.dev.cboxes.as<int>() + b0, lu_in, tensor_schur ? 1 : 0);
         kend();
         H2_LAUNCHED();
         const int wu0 = W.wu_cptr[c], nwu = W.wu_cptr[c + 1] - wu0;
-        if (nwu) {
+        if (nwu && !tensor_schur) {
+            kbegin(H2_K_TRSM);
+            launch_wtrsm<T>(true, W.nmax[c], nwu, s, ar, d_wu_box.as<int>() + wu0, d_wu_mn.as<int>() + wu0);
+            kend();
+            H2_LAUNCHED();
+            kbegin(H2_K_TRSM);
+            launch_wtrsm<T>(false, W.nmax[c], nwu, s, ar, d_wu_box.as<int>() + wu0, d_wu_mn.as<int>() + wu0);
+            kend();
+        } else if (nwu) {
             kbegin(H2_K_TRSM);
             k_wgemm<T, true><<<nwu, 256, 0, s>>>(ar, d_wu_box.as<int>() + wu0, d_wu_mn.as<int>() + wu0);
             kend();
@@ -701,9 +734,8 @@ void FactorImpl<T>::run_level(size_t a) {
             }
         }
         // ---- Schur update and zeroing of the eliminated rows / columns
-        const int t0 = W.tile_cptr[c];
         const int tg0 = S.sch_cptr[c], ntg = S.sch_cptr[c + 1] - tg0;
-        const int ntile = tensor_schur ? ntg : W.tile_cptr[c + 1] - t0;   // targets on the tensor path
+        const int ntile = ntg;                                             // one record / CTA per target
         if (ntile) {
             kbegin(H2_K_SCHUR);
             if (tensor_schur) {
@@ -715,9 +747,9 @@ void FactorImpl<T>::run_level(size_t a) {
                 H2_LAUNCHED();
                 count_launch();
             }
-            launch_schur(tensor_schur, ntile, s, ar, c, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(), d_c_box.as<int>(),
-                         d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_tile_tgt.as<int>() + t0,
-                         d_tile_mn.as<int>() + t0, d_trec.as<SchurTgt>() + tg0, d_crec.as<SchurCon>(),
+            launch_schur(tensor_schur, ntile, s, ar, c, tg0, d_tgt_blk.as<int>(), d_tgt_ptr.as<int>(),
+                         d_c_box.as<int>(), d_c_ablk.as<int>(), d_c_kpos.as<int>(), d_trec.as<SchurTgt>() + tg0,
+                         d_crec.as<SchurCon>(),
                          packA.as<unsigned char>(), packB.as<unsigned char>(), wait_budget);
             kend();
         }

@@ -49,6 +49,7 @@ struct LevelArgs {
     const int* nb_blkT;    // block id of (j, i) per N(i) position
     const int* diag_blk;   // block id of (i, i)
     const T* eps_fill;     // truncation threshold eps_lu * ||A_s|| of every box
+    const int* force_kt;   // debug: forced augmented ranks of the level, or null
     DevStatus* status;
 };
 

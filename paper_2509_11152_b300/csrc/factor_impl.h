@@ -20,7 +20,7 @@ struct LevelRT {
     // boxes of dense top matrices at this level: offset inside their system's matrix
     std::vector<int64_t> ttoff;
     std::vector<int> tsys;
-    DevBuf d_ttoff, d_tsys, d_eps;
+    DevBuf d_ttoff, d_tsys, d_eps, d_force;
     // device: sizes and offsets of this factorisation
     DevBuf d_n, d_k, d_kt, d_blk_off;
     DevBuf d_V_off, d_Q_off, d_LU_off, d_piv_off, d_WU_off, d_WL_off, d_WLld;
@@ -61,6 +61,8 @@ template <class T>
 struct FactorImpl : FactorBase {
     double eps_lu = 0, norm_a = 0;
     bool tensor_schur = false;                // H2_PREC_TF32X3: Schur update on tcgen05
+    std::vector<int> force;                   // debug: forced ranks of every level (concatenated)
+    std::vector<int64_t> force_off;           // offset of each level in `force`
     std::vector<LevelRT> lv;
     // dense top matrices (float64), one per system
     int64_t nt = 0;                           // sum of their orders

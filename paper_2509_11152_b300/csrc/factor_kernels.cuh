@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "factor_args.cuh"
+#include "lu_solve.cuh"
 #include "proj_tc.cuh"
 #include "schur_ws.cuh"
 
@@ -85,6 +86,15 @@ __global__ void k_leaf_basis(LevelArgs<T> a, T* V, const double* __restrict__ U,
 }
 
 // ================================================================== augmentation
+// Whether box i's fill rows can be skipped: sigma_max(Y) <= ||Y||_F, so when the
+// Frobenius norm is below eps_fill the truncated SVD keeps nothing (the margin covers
+// the rounding of the norm itself); with forced ranks (debug) when none is asked for.
+template <class T>
+__device__ inline bool fill_below(const LevelArgs<T>& a, int i, double ynorm2, T eps_fill) {
+    if (a.force_kt) return a.force_kt[i] - a.k[i] <= 0;
+    return ynorm2 <= (double)eps_fill * (double)eps_fill * (1.0 - 4e-6);
+}
+
 // Y = (I - V V^T) F for the live columns of one fill block of box i; Y^T is written
 // into the box's scratch rows (Alg. 2 truncSVD input).
 // The live rows of all the box's segments are stored back to back (segment order), so
@@ -289,11 +299,11 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
     }
     int keep = 0;
     // sigma_max(Y) <= ||Y||_F: when the Frobenius norm (accumulated in float64 by the
-    // gather) is below eps_fill, no singular value exceeds it and the truncated SVD
-    // keeps nothing, so the R-factor and the SVD are skipped (the margin covers the
-    // rounding of the norm itself)
-    const double yn2 = L.ynorm2[slot];
-    const bool below = yn2 <= (double)eps_fill * (double)eps_fill * (1.0 - 4e-6);
+    // gather, which then stores no Y) is below eps_fill, no singular value exceeds it
+    // and the truncated SVD keeps nothing, so the R-factor and the SVD are skipped
+    // forced ranks (debug): keep exactly force_kt - k vectors, whatever their size
+    const int fkeep = a.force_kt ? max(0, min(a.force_kt[i] - k, n - k)) : -1;
+    const bool below = fill_below(a, i, L.ynorm2[slot], eps_fill);   // the gather's decision
     if (live > 0 && k < n && !below) {
         // ---------------- R-factor of Y^T (R row-major in W, row stride ldw)
         for (int x = tid; x < n * ldw; x += blockDim.x) W[x] = T(0);
@@ -411,7 +421,7 @@ k_basis(LevelArgs<T> a, ColourLists L, int cur, const T* __restrict__ scratch,
         if (tid == 0) {
             int cnt = 0;
             for (int p = 0; p < meff; ++p) cnt += sig[p] > eps_fill;
-            ired[1] = min(cnt, n - k);
+            ired[1] = fkeep >= 0 ? min(fkeep, meff) : min(cnt, n - k);
         }
         __syncthreads();
         keep = ired[1];
@@ -899,10 +909,14 @@ __global__ void k_zero_redundant(LevelArgs<T> a, const int* __restrict__ z_box,
 
 // ================================================================== partial LU
 // Alg. 2 partial factorisation (Sec. 2.1, Eq. 2.1): LU with partial pivoting of
-// D_RR = D_ii[0:r, 0:r] (first maximal |value| wins) and its explicit inverse.
+// D_RR = D_ii[0:r, 0:r] (first maximal |value| wins), P D_RR = L U stored as one r x r
+// column-major matrix; the interchanges are replaced in `piv` by the row permutation
+// they compose to, (P y)[q] = y[perm[q]].  Then, in DI (offsets of Q):
+//   inverse != 0: the explicit inverse D_RR^-1 (W_U / W_L as GEMMs, GEMV solves);
+//   inverse == 0: the transposed factors (L U)^T, for the triangular solves of W_L.
 template <class T>
 __global__ void __launch_bounds__(256)
-k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
+k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem, int inverse) {
     const int i = boxes[blockIdx.x];
     const int n = a.n[i];
     const int r = n - a.kt[i];
@@ -973,26 +987,32 @@ k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
     }
     if (in_smem)
         for (int x = tid; x < r * r; x += blockDim.x) G[x] = W[x];
-    // D_RR^-1 = U^-1 L^-1 P^T: the permuted identity, then the two triangular solves
-    // (column parallel; the inverse feeds W_U / W_L as GEMMs and the diagonal solves)
     T* X = a.DI + a.Q_off[i];
-    if (tid == 0) {
-        // row a of P^T is e_{sigma(a)}; sigma from the interchanges in forward order
-        int* sg = reinterpret_cast<int*>(X + (int64_t)r * r - r);   // temporary: last column
-        for (int q = 0; q < r; ++q) sg[q] = q;
-        for (int j = 0; j < r; ++j) { const int p = pv[j]; const int t0 = sg[j]; sg[j] = sg[p]; sg[p] = t0; }
-    }
-    __syncthreads();
+    int my[4];                                         // perm[tid + 256 q] (r <= 1024)
     {
-        const int* sg = reinterpret_cast<const int*>(X + (int64_t)r * r - r);
-        int my[4];
+        // perm from the interchanges in forward order (temporary: X's last r entries)
+        int* sg = reinterpret_cast<int*>(X + (int64_t)r * r - r);
+        if (tid == 0) {
+            for (int q = 0; q < r; ++q) sg[q] = q;
+            for (int j = 0; j < r; ++j) { const int p = pv[j]; const int t0 = sg[j]; sg[j] = sg[p]; sg[p] = t0; }
+        }
+        __syncthreads();
         for (int q = 0; q < 4; ++q) my[q] = (tid + q * 256 < r) ? sg[tid + q * 256] : 0;
         __syncthreads();
-        for (int x = tid; x < r * r; x += blockDim.x) X[x] = T(0);
-        __syncthreads();
         for (int q = 0; q < 4; ++q)
-            if (tid + q * 256 < r) X[(tid + q * 256) + (int64_t)my[q] * r] = T(1);
+            if (tid + q * 256 < r) pv[tid + q * 256] = my[q];
     }
+    if (!inverse) {                                    // (L U)^T: X[c + q r] = G[q + c r]
+        for (int x = tid; x < r * r; x += blockDim.x) X[x / r + (int64_t)(x % r) * r] = W[x];
+        return;
+    }
+    // D_RR^-1 = U^-1 L^-1 P: row q of P is e_{perm[q]}, so column perm[q] of the
+    // permuted identity has its one in row q; then the two triangular solves (column
+    // parallel; the inverse feeds W_U / W_L as GEMMs and the diagonal solves)
+    for (int x = tid; x < r * r; x += blockDim.x) X[x] = T(0);
+    __syncthreads();
+    for (int q = 0; q < 4; ++q)
+        if (tid + q * 256 < r) X[(tid + q * 256) + (int64_t)my[q] * r] = T(1);
     __syncthreads();
     for (int j = 0; j < r; ++j) {                      // L (unit lower)
         const int m = r - j - 1;
@@ -1011,6 +1031,31 @@ k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem) {
             X[rr + (int64_t)c * r] -= W[rr + (int64_t)j * r] * X[j + (int64_t)c * r];
         }
         __syncthreads();
+    }
+}
+
+// Line c (< Nsum_i + kt_i) of the operand of W_U^i / W_L^i: column c of
+// [D_{i_R, j} ..., D_{i_R, i_S}] (LEFT, contiguous: ld 1) or row c of
+// [D_{j, i_R}; ...; D_{i_S, i_R}] (!LEFT: element q at ptr[q * ld]); null beyond the width.
+template <class T, bool LEFT>
+__device__ inline void w_line(const LevelArgs<T>& a, int i, int c, const T*& ptr, int64_t& ld) {
+    const int n = a.n[i], r = n - a.kt[i], ns = a.Nsum[i];
+    ptr = nullptr;
+    ld = 0;
+    if (c >= ns + a.kt[i]) return;
+    if (c >= ns) {
+        const T* Dii = a.blk + a.blk_off[a.diag_blk[i]];
+        if (LEFT) { ptr = Dii + (int64_t)(r + c - ns) * n; ld = 1; }
+        else { ptr = Dii + (r + c - ns); ld = n; }
+        return;
+    }
+    for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
+        const int j = a.nb_col[p];
+        if (j != i && a.nbofs[p] <= c && c < a.nbofs[p] + a.n[j]) {
+            if (LEFT) { ptr = a.blk + a.blk_off[a.nb_blk[p]] + (int64_t)(c - a.nbofs[p]) * n; ld = 1; }
+            else { ptr = a.blk + a.blk_off[a.nb_blkT[p]] + (c - a.nbofs[p]); ld = a.n[j]; }
+            return;
+        }
     }
 }
 
@@ -1036,29 +1081,7 @@ k_wgemm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const T* DI = a.DI + a.Q_off[i];
     // locate the gathered lines: columns of D_{i_R,*} (LEFT) or rows of D_{*,i_R}
-    if (tid < 64) {
-        const int c = (LEFT ? n0 : m0) + tid;
-        const T* ptr = nullptr;
-        int64_t ldl = 0;
-        if (c < nt) {
-            if (c >= ns) {
-                const T* Dii = a.blk + a.blk_off[a.diag_blk[i]];
-                if (LEFT) { ptr = Dii + (int64_t)(r + c - ns) * n; ldl = 1; }
-                else { ptr = Dii + (r + c - ns); ldl = n; }
-            } else {
-                for (int p = a.nb_ptr[i]; p < a.nb_ptr[i + 1]; ++p) {
-                    const int j = a.nb_col[p];
-                    if (j != i && a.nbofs[p] <= c && c < a.nbofs[p] + a.n[j]) {
-                        if (LEFT) { ptr = a.blk + a.blk_off[a.nb_blk[p]] + (int64_t)(c - a.nbofs[p]) * n; ldl = 1; }
-                        else { ptr = a.blk + a.blk_off[a.nb_blkT[p]] + (c - a.nbofs[p]); ldl = a.n[j]; }
-                        break;
-                    }
-                }
-            }
-        }
-        gptr[tid] = ptr;
-        gld[tid] = ldl;
-    }
+    if (tid < 64) w_line<T, LEFT>(a, i, (LEFT ? n0 : m0) + tid, gptr[tid], gld[tid]);
     __syncthreads();
     T acc[4][4];
 #pragma unroll
@@ -1112,21 +1135,79 @@ k_wgemm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w
         }
 }
 
+// The same factors by triangular solves with the LU factors (P D_RR = L U), for the
+// float32 / float64 factorisations, where D_RR^-1 formed explicitly in the working
+// precision would cost refinement steps on ill-conditioned problems:
+//   W_U^i = U^-1 L^-1 P [D_{i_R, j} ...]                     (LEFT)
+//   W_L^i = [D_{j, i_R}; ...] U^-1 L^-1 P, via W_L^T = P^T L^-T U^-T [...]^T  (!LEFT)
+// One CTA per (box, 64 lines of the operand), each warp 8 lines as the right-hand sides
+// of lu_solve.cuh (registers, no barrier after the line lookup).  RU = ceil(r_max / 32).
+template <class T, bool LEFT, int RU>
+__global__ void __launch_bounds__(256)
+k_wtrsm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_chunk) {
+    constexpr int CW = 8 * kLuCols;
+    __shared__ const T* gptr[CW];
+    __shared__ int64_t gld[CW];
+    const int i = w_box[blockIdx.x];
+    const int c0 = w_chunk[blockIdx.x] * CW;
+    const int n = a.n[i], kt = a.kt[i], r = n - kt, nt = a.Nsum[i] + kt;
+    if (r <= 0 || c0 >= nt) return;
+    const int tid = threadIdx.x, lane = tid & 31, cb = c0 + kLuCols * (tid >> 5);
+    if (tid < CW) w_line<T, LEFT>(a, i, c0 + tid, gptr[tid], gld[tid]);
+    __syncthreads();
+    if (cb >= nt) return;                          // warp-uniform
+    const int* perm = a.piv + a.piv_off[i];
+    int pq[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) pq[u] = (lane + 32 * u < r) ? perm[lane + 32 * u] : 0;
+    T x[RU][kLuCols];
+#pragma unroll
+    for (int c = 0; c < kLuCols; ++c) {
+        const T* src = gptr[cb - c0 + c];
+        const int64_t ld = gld[cb - c0 + c];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int q = lane + 32 * u;
+            x[u][c] = (src && q < r) ? src[(int64_t)(LEFT ? pq[u] : q) * ld] : T(0);
+        }
+    }
+    if (LEFT) {
+        lu_solve_warp<T, RU>(x, a.LU + a.LU_off[i], r, lane);
+#pragma unroll
+        for (int c = 0; c < kLuCols; ++c) {
+            if (cb + c >= nt) break;
+            T* out = a.WU + a.WU_off[i] + (int64_t)(cb + c) * r;
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                if (lane + 32 * u < r) out[lane + 32 * u] = x[u][c];
+        }
+    } else {
+        lu_solve_t_warp<T, RU>(x, a.DI + a.Q_off[i], r, lane);
+        const int64_t ld = a.WLld[i];
+#pragma unroll
+        for (int c = 0; c < kLuCols; ++c) {
+            if (cb + c >= nt) break;
+            T* out = a.WL + a.WL_off[i] + (cb + c);
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                if (lane + 32 * u < r) out[(int64_t)pq[u] * ld] = x[u][c];
+        }
+    }
+}
+
 // ================================================================== Schur update
 // Schur complement of Alg. 2 (Sec. 2.1; fill outside the near field goes to F), with
 // target-owned accumulation: X_jk -= sum_{i in colour, j,k in N(i)} D_{j,i_R} W_U^i[k]
-// as one GEMM per target whose K dimension runs over the contributors.  64x64 tiles,
-// 256 threads, 4x4 outputs per thread.
+// as one GEMM per target whose K dimension runs over the contributors.  One CTA per
+// target, its 64x64 tiles in turn, 256 threads, 4x4 outputs per thread.
 template <class T>
 __global__ void __launch_bounds__(256)
-k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
-        const int* __restrict__ c_box, const int* __restrict__ c_ablk, const int* __restrict__ c_kpos,
-        const int* __restrict__ tile_tgt, const int* __restrict__ tile_mn) {
+k_schur(LevelArgs<T> a, int cur, int tg0, const int* __restrict__ tgt_blk, const int* __restrict__ tgt_ptr,
+        const int* __restrict__ c_box, const int* __restrict__ c_ablk, const int* __restrict__ c_kpos) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ T As[2][BK][BM + 1];
     __shared__ T Bs[2][BK][BN + 1];
-    const int tt = tile_tgt[blockIdx.x];
-    const int mn = tile_mn[blockIdx.x];
+    const int tt = tg0 + blockIdx.x;              // one CTA per target, its tiles in turn
     const int tb = tgt_blk[tt];
     const int j = a.brow[tb], kb = a.bcol[tb];
     const int nj = a.n[j], nk = a.n[kb];
@@ -1135,88 +1216,91 @@ k_schur(LevelArgs<T> a, int cur, const int* __restrict__ tgt_blk, const int* __r
     const int row_lo = (a.colour[j] <= cur) ? nj - a.kt[j] : 0;
     const int col_lo = (a.colour[kb] <= cur) ? nk - a.kt[kb] : 0;
     const int m = nj - row_lo, nn = nk - col_lo;
-    const int m0 = (mn >> 16) * BM, n0 = (mn & 0xffff) * BN;
-    if (m0 >= m || n0 >= nn) return;
+    const int ntm = (m + BM - 1) / BM, ntn = (nn + BN - 1) / BN;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     // this thread's load slots: A rows 4*(tid%16)+q of k-column tid/16; B k-rows 4*(tid%4)+q of column tid/4
     const int la_k = tid >> 4, la_r = 4 * (tid & 15);
     const int lb_c = tid >> 2, lb_k = 4 * (tid & 3);
-    T acc[4][4];
+    for (int tile = 0; tile < ntm * ntn; ++tile) {
+        const int m0 = (tile / ntn) * BM, n0 = (tile % ntn) * BN;
+        T acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    // K-steps run over (contributor, 16-wide slice); the next step's operands are
-    // fetched into registers while the current step computes from shared memory
-    int c = tgt_ptr[tt];
-    const int cend = tgt_ptr[tt + 1];
-    int k0 = 0, ri = 0;
-    const T* A = nullptr;
-    const T* B = nullptr;
-    auto advance = [&](bool first) -> bool {        // move (c, k0) to the next valid step
-        if (!first) {
-            k0 += BK;
-            if (k0 < ri) return true;
-            ++c;
-        }
-        for (; c < cend; ++c) {
-            const int i = c_box[c];
-            ri = a.n[i] - a.kt[i];
-            if (ri <= 0) continue;
-            A = a.blk + a.blk_off[c_ablk[c]] + row_lo;                        // m x ri, ld nj
-            // W_U^i holds all n_k columns of a neighbour k (col_lo: skip the zero ones of
-            // an eliminated k) but only the skeleton columns of i itself
-            B = a.WU + a.WU_off[i] +
-                (int64_t)(a.nbofs[a.nb_ptr[i] + c_kpos[c]] + (kb == i ? 0 : col_lo)) * ri;   // ri x nn, ld ri
-            k0 = 0;
-            return true;
-        }
-        return false;
-    };
-    T ra[4], rb[4];
-    auto fetch = [&]() {
+            for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        // K-steps run over (contributor, 16-wide slice); the next step's operands are
+        // fetched into registers while the current step computes from shared memory
+        int c = tgt_ptr[tt];
+        const int cend = tgt_ptr[tt + 1];
+        int k0 = 0, ri = 0;
+        const T* A = nullptr;
+        const T* B = nullptr;
+        auto advance = [&](bool first) -> bool {    // move (c, k0) to the next valid step
+            if (!first) {
+                k0 += BK;
+                if (k0 < ri) return true;
+                ++c;
+            }
+            for (; c < cend; ++c) {
+                const int i = c_box[c];
+                ri = a.n[i] - a.kt[i];
+                if (ri <= 0) continue;
+                A = a.blk + a.blk_off[c_ablk[c]] + row_lo;                        // m x ri, ld nj
+                // W_U^i holds all n_k columns of a neighbour k (col_lo: skip the zero ones
+                // of an eliminated k) but only the skeleton columns of i itself
+                B = a.WU + a.WU_off[i] +
+                    (int64_t)(a.nbofs[a.nb_ptr[i] + c_kpos[c]] + (kb == i ? 0 : col_lo)) * ri;   // ri x nn, ld ri
+                k0 = 0;
+                return true;
+            }
+            return false;
+        };
+        T ra[4], rb[4];
+        auto fetch = [&]() {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int gr = m0 + la_r + q, gk = k0 + la_k;
-            ra[q] = (gr < m && gk < ri) ? A[gr + (int64_t)gk * nj] : T(0);
-            const int gc = n0 + lb_c, gk2 = k0 + lb_k + q;
-            rb[q] = (gc < nn && gk2 < ri) ? B[gk2 + (int64_t)gc * ri] : T(0);
-        }
-    };
-    bool have = advance(true);
-    if (have) fetch();
-    int buf = 0;
-    while (have) {
+            for (int q = 0; q < 4; ++q) {
+                const int gr = m0 + la_r + q, gk = k0 + la_k;
+                ra[q] = (gr < m && gk < ri) ? A[gr + (int64_t)gk * nj] : T(0);
+                const int gc = n0 + lb_c, gk2 = k0 + lb_k + q;
+                rb[q] = (gc < nn && gk2 < ri) ? B[gk2 + (int64_t)gc * ri] : T(0);
+            }
+        };
+        bool have = advance(true);
+        if (have) fetch();
+        int buf = 0;
+        while (have) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            As[buf][la_k][la_r + q] = ra[q];
-            Bs[buf][lb_k + q][lb_c] = rb[q];
-        }
-        __syncthreads();
-        have = advance(false);
-        if (have) fetch();                           // overlaps with the products below
+            for (int q = 0; q < 4; ++q) {
+                As[buf][la_k][la_r + q] = ra[q];
+                Bs[buf][lb_k + q][lb_c] = rb[q];
+            }
+            __syncthreads();
+            have = advance(false);
+            if (have) fetch();                       // overlaps with the products below
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T av[4], bv[4];
+            for (int kk = 0; kk < BK; ++kk) {
+                T av[4], bv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) av[u] = As[buf][kk][tx + 16 * u];
+                for (int u = 0; u < 4; ++u) av[u] = As[buf][kk][tx + 16 * u];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) bv[v] = Bs[buf][kk][ty + 16 * v];
+                for (int v = 0; v < 4; ++v) bv[v] = Bs[buf][kk][ty + 16 * v];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
-        }
-        buf ^= 1;                                    // the other buffer is free: its last
-    }                                                // readers passed this step's barrier
-    T* Cm = a.blk + a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
+                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+            }
+            buf ^= 1;                                // the other buffer is free: its last
+        }                                            // readers passed this step's barrier
+        T* Cm = a.blk + a.blk_off[tb] + row_lo + (int64_t)col_lo * nj;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int gr = m0 + tx + 16 * u, gc = n0 + ty + 16 * v;
-            if (gr < m && gc < nn) Cm[gr + (int64_t)gc * nj] -= acc[u][v];
-        }
+            for (int v = 0; v < 4; ++v) {
+                const int gr = m0 + tx + 16 * u, gc = n0 + ty + 16 * v;
+                if (gr < m && gc < nn) Cm[gr + (int64_t)gc * nj] -= acc[u][v];
+            }
+        __syncthreads();                             // the stages are reused by the next tile
+    }
 }
 
 // ---- tensor-core path: operand packing, records, update (see schur_ws.cuh)

@@ -8,6 +8,11 @@
 
 namespace h2rs {
 
+// Every product kernel: one thread per row of its result, RB right-hand sides per pass
+// in registers (a matrix entry loaded once serves RB columns; RB = 1 for one column).
+constexpr int kMvRB = 8;
+
+template <int RB>
 __global__ void mv_leaf_up(const double* __restrict__ U, const int64_t* __restrict__ U_off,
                            const int64_t* __restrict__ start, const int64_t* __restrict__ size,
                            const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off,
@@ -19,39 +24,62 @@ __global__ void mv_leaf_up(const double* __restrict__ U, const int64_t* __restri
     const double* Ui = U + U_off[i];
     const double* xi = x + start[g];
     double* out = xh + coef_off[g] * nrhs;
-    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
-        const int a = e % k, c = e / k;
-        const double* u = Ui + (int64_t)a * n;
-        const double* xc = xi + (int64_t)c * ldx;
-        double acc = 0;
-        for (int q = 0; q < n; ++q) acc += u[q] * xc[q];
-        out[e] = acc;
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < k; a += blockDim.x) {
+            double acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = 0;
+            const double* u = Ui + (int64_t)a * n;
+            for (int q = 0; q < n; ++q) {
+                const double uv = u[q];
+#pragma unroll
+                for (int cc = 0; cc < RB; ++cc)
+                    if (cc < cm) acc[cc] += uv * xi[q + (int64_t)(c0 + cc) * ldx];
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) out[a + (int64_t)(c0 + cc) * k] = acc[cc];
+        }
     }
 }
 
 // xh_p = sum_c E_c^T xh_c for the nodes p of one level (first = first node id; the
 // children of p are child0[p] and child0[p] + 1)
+template <int RB>
 __global__ void mv_up(const double* __restrict__ E, const int64_t* __restrict__ E_off,
                       const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off, int64_t first,
                       const int64_t* __restrict__ child0, double* __restrict__ xh, int nrhs) {
     const int64_t p = first + blockIdx.x;
-    const int64_t c0 = child0[p];
+    const int64_t c0n = child0[p];
     const int kp = (int)rank[p];
     double* out = xh + coef_off[p] * nrhs;
-    for (int e = threadIdx.x; e < kp * nrhs; e += blockDim.x) {
-        const int a = e % kp, c = e / kp;
-        double acc = 0;
-        for (int64_t ch = c0; ch <= c0 + 1; ++ch) {
-            const int kc = (int)rank[ch];
-            const double* Ec = E + E_off[ch] + (int64_t)a * kc;   // column a of E_c
-            const double* xc = xh + coef_off[ch] * nrhs + (int64_t)c * kc;
-            for (int q = 0; q < kc; ++q) acc += Ec[q] * xc[q];
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < kp; a += blockDim.x) {
+            double acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = 0;
+            for (int64_t ch = c0n; ch <= c0n + 1; ++ch) {
+                const int kc = (int)rank[ch];
+                const double* Ec = E + E_off[ch] + (int64_t)a * kc;   // column a of E_c
+                const double* xc = xh + coef_off[ch] * nrhs + (int64_t)c0 * kc;
+                for (int q = 0; q < kc; ++q) {
+                    const double ev = Ec[q];
+#pragma unroll
+                    for (int cc = 0; cc < RB; ++cc)
+                        if (cc < cm) acc[cc] += ev * xc[q + (int64_t)cc * kc];
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) out[a + (int64_t)(c0 + cc) * kp] = acc[cc];
         }
-        out[e] = acc;
     }
 }
 
 // yh_s = sum_{t admissible} S_st xh_t for every node s
+template <int RB>
 __global__ void mv_couple(const double* __restrict__ S, const int64_t* __restrict__ S_off,
                           const int64_t* __restrict__ adm_ptr, const int64_t* __restrict__ adm_col,
                           const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off,
@@ -59,21 +87,33 @@ __global__ void mv_couple(const double* __restrict__ S, const int64_t* __restric
     const int64_t s = blockIdx.x;
     const int ks = (int)rank[s];
     double* out = yh + coef_off[s] * nrhs;
-    for (int e = threadIdx.x; e < ks * nrhs; e += blockDim.x) {
-        const int a = e % ks, c = e / ks;
-        double acc = 0;
-        for (int64_t q = adm_ptr[s]; q < adm_ptr[s + 1]; ++q) {
-            const int64_t t = adm_col[q];
-            const int kt = (int)rank[t];
-            const double* St = S + S_off[q] + a;
-            const double* xt = xh + coef_off[t] * nrhs + (int64_t)c * kt;
-            for (int b = 0; b < kt; ++b) acc += St[(int64_t)b * ks] * xt[b];
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < ks; a += blockDim.x) {
+            double acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = 0;
+            for (int64_t q = adm_ptr[s]; q < adm_ptr[s + 1]; ++q) {
+                const int64_t t = adm_col[q];
+                const int kt = (int)rank[t];
+                const double* St = S + S_off[q] + a;
+                const double* xt = xh + coef_off[t] * nrhs + (int64_t)c0 * kt;
+                for (int b = 0; b < kt; ++b) {
+                    const double sv = St[(int64_t)b * ks];
+#pragma unroll
+                    for (int cc = 0; cc < RB; ++cc)
+                        if (cc < cm) acc[cc] += sv * xt[b + (int64_t)cc * kt];
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) out[a + (int64_t)(c0 + cc) * ks] = acc[cc];
         }
-        out[e] = acc;
     }
 }
 
 // yh_c += E_c yh_parent for the nodes c of one level (roots of a forest have none)
+template <int RB>
 __global__ void mv_down(const double* __restrict__ E, const int64_t* __restrict__ E_off,
                         const int64_t* __restrict__ rank, const int64_t* __restrict__ coef_off, int64_t first,
                         const int64_t* __restrict__ parent, double* __restrict__ yh, int nrhs) {
@@ -84,15 +124,27 @@ __global__ void mv_down(const double* __restrict__ E, const int64_t* __restrict_
     double* out = yh + coef_off[g] * nrhs;
     const double* yp = yh + coef_off[p] * nrhs;
     const double* Eg = E + E_off[g];
-    for (int e = threadIdx.x; e < kc * nrhs; e += blockDim.x) {
-        const int a = e % kc, c = e / kc;
-        double acc = 0;
-        for (int b = 0; b < kp; ++b) acc += Eg[a + (int64_t)b * kc] * yp[b + (int64_t)c * kp];
-        out[e] += acc;
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < kc; a += blockDim.x) {
+            double acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = 0;
+            for (int b = 0; b < kp; ++b) {
+                const double ev = Eg[a + (int64_t)b * kc];
+#pragma unroll
+                for (int cc = 0; cc < RB; ++cc)
+                    if (cc < cm) acc[cc] += ev * yp[b + (int64_t)(c0 + cc) * kp];
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) out[a + (int64_t)(c0 + cc) * kc] += acc[cc];
+        }
     }
 }
 
 // y_i = U_i yh_i + sum_{t near} D_it x_t on the leaves
+template <int RB>
 __global__ void mv_leaf_down(const double* __restrict__ U, const int64_t* __restrict__ U_off,
                              const double* __restrict__ D, const int64_t* __restrict__ D_off,
                              const int64_t* __restrict__ inad_ptr, const int64_t* __restrict__ inad_col,
@@ -106,18 +158,34 @@ __global__ void mv_leaf_down(const double* __restrict__ U, const int64_t* __rest
     const double* Ui = U + U_off[i];
     const double* yi = yh + coef_off[g] * nrhs;
     const int64_t base = inad_ptr[first];
-    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
-        const int a = e % n, c = e / n;
-        double acc = 0;
-        for (int b = 0; b < k; ++b) acc += Ui[a + (int64_t)b * n] * yi[b + (int64_t)c * k];
-        for (int64_t q = inad_ptr[g]; q < inad_ptr[g + 1]; ++q) {
-            const int64_t t = inad_col[q];
-            const int nt = (int)size[t];
-            const double* Dq = D + D_off[q - base] + a;
-            const double* xt = x + start[t] + (int64_t)c * ldx;
-            for (int b = 0; b < nt; ++b) acc += Dq[(int64_t)b * n] * xt[b];
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+            double acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = 0;
+            for (int b = 0; b < k; ++b) {
+                const double uv = Ui[a + (int64_t)b * n];
+#pragma unroll
+                for (int cc = 0; cc < RB; ++cc)
+                    if (cc < cm) acc[cc] += uv * yi[b + (int64_t)(c0 + cc) * k];
+            }
+            for (int64_t q = inad_ptr[g]; q < inad_ptr[g + 1]; ++q) {
+                const int64_t t = inad_col[q];
+                const int nt = (int)size[t];
+                const double* Dq = D + D_off[q - base] + a;
+                const double* xt = x + start[t] + (int64_t)c0 * ldx;
+                for (int b = 0; b < nt; ++b) {
+                    const double dv = Dq[(int64_t)b * n];
+#pragma unroll
+                    for (int cc = 0; cc < RB; ++cc)
+                        if (cc < cm) acc[cc] += dv * xt[b + (int64_t)cc * ldx];
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) y[start[g] + a + (int64_t)(c0 + cc) * ldy] = acc[cc];
         }
-        y[start[g] + a + (int64_t)c * ldy] = acc;
     }
 }
 
@@ -269,29 +337,47 @@ void matvec_dev(const MatrixObj& M, int nrhs, const double* x, int64_t ldx, doub
     const int nleaf = (int)H.lev_cnt[d];
     const int64_t* rank = M.d_rank.as<int64_t>();
     const int64_t* coef = M.d_coef_off.as<int64_t>();
-    mv_leaf_up<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
-                                     M.d_node_size.as<int64_t>(), rank, coef, first_leaf, x, ldx,
-                                     xh.p, nrhs);
+    const bool one = nrhs == 1;
+    if (one) mv_leaf_up<1><<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
+                                                 M.d_node_size.as<int64_t>(), rank, coef, first_leaf, x, ldx, xh.p, nrhs);
+    else mv_leaf_up<kMvRB><<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.d_node_start.as<int64_t>(),
+                                                 M.d_node_size.as<int64_t>(), rank, coef, first_leaf, x, ldx, xh.p, nrhs);
     count_launch();
     for (int l = d; l >= 1; --l) {
-        mv_up<<<(unsigned)H.lev_cnt[l - 1], 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef,
-                                                         H.lev_first[l - 1], M.d_child0.as<int64_t>(), xh.p, nrhs);
+        const unsigned g = (unsigned)H.lev_cnt[l - 1];
+        if (one) mv_up<1><<<g, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, H.lev_first[l - 1],
+                                            M.d_child0.as<int64_t>(), xh.p, nrhs);
+        else mv_up<kMvRB><<<g, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, H.lev_first[l - 1],
+                                            M.d_child0.as<int64_t>(), xh.p, nrhs);
         count_launch();
     }
-    mv_couple<<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
-                                                  M.d_adm_ptr.as<int64_t>(), M.d_adm_col.as<int64_t>(), rank,
-                                                  coef, xh.p, yh.p, nrhs);
+    if (one) mv_couple<1><<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
+                                                             M.d_adm_ptr.as<int64_t>(), M.d_adm_col.as<int64_t>(),
+                                                             rank, coef, xh.p, yh.p, nrhs);
+    else mv_couple<kMvRB><<<(unsigned)H.nnodes, 128, 0, s>>>(M.S.as<double>(), M.d_S_off.as<int64_t>(),
+                                                             M.d_adm_ptr.as<int64_t>(), M.d_adm_col.as<int64_t>(),
+                                                             rank, coef, xh.p, yh.p, nrhs);
     count_launch();
     for (int l = 1; l <= d; ++l) {
-        mv_down<<<(unsigned)H.lev_cnt[l], 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef,
-                                                       H.lev_first[l], M.d_parent.as<int64_t>(), yh.p, nrhs);
+        const unsigned g = (unsigned)H.lev_cnt[l];
+        if (one) mv_down<1><<<g, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, H.lev_first[l],
+                                              M.d_parent.as<int64_t>(), yh.p, nrhs);
+        else mv_down<kMvRB><<<g, 128, 0, s>>>(M.E.as<double>(), M.d_E_off.as<int64_t>(), rank, coef, H.lev_first[l],
+                                              M.d_parent.as<int64_t>(), yh.p, nrhs);
         count_launch();
     }
-    mv_leaf_down<<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),
-                                       M.d_D_off.as<int64_t>(), M.d_inad_ptr.as<int64_t>(),
-                                       M.d_inad_col.as<int64_t>(), M.d_node_start.as<int64_t>(),
-                                       M.d_node_size.as<int64_t>(), rank, coef, first_leaf,
-                                       yh.p, x, ldx, y, ldy, nrhs);
+    if (one)
+        mv_leaf_down<1><<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),
+                                              M.d_D_off.as<int64_t>(), M.d_inad_ptr.as<int64_t>(),
+                                              M.d_inad_col.as<int64_t>(), M.d_node_start.as<int64_t>(),
+                                              M.d_node_size.as<int64_t>(), rank, coef, first_leaf, yh.p, x, ldx, y,
+                                              ldy, nrhs);
+    else
+        mv_leaf_down<kMvRB><<<nleaf, 128, 0, s>>>(M.U.as<double>(), M.d_U_off.as<int64_t>(), M.D.as<double>(),
+                                                  M.d_D_off.as<int64_t>(), M.d_inad_ptr.as<int64_t>(),
+                                                  M.d_inad_col.as<int64_t>(), M.d_node_start.as<int64_t>(),
+                                                  M.d_node_size.as<int64_t>(), rank, coef, first_leaf, yh.p, x, ldx,
+                                                  y, ldy, nrhs);
     count_launch();
     H2_CUDA_CHECK(cudaGetLastError());
 }

@@ -4,6 +4,7 @@
 // update, then Q~).  Vectors of a level hold each box's coordinates contiguously:
 // box i at offset voff[i]*nrhs, n_i x nrhs column-major.
 #include "factor_impl.h"
+#include "lu_solve.cuh"
 
 namespace h2rs {
 
@@ -34,8 +35,13 @@ __global__ void s_store(double* __restrict__ b, int64_t ldb, int nrhs, const int
     }
 }
 
-// x_i <- Q~_i^T x_i (trans = 1) or Q~_i x_i (trans = 0) for the boxes of a colour
-template <class T>
+// Right-hand sides in register blocks of RB columns: a matrix entry loaded once serves
+// RB columns (RB = 1 for a single right-hand side).
+constexpr int kRB = 8;
+
+// x_i <- Q~_i^T x_i (trans = 1) or Q~_i x_i (trans = 0) for the boxes of a colour; one
+// thread per row of the result, RB right-hand sides per pass
+template <class T, int RB>
 __global__ void s_apply_q(const int* __restrict__ boxes, const int* __restrict__ n, const T* __restrict__ Q,
                           const int64_t* __restrict__ Q_off, const int64_t* __restrict__ voff, T* __restrict__ x,
                           int nrhs, int trans) {
@@ -48,21 +54,28 @@ __global__ void s_apply_q(const int* __restrict__ boxes, const int* __restrict__
     const T* Qi = Q + Q_off[i];
     for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) xs[e] = xi[e];
     __syncthreads();
-    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
-        const int a = e % ni, c = e / ni;
-        T acc = 0;
-        if (trans) {
-            const T* qa = Qi + (int64_t)a * ni;
-            for (int q = 0; q < ni; ++q) acc += qa[q] * xs[q + c * ni];
-        } else {
-            for (int q = 0; q < ni; ++q) acc += Qi[a + (int64_t)q * ni] * xs[q + c * ni];
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < ni; a += blockDim.x) {
+            T acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = T(0);
+            for (int q = 0; q < ni; ++q) {
+                const T qv = trans ? Qi[q + (int64_t)a * ni] : Qi[a + (int64_t)q * ni];
+#pragma unroll
+                for (int cc = 0; cc < RB; ++cc)
+                    if (cc < cm) acc[cc] += qv * xs[q + (c0 + cc) * ni];
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) xi[a + (int64_t)(c0 + cc) * ni] = acc[cc];
         }
-        xi[e] = acc;
     }
 }
 
-// forward L update of a colour, target owned: x_j -= sum_i W_L^i[j] x_{i_R}
-template <class T>
+// forward L update of a colour, target owned: x_j -= sum_i W_L^i[j] x_{i_R}; one thread
+// per updated row, RB right-hand sides per pass
+template <class T, int RB>
 __global__ void s_fwd_l(const int* __restrict__ tbox, const int* __restrict__ tptr, const int* __restrict__ ci,
                         const int* __restrict__ cpos, int cur, const int* __restrict__ colour,
                         const int* __restrict__ n, const int* __restrict__ kt, const int* __restrict__ nb_ptr,
@@ -76,29 +89,41 @@ __global__ void s_fwd_l(const int* __restrict__ tbox, const int* __restrict__ tp
     const int lo = (colour[j] <= cur) ? nj - kt[j] : 0;
     const int m = nj - lo;
     T* xj = x + voff[j] * nrhs;
-    for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
-        const int a = e % m, c = e / m;
-        T acc = 0;
-        for (int q = tptr[t]; q < tptr[t + 1]; ++q) {
-            const int i = ci[q];
-            const int ri = n[i] - kt[i];
-            if (ri <= 0) continue;
-            // W_L^i holds all n_j rows of a neighbour j (skip the zero rows of an
-            // eliminated j) but only the skeleton rows of i itself
-            const int row = nbofs[nb_ptr[i] + cpos[q]] + (j == i ? 0 : lo) + a;
-            const T* W = WL + WL_off[i] + row;
-            const int64_t ld = WLld[i];
-            const T* xr = x + voff[i] * nrhs + (int64_t)c * n[i];
-            for (int b = 0; b < ri; ++b) acc += W[(int64_t)b * ld] * xr[b];
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        for (int a = threadIdx.x; a < m; a += blockDim.x) {
+            T acc[RB];
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[cc] = T(0);
+            for (int q = tptr[t]; q < tptr[t + 1]; ++q) {
+                const int i = ci[q];
+                const int ni = n[i], ri = ni - kt[i];
+                if (ri <= 0) continue;
+                // W_L^i holds all n_j rows of a neighbour j (skip the zero rows of an
+                // eliminated j) but only the skeleton rows of i itself
+                const int row = nbofs[nb_ptr[i] + cpos[q]] + (j == i ? 0 : lo) + a;
+                const T* W = WL + WL_off[i] + row;
+                const int64_t ld = WLld[i];
+                const T* xr = x + voff[i] * nrhs + (int64_t)c0 * ni;
+                for (int b = 0; b < ri; ++b) {
+                    const T w = W[(int64_t)b * ld];
+#pragma unroll
+                    for (int cc = 0; cc < RB; ++cc)
+                        if (cc < cm) acc[cc] += w * xr[b + (int64_t)cc * ni];
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc < cm) xj[lo + a + (int64_t)(c0 + cc) * nj] -= acc[cc];
         }
-        xj[lo + a + (int64_t)c * nj] -= acc;
     }
 }
 
 // backward U update of a colour: x_{i_R} -= sum_k W_U^i[k] x_k (box owned).  One block
 // per box; warp w takes every 8th column of each neighbour segment of W_U^i, lane l
-// accumulates rows l + 32u in registers (RU per lane), then the 8 warps are summed.
-template <class T, int RU>
+// accumulates rows l + 32u (RU per lane) for RB right-hand sides in registers, then the
+// 8 warps are summed.
+template <class T, int RU, int RB>
 __global__ void __launch_bounds__(256)
 s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n, const int* __restrict__ kt,
         const int* __restrict__ nb_ptr, const int* __restrict__ nb_col,
@@ -110,41 +135,53 @@ s_bwd_u(const int* __restrict__ boxes, const int* __restrict__ n, const int* __r
     if (ri <= 0) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* red = reinterpret_cast<T*>(sm_raw);                 // 8 x ri
+    T* red = reinterpret_cast<T*>(sm_raw);                 // 8 x ri x RB
     T* xi = x + voff[i] * nrhs;
     const T* Wi = WU + WU_off[i];
-    for (int c = 0; c < nrhs; ++c) {
-        T acc[RU];
+    for (int c0 = 0; c0 < nrhs; c0 += RB) {
+        const int cm = min(RB, nrhs - c0);
+        T acc[RU][RB];
 #pragma unroll
-        for (int u = 0; u < RU; ++u) acc[u] = T(0);
+        for (int u = 0; u < RU; ++u)
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[u][cc] = T(0);
         for (int p = nb_ptr[i]; p < nb_ptr[i + 1]; ++p) {
             const int jb = nb_col[p];
             const int o = nbofs[p];
             const T* xs;
-            int wdt;
-            if (jb == i) { xs = xi + (int64_t)c * ni + ri; wdt = kt[i]; }
-            else { xs = x + voff[jb] * nrhs + (int64_t)c * n[jb]; wdt = n[jb]; }
+            int wdt, nx;
+            if (jb == i) { xs = xi + (int64_t)c0 * ni + ri; wdt = kt[i]; nx = ni; }
+            else { nx = n[jb]; xs = x + voff[jb] * nrhs + (int64_t)c0 * nx; wdt = nx; }
             for (int b = w; b < wdt; b += 8) {
-                const T xb = xs[b];
+                T xb[RB];
+#pragma unroll
+                for (int cc = 0; cc < RB; ++cc) xb[cc] = cc < cm ? xs[b + (int64_t)cc * nx] : T(0);
                 const T* col = Wi + (int64_t)(o + b) * ri;
 #pragma unroll
                 for (int u = 0; u < RU; ++u) {
                     const int aa = lane + 32 * u;
-                    if (aa < ri) acc[u] += col[aa] * xb;
+                    if (aa < ri) {
+                        const T wv = col[aa];
+#pragma unroll
+                        for (int cc = 0; cc < RB; ++cc) acc[u][cc] += wv * xb[cc];
+                    }
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
             const int aa = lane + 32 * u;
-            if (aa < ri) red[w * ri + aa] = acc[u];
+            if (aa < ri)
+#pragma unroll
+                for (int cc = 0; cc < RB; ++cc) red[(w * ri + aa) * RB + cc] = acc[u][cc];
         }
         __syncthreads();
-        for (int aa = threadIdx.x; aa < ri; aa += blockDim.x) {
+        for (int e = threadIdx.x; e < ri * cm; e += blockDim.x) {
+            const int aa = e % ri, cc = e / ri;
             T sacc = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) sacc += red[q * ri + aa];
-            xi[aa + (int64_t)c * ni] -= sacc;
+            for (int q = 0; q < 8; ++q) sacc += red[(q * ri + aa) * RB + cc];
+            xi[aa + (int64_t)(c0 + cc) * ni] -= sacc;
         }
         __syncthreads();
     }
@@ -170,6 +207,40 @@ __global__ void s_diag(const int* __restrict__ boxes, const int* __restrict__ n,
         T acc = 0;
         for (int q = 0; q < r; ++q) acc += D[a + (int64_t)q * r] * xs[q + c * r];
         xi[a + (int64_t)c * ni] = acc;
+    }
+}
+
+// diagonal solve by triangular solves with the LU factors (P D_RR = L U; perm in `piv`):
+// x_{i_R} <- U^-1 L^-1 P x_{i_R}, one block per skeletonised box, each warp 8 right-hand
+// sides in registers (lu_solve.cuh).  A warp reads all of its columns before it writes.
+template <class T, int RU>
+__global__ void __launch_bounds__(256)
+s_diag_lu(const int* __restrict__ boxes, const int* __restrict__ n, const int* __restrict__ kt,
+          const T* __restrict__ LU, const int64_t* __restrict__ LU_off, const int* __restrict__ piv,
+          const int64_t* __restrict__ piv_off, const int64_t* __restrict__ voff, T* __restrict__ x, int nrhs) {
+    const int i = boxes[blockIdx.x];
+    const int ni = n[i], r = ni - kt[i];
+    if (r <= 0) return;
+    const int lane = threadIdx.x & 31;
+    const int* perm = piv + piv_off[i];
+    const T* G = LU + LU_off[i];
+    T* xi = x + voff[i] * nrhs;
+    int pq[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) pq[u] = (lane + 32 * u < r) ? perm[lane + 32 * u] : 0;
+    for (int c0 = kLuCols * (threadIdx.x >> 5); c0 < nrhs; c0 += kLuCols * (blockDim.x >> 5)) {
+        T v[RU][kLuCols];
+#pragma unroll
+        for (int c = 0; c < kLuCols; ++c)
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                v[u][c] = (c0 + c < nrhs && lane + 32 * u < r) ? xi[pq[u] + (int64_t)(c0 + c) * ni] : T(0);
+        lu_solve_warp<T, RU>(v, G, r, lane);
+#pragma unroll
+        for (int c = 0; c < kLuCols; ++c)
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                if (c0 + c < nrhs && lane + 32 * u < r) xi[lane + 32 * u + (int64_t)(c0 + c) * ni] = v[u][c];
     }
 }
 
@@ -259,16 +330,57 @@ static void allow_smem(K kern) {
                                        optin - (int)fa.sharedSizeBytes));
 }
 
+template <class T, int RB>
+static void launch_bwd_u_rb(int nmax, int nb, cudaStream_t s, const int* boxes, const int* n, const int* kt,
+                            const int* nb_ptr, const int* nb_col, const int* nbofs, const T* WU,
+                            const int64_t* WU_off, const int64_t* voff, T* x, int nrhs) {
+    const int smem = 8 * nmax * RB * (int)sizeof(T);
+    if (nmax <= 32) s_bwd_u<T, 1, RB><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else if (nmax <= 64) s_bwd_u<T, 2, RB><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else if (nmax <= 128) s_bwd_u<T, 4, RB><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else if (nmax <= 256) s_bwd_u<T, 8, RB><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the solve"};
+}
+
+// backward U update: RB = 4 right-hand sides per pass (RU rows per lane x RB registers)
 template <class T>
 static void launch_bwd_u(int nmax, int nb, cudaStream_t s, const int* boxes, const int* n, const int* kt,
                          const int* nb_ptr, const int* nb_col, const int* nbofs, const T* WU,
                          const int64_t* WU_off, const int64_t* voff, T* x, int nrhs) {
-    const int smem = 8 * nmax * (int)sizeof(T);
-    if (nmax <= 32) s_bwd_u<T, 1><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
-    else if (nmax <= 64) s_bwd_u<T, 2><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
-    else if (nmax <= 128) s_bwd_u<T, 4><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
-    else if (nmax <= 256) s_bwd_u<T, 8><<<nb, 256, smem, s>>>(boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    if (nrhs == 1) launch_bwd_u_rb<T, 1>(nmax, nb, s, boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+    else launch_bwd_u_rb<T, 4>(nmax, nb, s, boxes, n, kt, nb_ptr, nb_col, nbofs, WU, WU_off, voff, x, nrhs);
+}
+
+template <class T>
+static void launch_diag_lu(int nmax, unsigned nb, cudaStream_t s, const int* boxes, const int* n, const int* kt,
+                           const T* LU, const int64_t* LU_off, const int* piv, const int64_t* piv_off,
+                           const int64_t* voff, T* x, int nrhs) {
+    const int th = 32 * std::min(8, (nrhs + kLuCols - 1) / kLuCols);
+    if (nmax <= 32) s_diag_lu<T, 1><<<nb, th, 0, s>>>(boxes, n, kt, LU, LU_off, piv, piv_off, voff, x, nrhs);
+    else if (nmax <= 64) s_diag_lu<T, 2><<<nb, th, 0, s>>>(boxes, n, kt, LU, LU_off, piv, piv_off, voff, x, nrhs);
+    else if (nmax <= 128) s_diag_lu<T, 4><<<nb, th, 0, s>>>(boxes, n, kt, LU, LU_off, piv, piv_off, voff, x, nrhs);
+    else if (nmax <= 256) s_diag_lu<T, 8><<<nb, th, 0, s>>>(boxes, n, kt, LU, LU_off, piv, piv_off, voff, x, nrhs);
     else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the solve"};
+}
+
+template <class T>
+static void launch_apply_q(int nb, int smem, cudaStream_t s, const int* boxes, const int* n, const T* Q,
+                           const int64_t* Q_off, const int64_t* voff, T* x, int nrhs, int trans) {
+    if (nrhs == 1) s_apply_q<T, 1><<<nb, 256, smem, s>>>(boxes, n, Q, Q_off, voff, x, nrhs, trans);
+    else s_apply_q<T, kRB><<<nb, 256, smem, s>>>(boxes, n, Q, Q_off, voff, x, nrhs, trans);
+}
+
+template <class T>
+static void launch_fwd_l(int nt, cudaStream_t s, const int* tbox, const int* tptr, const int* ci, const int* cpos,
+                         int cur, const int* colour, const int* n, const int* kt, const int* nb_ptr,
+                         const int* nbofs, const T* WL, const int64_t* WL_off, const int* WLld,
+                         const int64_t* voff, T* x, int nrhs) {
+    if (nrhs == 1)
+        s_fwd_l<T, 1><<<nt, 256, 0, s>>>(tbox, tptr, ci, cpos, cur, colour, n, kt, nb_ptr, nbofs, WL, WL_off, WLld,
+                                         voff, x, nrhs);
+    else
+        s_fwd_l<T, kRB><<<nt, 256, 0, s>>>(tbox, tptr, ci, cpos, cur, colour, n, kt, nb_ptr, nbofs, WL, WL_off,
+                                           WLld, voff, x, nrhs);
 }
 
 template <class T>
@@ -276,8 +388,14 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
     cudaStream_t s = stream;
     static bool smem_ready = false;
     if (!smem_ready) {
-        allow_smem(s_apply_q<T>);
+        allow_smem(s_apply_q<T, 1>);
+        allow_smem(s_apply_q<T, kRB>);
         allow_smem(s_diag<T>);
+        allow_smem(s_bwd_u<T, 8, 1>);
+        allow_smem(s_bwd_u<T, 8, 4>);
+        allow_smem(s_bwd_u<T, 4, 4>);
+        allow_smem(s_bwd_u<T, 2, 4>);
+        allow_smem(s_bwd_u<T, 1, 4>);
         smem_ready = true;
     }
     const Plan& P = A->plan;
@@ -306,25 +424,29 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
         const int qsm = nmax * nrhs * (int)sizeof(T);
         for (int c = 0; c < S.ncolour; ++c) {
             const int b0 = S.cbox_ptr[c], nb = S.cbox_ptr[c + 1] - b0;
-            s_apply_q<T><<<nb, 256, qsm, s>>>(S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
-                                              L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
-                                              vec[a].as<T>(), nrhs, 1);
+            launch_apply_q<T>(nb, qsm, s, S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
+                              L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs, 1);
             count_launch();
             const int t0 = S.fl_cptr[c], nt_ = S.fl_cptr[c + 1] - t0;
             if (nt_) {
-                s_fwd_l<T><<<nt_, 256, 0, s>>>(L.d_fl_tbox.as<int>() + t0, L.d_fl_tptr.as<int>() + t0,
-                                               L.d_fl_ci.as<int>(), L.d_fl_cpos.as<int>(), c,
-                                               L.d_colour.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(),
-                                               L.d_nb_ptr.as<int>(), L.d_nbofs.as<int>(), L.WL.as<T>(),
-                                               L.d_WL_off.as<int64_t>(), L.d_WLld.as<int>(),
-                                               L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
+                launch_fwd_l<T>(nt_, s, L.d_fl_tbox.as<int>() + t0, L.d_fl_tptr.as<int>() + t0,
+                                L.d_fl_ci.as<int>(), L.d_fl_cpos.as<int>(), c, L.d_colour.as<int>(),
+                                L.d_n.as<int>(), L.d_kt.as<int>(), L.d_nb_ptr.as<int>(), L.d_nbofs.as<int>(),
+                                L.WL.as<T>(), L.d_WL_off.as<int64_t>(), L.d_WLld.as<int>(),
+                                L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
                 count_launch();
             }
         }
         if (!S.skel_boxes.empty()) {
-            s_diag<T><<<(unsigned)S.skel_boxes.size(), 256, nmax * nrhs * (int)sizeof(T), s>>>(
-                L.d_skel_boxes.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(), L.DI.as<T>(),
-                L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
+            const unsigned nsk = (unsigned)S.skel_boxes.size();
+            if (tensor_schur)                      // explicit inverse (GEMV)
+                s_diag<T><<<nsk, 256, nmax * nrhs * (int)sizeof(T), s>>>(
+                    L.d_skel_boxes.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(), L.DI.as<T>(),
+                    L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
+            else
+                launch_diag_lu<T>(nmax, nsk, s, L.d_skel_boxes.as<int>(), L.d_n.as<int>(), L.d_kt.as<int>(),
+                                  L.LU.as<T>(), L.d_LU_off.as<int64_t>(), L.piv.as<int>(),
+                                  L.d_piv_off.as<int64_t>(), L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs);
             count_launch();
         }
         LevelRT& Pn = lv[a + 1];
@@ -376,9 +498,8 @@ void FactorImpl<T>::solve_dev(double* b, int nrhs, int64_t ldb) {
                             L.WU.as<T>(), L.d_WU_off.as<int64_t>(), L.d_voff.as<int64_t>(),
                             vec[a].as<T>(), nrhs);
             count_launch();
-            s_apply_q<T><<<nb, 256, qsm, s>>>(S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
-                                              L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(),
-                                              vec[a].as<T>(), nrhs, 0);
+            launch_apply_q<T>(nb, qsm, s, S.dev.cboxes.as<int>() + b0, L.d_n.as<int>(), L.Q.as<T>(),
+                              L.d_Q_off.as<int64_t>(), L.d_voff.as<int64_t>(), vec[a].as<T>(), nrhs, 0);
             count_launch();
         }
     }

@@ -242,3 +242,31 @@ def test_schur_pipeline_timeout_is_reported_and_context_survives(h):
     xt = h.colmajor(torch.zeros_like(bt))
     it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
     assert ok and berr <= BERR_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("name,over,eps", [CASES[4], CASES[5], CASES[9]], ids=[IDS[4], IDS[5], IDS[9]])
+def test_reduced_precision_layout_matches_oracle_under_forced_ranks(h, name, over, eps, prec):
+    """With the oracle's augmented ranks forced (opts.force_ranks), a float32 factor's
+    level sizes, ranks, colours, block pattern and prefix-sum offsets equal the
+    oracle's entry by entry, and the factor still refines to the float64 target."""
+    pb, A, b, Z0, x0 = oracle_solution(name, eps, 2, 1, **over)
+    ranks = [np.asarray([bx.kt for bx in lv.boxes], np.int32) for lv in Z0.levels]
+    M = h.h2_matrix_create(pb.A)
+    Z = h.h2_factor_create(M, eps, pb.norm_a, h.H2_PREC_FP32 if prec == "fp32" else h.H2_PREC_TF32X3,
+                           force_ranks=ranks)
+    st = h.h2_factor_stats_get(Z)
+    assert st["nlevels"] == len(Z0.levels) and st["top_size"] == sum(Z0.top_sizes)
+    for li, lv in enumerate(Z0.levels):
+        lay = h.h2_layout_get(Z, li)
+        assert np.array_equal(lay["sizes"], np.asarray(lv.sizes)), li
+        assert np.array_equal(lay["ranks"], ranks[li]), li
+        assert np.array_equal(lay["colour"], np.asarray(lv.colour, np.int32)), li
+        assert np.array_equal(lay["row_ptr"], lv.layout["row_ptr"]), li
+        assert np.array_equal(lay["col"], lv.layout["col"]), li
+        assert np.array_equal(lay["kind"], lv.layout["kind"].astype(np.int32)), li
+        assert np.array_equal(lay["offset"], lv.layout["offset"]), li
+    bt = h.colmajor(torch.from_numpy(b).cuda())
+    xt = h.colmajor(torch.zeros_like(bt))
+    it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
+    assert ok and berr <= BERR_TOL, (it, berr)
