@@ -60,6 +60,9 @@ def _args():
                         "(fp32) or on the tensor cores as split TF32 (tf32x3); auto = tf32x3 for the "
                         "sphere, fp32 for the uneven batch (whose ill-conditioned systems need the "
                         "more accurate factor)")
+    p.add_argument("--w-step", default="auto", choices=["auto", "triangular", "inverse"],
+                   help="how the mixed arm applies D_RR^-1 in W_U, W_L and the diagonal solve: "
+                        "auto = the library's default for the precision")
     p.add_argument("--nsys", type=int, default=64, help="uneven batch: number of systems")
     p.add_argument("--nmin", type=int, default=2048, help="uneven batch: smallest system")
     p.add_argument("--nmax", type=int, default=16384, help="uneven batch: largest system")
@@ -390,8 +393,11 @@ def run_ours(args, dist, rank, ws):
     if args.precision == "auto":
         args.precision = "fp32" if args.workload == "uneven" else "tf32x3"
     prec_mixed = h.H2_PREC_TF32X3 if args.precision == "tf32x3" else h.H2_PREC_FP32
+    wflag = {"auto": 0, "triangular": binding.H2_FLAG_W_TRIANGULAR, "inverse": binding.H2_FLAG_W_INVERSE}[args.w_step]
 
     def step(prec, flags=0):
+        if prec == prec_mixed:
+            flags |= wflag
         Z = h.h2_factor_create(M, w.tol, norm_arg, prec, stream=stream, flags=flags)
         x.zero_()
         it, berr, ok = h.h2_refine_solve(Z, M, b, x, BERR_TOL, MAXIT)
@@ -471,6 +477,7 @@ def run_ours(args, dist, rank, ws):
                        "precision": "float32 factor/solve" + (", Schur update on tcgen05 tensor cores as split "
                                      "TF32 (hi*hi + hi*lo + lo*hi)" if args.precision == "tf32x3" else "")
                                      + ", float64 top LU + refinement",
+                       "w_step": args.w_step,
                        "parallelism": (f"systems split over {ws} GPUs (LPT)" if uneven else f"replicas x{ws}"),
                        "l2": "inputs larger than L2 (matrix "
                        f"{sum(A.nbytes() for A in As) / 1e9:.1f} GB)", "setup_s": round(setup_s, 1),
@@ -509,7 +516,7 @@ def run_ours(args, dist, rank, ws):
             torch.cuda.synchronize()
             f0 = time.perf_counter()
             Mh = h.h2_matrix_create_batch(Ahs, stream=stream)
-            Z = h.h2_factor_create(Mh, w.tol, norm_arg, prec_mixed, stream=stream)
+            Z = h.h2_factor_create(Mh, w.tol, norm_arg, prec_mixed, stream=stream, flags=wflag)
             it, berr, ok = h.h2_refine_solve(Z, Mh, bh, xh, BERR_TOL, MAXIT)
             torch.cuda.synchronize()
             e2e.append(time.perf_counter() - f0)

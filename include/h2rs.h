@@ -196,6 +196,13 @@ typedef struct {
  * waits, with the full budget, for the MMAs it issued before freeing tensor memory);
  * the library stays usable afterwards */
 #define H2_FLAG_DEBUG_SHORT_WAIT 2
+/* h2_factor_opts.flags: how D_RR^-1 (Sec. 2.1, Eq. 2.1) is applied in W_U, W_L and the
+ * diagonal solve step.  By default H2_PREC_FP32 / H2_PREC_FP64 use triangular solves
+ * with the LU factors and H2_PREC_TF32X3 forms D_RR^-1 explicitly and applies it as
+ * GEMMs; these flags override the default (setting both is H2_ERR_ARG).  Triangular
+ * solves are the more accurate on ill-conditioned problems. */
+#define H2_FLAG_W_TRIANGULAR 4
+#define H2_FLAG_W_INVERSE 8
 
 /* kernel ids of h2_factor_stats.kernel_* */
 enum {

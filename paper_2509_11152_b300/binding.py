@@ -59,6 +59,8 @@ PHASES = ["augment", "project", "lu_trsm", "schur", "close", "top", "leaf_load",
 KERNELS = ["gather", "basis", "proj", "zero", "lu", "trsm", "schur", "close", "top", "load", "pack"]
 H2_FLAG_TIME_KERNELS = 1
 H2_FLAG_DEBUG_SHORT_WAIT = 2
+H2_FLAG_W_TRIANGULAR = 4
+H2_FLAG_W_INVERSE = 8
 
 # (name, restype, argtypes) of every exported entry point
 _SIGS = [

@@ -314,9 +314,10 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
         // One restarted flexible-GMRES cycle on A d = r, right-preconditioned by the
         // factor, classical Gram-Schmidt applied twice; float64.  The preconditioned
         // vectors z_j = M^-1 v_j are kept and d = Z y, so A Z = V H holds to float64
-        // rounding and the cycle's residual estimate is the true residual even though a
-        // reduced-precision solve is not exactly linear (forming d = M^-1 V y with a
-        // fresh solve instead would cap each cycle's gain at the solve's accuracy).
+        // rounding and the cycle's residual estimate is the true residual.  M^-1 is
+        // applied in float64 arithmetic over the stored factor (a fixed linear operator):
+        // a float32 solve of an ill-conditioned system has rounding errors near
+        // u_32 cond(A), which the Krylov space would have to absorb at every step.
         // Every channel (right-hand side of one system) has its own Krylov basis and
         // Hessenberg matrix, so a batch converges like its slowest system.  Used once
         // plain correction steps stop contracting (eps_lu * cond(A) near 1).
@@ -347,7 +348,7 @@ int h2_refine_solve(const h2_factor* Z, const h2_matrix* A, int32_t nrhs, const 
                 double* w = V + (size_t)(j + 1) * n * nrhs;
                 double* zj = Zb.as<double>() + (size_t)j * n * nrhs;
                 H2_CUDA_CHECK(cudaMemcpyAsync(zj, vj, vbytes, cudaMemcpyDeviceToDevice, s));
-                F.solve_dev(zj, nrhs, n);                                    // z_j = M^-1 v_j
+                F.solve_dev(zj, nrhs, n, true);                              // z_j = M^-1 v_j
                 matvec_dev(A->m, nrhs, zj, n, w, n, s);                       // A z_j
                 for (int pass = 0; pass < 2; ++pass) {
                     multidot_dev(V, w, j + 1, n, nrhs, seg, nseg, hd, s);

@@ -155,23 +155,49 @@ static void launch_pack(int npk, int c, cudaStream_t s, const LevelArgs<float>& 
     k_schur_pack<<<dim3(npk, 2), 256, 0, s>>>(ar, c, box, pos, off, pA, pB);
 }
 
-// W_U (left) / W_L by triangular solves, one CTA per (box, 64-line chunk)
-template <class T>
-static void launch_wtrsm(bool left, int nmax, int nblk, cudaStream_t s, const LevelArgs<T>& ar, const int* box,
-                         const int* chunk) {
-    if (left) {
-        if (nmax <= 32) k_wtrsm<T, true, 1><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else if (nmax <= 64) k_wtrsm<T, true, 2><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else if (nmax <= 128) k_wtrsm<T, true, 4><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else if (nmax <= 256) k_wtrsm<T, true, 8><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the triangular solves"};
+// W_U (left) / W_L by triangular solves: CTAs per box enough for about four per SM
+// (at most 8), the factors staged in shared memory when r_max^2 words fit
+template <class T, bool LEFT, int RU>
+static void launch_wtrsm_ru(int nmax, int nbmax, int nbx, cudaStream_t s, const LevelArgs<T>& ar,
+                            const int* boxes) {
+    static const int lim = std::min(raise_smem(k_wtrsm<T, LEFT, RU, true>), raise_smem(k_wtrsm<T, LEFT, RU, false>));
+    const size_t sm = wtrsm_smem<T>(nmax * nmax, nbmax);
+    const dim3 grid((unsigned)nbx, (unsigned)std::max(1, std::min(8, (4 * num_sms() + nbx - 1) / nbx)));
+    if (sm <= (size_t)lim) {
+        k_wtrsm<T, LEFT, RU, true><<<grid, 256, sm, s>>>(ar, boxes, nmax * nmax);
     } else {
-        if (nmax <= 32) k_wtrsm<T, false, 1><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else if (nmax <= 64) k_wtrsm<T, false, 2><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else if (nmax <= 128) k_wtrsm<T, false, 4><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else if (nmax <= 256) k_wtrsm<T, false, 8><<<nblk, 256, 0, s>>>(ar, box, chunk);
-        else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the triangular solves"};
+        const size_t sm0 = wtrsm_smem<T>(0, nbmax);
+        if (sm0 > (size_t)lim) throw Error{H2_ERR_ARG, "near field too large for the triangular solves"};
+        k_wtrsm<T, LEFT, RU, false><<<grid, 256, sm0, s>>>(ar, boxes, 0);
     }
+}
+
+template <class T, bool LEFT>
+static void launch_wtrsm(int nmax, int nbmax, int nbx, cudaStream_t s, const LevelArgs<T>& ar, const int* boxes) {
+    if (nmax <= 32) launch_wtrsm_ru<T, LEFT, 1>(nmax, nbmax, nbx, s, ar, boxes);
+    else if (nmax <= 64) launch_wtrsm_ru<T, LEFT, 2>(nmax, nbmax, nbx, s, ar, boxes);
+    else if (nmax <= 128) launch_wtrsm_ru<T, LEFT, 4>(nmax, nbmax, nbx, s, ar, boxes);
+    else if (nmax <= 256) launch_wtrsm_ru<T, LEFT, 8>(nmax, nbmax, nbx, s, ar, boxes);
+    else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the triangular solves"};
+}
+
+// D_RR^-1 from the LU factors, CTAs per box as for the triangular solves
+template <class T, int RU>
+static void launch_inverse_ru(int nmax, int nbx, cudaStream_t s, const LevelArgs<T>& ar, const int* boxes) {
+    static const int lim = raise_smem(k_inverse<T, RU, true>);
+    const size_t sm = (size_t)nmax * nmax * sizeof(T);
+    const dim3 grid((unsigned)nbx, (unsigned)std::max(1, std::min(8, (4 * num_sms() + nbx - 1) / nbx)));
+    if (sm <= (size_t)lim) k_inverse<T, RU, true><<<grid, 256, sm, s>>>(ar, boxes, nmax * nmax);
+    else k_inverse<T, RU, false><<<grid, 256, 0, s>>>(ar, boxes, 0);
+}
+
+template <class T>
+static void launch_inverse(int nmax, int nbx, cudaStream_t s, const LevelArgs<T>& ar, const int* boxes) {
+    if (nmax <= 32) launch_inverse_ru<T, 1>(nmax, nbx, s, ar, boxes);
+    else if (nmax <= 64) launch_inverse_ru<T, 2>(nmax, nbx, s, ar, boxes);
+    else if (nmax <= 128) launch_inverse_ru<T, 4>(nmax, nbx, s, ar, boxes);
+    else if (nmax <= 256) launch_inverse_ru<T, 8>(nmax, nbx, s, ar, boxes);
+    else throw Error{H2_ERR_ARG, "box size above 256 is not supported by the inverse"};
 }
 
 template <class T>
@@ -207,6 +233,11 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
     norm_a = o.norm_a;
     precision = o.precision;
     tensor_schur = o.precision == H2_PREC_TF32X3;
+    w_inverse = tensor_schur;
+    if (o.flags & H2_FLAG_W_TRIANGULAR) w_inverse = false;
+    if (o.flags & H2_FLAG_W_INVERSE) w_inverse = true;
+    H2_REQUIRE(!((o.flags & H2_FLAG_W_TRIANGULAR) && (o.flags & H2_FLAG_W_INVERSE)), H2_ERR_ARG,
+               "H2_FLAG_W_TRIANGULAR and H2_FLAG_W_INVERSE exclude each other");
     norm_sys.assign(A->H.nsys, o.norm_a);
     if (o.sys_norm_a)
         for (int z = 0; z < A->H.nsys; ++z) {
@@ -413,10 +444,8 @@ void FactorImpl<T>::setup_level(size_t a) {
 struct ColourWork {
     std::vector<int64_t> ybase, ylead, wbase;             // basis: per box
     std::vector<int64_t> scratch_need;                     // per colour (elements)
-    std::vector<int> smem_basis, w_in_smem, smem_gather, gather_pc, gather_vs, nmax;
-    // W_U / W_L: GEMM tiles (box, 64 x 64 tile; explicit inverse) or, for the triangular
-    // solves, (box, 64-line chunk) in wu_box / wu_mn
-    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;
+    std::vector<int> smem_basis, w_in_smem, smem_gather, gather_pc, gather_vs, nmax, nbmax;
+    std::vector<int> wu_box, wu_mn, wu_cptr, wl_box, wl_mn, wl_cptr;   // W_U / W_L GEMM tiles (TF32X3)
 };
 
 // Algorithmic flops and bytes of one level's phases (the roofline definitions of the
@@ -534,12 +563,7 @@ void FactorImpl<T>::run_level(size_t a) {
             kmax = std::max(kmax, L.k[i]);
             csz = std::max(csz, basis_chunk_elems(n));
             const int wide = L.Nsum[i] + n;          // bound of the width sum n_j + k~_i
-            if (!tensor_schur) {
-                for (int ch = 0; ch * 64 < wide; ++ch) {
-                    W.wu_box.push_back(i);
-                    W.wu_mn.push_back(ch);
-                }
-            } else {
+            if (w_inverse)                           // GEMM tiles (the triangular solves take a CTA per box)
                 for (int tm = 0; tm * 64 < n; ++tm)
                     for (int tn = 0; tn * 64 < wide; ++tn) {
                         W.wu_box.push_back(i);
@@ -547,7 +571,6 @@ void FactorImpl<T>::run_level(size_t a) {
                         W.wl_box.push_back(i);
                         W.wl_mn.push_back((tn << 16) | tm);
                     }
-            }
         }
         for (int q = S.cbox_ptr[c]; q < S.cbox_ptr[c + 1]; ++q) W.wbase[q] += ysum;   // after the Y^T rows
         W.wu_cptr.push_back((int)W.wu_box.size());
@@ -575,6 +598,12 @@ void FactorImpl<T>::run_level(size_t a) {
         W.smem_basis.push_back((int)(base + (in_sm ? wsm : 0)));
         W.smem_gather.push_back((int)gsm);
         W.nmax.push_back(nmax);
+        int nbm = 1;
+        for (int q = S.cbox_ptr[c]; q < S.cbox_ptr[c + 1]; ++q) {
+            const int i = S.cboxes[c][q - S.cbox_ptr[c]];
+            nbm = std::max(nbm, S.nb_ptr[i + 1] - S.nb_ptr[i]);
+        }
+        W.nbmax.push_back(nbm);
         W.scratch_need.push_back(ysum + (in_sm ? 0 : wsum));
     }
     stats.host_ms[0] += ht.lap();
@@ -696,17 +725,23 @@ void FactorImpl<T>::run_level(size_t a) {
         const size_t lu_sm = (size_t)W.nmax[c] * W.nmax[c] * sizeof(T);
         const int lu_in = lu_sm <= (size_t)smem_limits<T>().lu;
         kbegin(H2_K_LU);
-        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, S.dev.cboxes.as<int>() + b0, lu_in, tensor_schur ? 1 : 0);
+        k_lu<T><<<nbx, 256, lu_in ? lu_sm : 0, s>>>(ar, S.dev.cboxes.as<int>() + b0, lu_in, w_inverse ? 0 : 1);
         kend();
+        if (w_inverse) {                           // D_RR^-1 (counted with the LU)
+            H2_LAUNCHED();
+            kbegin(H2_K_LU);
+            launch_inverse<T>(W.nmax[c], nbx, s, ar, S.dev.cboxes.as<int>() + b0);
+            kend();
+        }
         H2_LAUNCHED();
         const int wu0 = W.wu_cptr[c], nwu = W.wu_cptr[c + 1] - wu0;
-        if (nwu && !tensor_schur) {
+        if (!w_inverse) {
             kbegin(H2_K_TRSM);
-            launch_wtrsm<T>(true, W.nmax[c], nwu, s, ar, d_wu_box.as<int>() + wu0, d_wu_mn.as<int>() + wu0);
+            launch_wtrsm<T, true>(W.nmax[c], W.nbmax[c], nbx, s, ar, S.dev.cboxes.as<int>() + b0);
             kend();
             H2_LAUNCHED();
             kbegin(H2_K_TRSM);
-            launch_wtrsm<T>(false, W.nmax[c], nwu, s, ar, d_wu_box.as<int>() + wu0, d_wu_mn.as<int>() + wu0);
+            launch_wtrsm<T, false>(W.nmax[c], W.nbmax[c], nbx, s, ar, S.dev.cboxes.as<int>() + b0);
             kend();
         } else if (nwu) {
             kbegin(H2_K_TRSM);

@@ -44,7 +44,9 @@ struct FactorBase {
     virtual ~FactorBase() = default;
     virtual void factorize() = 0;
     // x <- A^-1 b in place; b is float64, device, n x nrhs with leading dimension ldb
-    virtual void solve_dev(double* b, int nrhs, int64_t ldb) = 0;
+    // x = M^-1 b in place; wide: float64 vectors and arithmetic whatever the factor's
+    // storage precision (a fixed linear operator for Krylov refinement)
+    virtual void solve_dev(double* b, int nrhs, int64_t ldb, bool wide = false) = 0;
     h2_factor_stats stats{};
     int64_t bytes_now = 0;
     int precision = H2_PREC_FP64;
@@ -61,6 +63,7 @@ template <class T>
 struct FactorImpl : FactorBase {
     double eps_lu = 0, norm_a = 0;
     bool tensor_schur = false;                // H2_PREC_TF32X3: Schur update on tcgen05
+    bool w_inverse = false;                   // D_RR^-1 formed explicitly (W_U, W_L, diagonal solve)
     std::vector<int> force;                   // debug: forced ranks of every level (concatenated)
     std::vector<int64_t> force_off;           // offset of each level in `force`
     std::vector<LevelRT> lv;
@@ -86,7 +89,9 @@ struct FactorImpl : FactorBase {
     FactorImpl(const MatrixObj* A_, const h2_factor_opts& o);
     ~FactorImpl() override;
     void factorize() override;
-    void solve_dev(double* b, int nrhs, int64_t ldb) override;
+    void solve_dev(double* b, int nrhs, int64_t ldb, bool wide = false) override;
+    template <class V>
+    void solve_in(double* b, int nrhs, int64_t ldb);
 
    private:
     void setup_level(size_t a);

@@ -911,12 +911,12 @@ __global__ void k_zero_redundant(LevelArgs<T> a, const int* __restrict__ z_box,
 // Alg. 2 partial factorisation (Sec. 2.1, Eq. 2.1): LU with partial pivoting of
 // D_RR = D_ii[0:r, 0:r] (first maximal |value| wins), P D_RR = L U stored as one r x r
 // column-major matrix; the interchanges are replaced in `piv` by the row permutation
-// they compose to, (P y)[q] = y[perm[q]].  Then, in DI (offsets of Q):
-//   inverse != 0: the explicit inverse D_RR^-1 (W_U / W_L as GEMMs, GEMV solves);
-//   inverse == 0: the transposed factors (L U)^T, for the triangular solves of W_L.
+// they compose to, (P y)[q] = y[perm[q]].  With `transposed`, DI (offsets of Q) receives
+// (L U)^T for the triangular solves of W_L; otherwise DI is scratch here and k_inverse
+// fills it with D_RR^-1.
 template <class T>
 __global__ void __launch_bounds__(256)
-k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem, int inverse) {
+k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem, int transposed) {
     const int i = boxes[blockIdx.x];
     const int n = a.n[i];
     const int r = n - a.kt[i];
@@ -960,14 +960,16 @@ k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem, int inverse) {
                 if (rv[w] > bb || (rv[w] == bb && ri[w] < bx)) { bb = rv[w]; bx = ri[w]; }
             piv_s = bx;
             pv_s = bb;
-            pv[j] = bx;
         }
         __syncthreads();
         const int p = piv_s;
+        // a column without a finite non-zero entry (all NaN leaves bx = INT_MAX) keeps
+        // pv[j] = j: the interchanges stored are always valid row indices
         if (!(pv_s > T(0)) || !t_finite(pv_s)) {
             if (tid == 0) dev_fail(a.status, H2_ERR_SINGULAR, a.level, i);
             return;
         }
+        if (tid == 0) pv[j] = p;
         if (p != j)
             for (int c = tid; c < r; c += blockDim.x) {
                 const T t0 = W[j + (int64_t)c * r];
@@ -1002,35 +1004,53 @@ k_lu(LevelArgs<T> a, const int* __restrict__ boxes, int in_smem, int inverse) {
         for (int q = 0; q < 4; ++q)
             if (tid + q * 256 < r) pv[tid + q * 256] = my[q];
     }
-    if (!inverse) {                                    // (L U)^T: X[c + q r] = G[q + c r]
+    if (transposed)                                    // (L U)^T: X[c + q r] = G[q + c r]
         for (int x = tid; x < r * r; x += blockDim.x) X[x / r + (int64_t)(x % r) * r] = W[x];
-        return;
+}
+
+// D_RR^-1 = U^-1 L^-1 P formed column by column from the LU factors of k_lu: column c
+// is the triangular solve of P e_c ((P e_c)[q] = 1 where perm[q] = c), 8 columns per warp
+// (lu_solve.cuh), the factors staged in shared memory when SM (the first gsz words).
+// gridDim.y CTAs per box (blockIdx.x = box of the colour).  The inverse feeds W_U / W_L
+// as GEMMs and the diagonal solve step (H2_PREC_TF32X3 by default).
+template <class T, int RU, bool SM>
+__global__ void __launch_bounds__(256)
+k_inverse(LevelArgs<T> a, const int* __restrict__ boxes, int gsz) {
+    const int i = boxes[blockIdx.x];
+    const int r = a.n[i] - a.kt[i];
+    if (r <= 0) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const T* G = a.LU + a.LU_off[i];
+    if (SM) {
+        T* Gs = reinterpret_cast<T*>(sm_raw);
+        for (int x = threadIdx.x; x < r * r && x < gsz; x += blockDim.x) Gs[x] = G[x];
+        __syncthreads();
+        G = Gs;
     }
-    // D_RR^-1 = U^-1 L^-1 P: row q of P is e_{perm[q]}, so column perm[q] of the
-    // permuted identity has its one in row q; then the two triangular solves (column
-    // parallel; the inverse feeds W_U / W_L as GEMMs and the diagonal solves)
-    for (int x = tid; x < r * r; x += blockDim.x) X[x] = T(0);
-    __syncthreads();
-    for (int q = 0; q < 4; ++q)
-        if (tid + q * 256 < r) X[(tid + q * 256) + (int64_t)my[q] * r] = T(1);
-    __syncthreads();
-    for (int j = 0; j < r; ++j) {                      // L (unit lower)
-        const int m = r - j - 1;
-        for (int x = tid; x < m * r; x += blockDim.x) {
-            const int rr = j + 1 + x % m, c = x / m;
-            X[rr + (int64_t)c * r] -= W[rr + (int64_t)j * r] * X[j + (int64_t)c * r];
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int* perm = a.piv + a.piv_off[i];
+    int pq[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+        const int q = lane + 32 * u;
+        const int pv = q < r ? perm[q] : -1;
+        pq[u] = (unsigned)pv < (unsigned)r ? pv : -1;
     }
-    for (int j = r - 1; j >= 0; --j) {                 // U
-        const T d = W[j + (int64_t)j * r];
-        for (int c = tid; c < r; c += blockDim.x) X[j + (int64_t)c * r] /= d;
-        __syncthreads();
-        for (int x = tid; x < j * r; x += blockDim.x) {
-            const int rr = x % j, c = x / j;
-            X[rr + (int64_t)c * r] -= W[rr + (int64_t)j * r] * X[j + (int64_t)c * r];
+    T* X = a.DI + a.Q_off[i];
+    for (int c0 = kLuCols * (blockIdx.y * nw + (threadIdx.x >> 5)); c0 < r; c0 += kLuCols * nw * gridDim.y) {
+        T x[RU][kLuCols];
+#pragma unroll
+        for (int c = 0; c < kLuCols; ++c)
+#pragma unroll
+            for (int u = 0; u < RU; ++u) x[u][c] = pq[u] == c0 + c ? T(1) : T(0);
+        lu_solve_warp(x, G, r, lane);
+#pragma unroll
+        for (int c = 0; c < kLuCols; ++c) {
+            if (c0 + c >= r) break;
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                if (lane + 32 * u < r) X[lane + 32 * u + (int64_t)(c0 + c) * r] = x[u][c];
         }
-        __syncthreads();
     }
 }
 
@@ -1140,59 +1160,127 @@ k_wgemm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w
 // precision would cost refinement steps on ill-conditioned problems:
 //   W_U^i = U^-1 L^-1 P [D_{i_R, j} ...]                     (LEFT)
 //   W_L^i = [D_{j, i_R}; ...] U^-1 L^-1 P, via W_L^T = P^T L^-T U^-T [...]^T  (!LEFT)
-// One CTA per (box, 64 lines of the operand), each warp 8 lines as the right-hand sides
-// of lu_solve.cuh (registers, no barrier after the line lookup).  RU = ceil(r_max / 32).
-template <class T, bool LEFT, int RU>
+// gridDim.y CTAs per box (blockIdx.x = box of the colour).  Each stages the factors (LU,
+// or its transpose for W_L) in shared memory when SM (the first gsz words), and a table
+// of the operand's segments (one per neighbour j != i, then i's skeleton part: base,
+// line and entry strides, first line, length, prefix of 8-line groups).  Its warps then
+// take the 8-line groups in turn (every gridDim.y * 8-th) as the right-hand sides of
+// lu_solve.cuh (registers).  RU = ceil(r_max / 32).
+template <class T, bool LEFT, int RU, bool SM>
 __global__ void __launch_bounds__(256)
-k_wtrsm(LevelArgs<T> a, const int* __restrict__ w_box, const int* __restrict__ w_chunk) {
-    constexpr int CW = 8 * kLuCols;
-    __shared__ const T* gptr[CW];
-    __shared__ int64_t gld[CW];
-    const int i = w_box[blockIdx.x];
-    const int c0 = w_chunk[blockIdx.x] * CW;
-    const int n = a.n[i], kt = a.kt[i], r = n - kt, nt = a.Nsum[i] + kt;
-    if (r <= 0 || c0 >= nt) return;
-    const int tid = threadIdx.x, lane = tid & 31, cb = c0 + kLuCols * (tid >> 5);
-    if (tid < CW) w_line<T, LEFT>(a, i, c0 + tid, gptr[tid], gld[tid]);
+k_wtrsm(LevelArgs<T> a, const int* __restrict__ boxes, int gsz) {
+    const int i = boxes[blockIdx.x];
+    const int n = a.n[i], kt = a.kt[i], r = n - kt, ns = a.Nsum[i];
+    if (r <= 0) return;
+    const int p0 = a.nb_ptr[i], np = a.nb_ptr[i + 1] - p0;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    unsigned char* tb = sm_raw + ((size_t)gsz * sizeof(T) + 15) / 16 * 16;
+    const T** sbase = reinterpret_cast<const T**>(tb);             // np + 1 segments
+    int* sofs = reinterpret_cast<int*>(sbase + np + 1);             // first line (column of W_U)
+    int* slen = sofs + np + 1;                                       // lines
+    int* sls = slen + np + 1;                                        // stride between lines
+    int* ses = sls + np + 1;                                         // stride between a line's entries
+    int* sgrp = ses + np + 1;                                        // prefix of 8-line groups, np + 2
+    for (int t = threadIdx.x; t <= np; t += blockDim.x) {
+        if (t < np) {
+            const int p = p0 + t, j = a.nb_col[p];
+            sbase[t] = a.blk + a.blk_off[LEFT ? a.nb_blk[p] : a.nb_blkT[p]];
+            sofs[t] = a.nbofs[p];
+            slen[t] = j == i ? 0 : a.n[j];                           // i's own columns: the last segment
+            sls[t] = LEFT ? n : 1;
+            ses[t] = LEFT ? 1 : a.n[j];
+        } else {
+            const T* Dii = a.blk + a.blk_off[a.diag_blk[i]];
+            sbase[t] = LEFT ? Dii + (int64_t)r * n : Dii + r;
+            sofs[t] = ns;
+            slen[t] = kt;
+            sls[t] = LEFT ? n : 1;
+            ses[t] = LEFT ? 1 : n;
+        }
+    }
+    const T* G = LEFT ? a.LU + a.LU_off[i] : a.DI + a.Q_off[i];
+    if (SM) {
+        T* Gs = reinterpret_cast<T*>(sm_raw);
+        for (int x = threadIdx.x; x < r * r; x += blockDim.x) Gs[x] = G[x];
+        G = Gs;
+    }
     __syncthreads();
-    if (cb >= nt) return;                          // warp-uniform
+    if (threadIdx.x < 32) {                                          // group prefix (warp scan)
+        int carry = 0;
+        for (int t0 = 0; t0 <= np; t0 += 32) {
+            const int t = t0 + threadIdx.x;
+            int v = t <= np ? (slen[t] + kLuCols - 1) / kLuCols : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if ((int)threadIdx.x >= o) v += u;
+            }
+            if (t <= np) sgrp[t + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (threadIdx.x == 0) sgrp[0] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int* perm = a.piv + a.piv_off[i];
     int pq[RU];
 #pragma unroll
-    for (int u = 0; u < RU; ++u) pq[u] = (lane + 32 * u < r) ? perm[lane + 32 * u] : 0;
-    T x[RU][kLuCols];
+    for (int u = 0; u < RU; ++u) {                     // row permutation, bounds-checked
+        const int q = lane + 32 * u;
+        const int pv = q < r ? perm[q] : 0;
+        pq[u] = (unsigned)pv < (unsigned)r ? pv : 0;
+    }
+    const int64_t ldl = a.WLld[i];
+    const int ngrp = sgrp[np + 1];
+    for (int g = blockIdx.y * nw + (threadIdx.x >> 5); g < ngrp; g += nw * gridDim.y) {
+        int lo = 0, hi = np;                           // last segment with sgrp <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sgrp[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const int l0 = (g - sgrp[lo]) * kLuCols;       // first line of the group in the segment
+        const int nl = min(kLuCols, slen[lo] - l0);
+        const int c0 = sofs[lo] + l0;                  // its column of W_U (row of W_L)
+        const T* src0 = sbase[lo] + (int64_t)l0 * sls[lo];
+        const int64_t ls = sls[lo], es = ses[lo];
+        T x[RU][kLuCols];
 #pragma unroll
-    for (int c = 0; c < kLuCols; ++c) {
-        const T* src = gptr[cb - c0 + c];
-        const int64_t ld = gld[cb - c0 + c];
+        for (int c = 0; c < kLuCols; ++c)
 #pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            const int q = lane + 32 * u;
-            x[u][c] = (src && q < r) ? src[(int64_t)(LEFT ? pq[u] : q) * ld] : T(0);
+            for (int u = 0; u < RU; ++u) {
+                const int q = lane + 32 * u;
+                x[u][c] = (c < nl && q < r) ? src0[c * ls + (int64_t)(LEFT ? pq[u] : q) * es] : T(0);
+            }
+        if (LEFT) {
+            lu_solve_warp(x, G, r, lane);
+#pragma unroll
+            for (int c = 0; c < kLuCols; ++c) {
+                if (c >= nl) break;
+                T* out = a.WU + a.WU_off[i] + (int64_t)(c0 + c) * r;
+#pragma unroll
+                for (int u = 0; u < RU; ++u)
+                    if (lane + 32 * u < r) out[lane + 32 * u] = x[u][c];
+            }
+        } else {
+            lu_solve_t_warp(x, G, r, lane);
+#pragma unroll
+            for (int c = 0; c < kLuCols; ++c) {
+                if (c >= nl) break;
+                T* out = a.WL + a.WL_off[i] + (c0 + c);
+#pragma unroll
+                for (int u = 0; u < RU; ++u)
+                    if (lane + 32 * u < r) out[(int64_t)pq[u] * ldl] = x[u][c];
+            }
         }
     }
-    if (LEFT) {
-        lu_solve_warp<T, RU>(x, a.LU + a.LU_off[i], r, lane);
-#pragma unroll
-        for (int c = 0; c < kLuCols; ++c) {
-            if (cb + c >= nt) break;
-            T* out = a.WU + a.WU_off[i] + (int64_t)(cb + c) * r;
-#pragma unroll
-            for (int u = 0; u < RU; ++u)
-                if (lane + 32 * u < r) out[lane + 32 * u] = x[u][c];
-        }
-    } else {
-        lu_solve_t_warp<T, RU>(x, a.DI + a.Q_off[i], r, lane);
-        const int64_t ld = a.WLld[i];
-#pragma unroll
-        for (int c = 0; c < kLuCols; ++c) {
-            if (cb + c >= nt) break;
-            T* out = a.WL + a.WL_off[i] + (cb + c);
-#pragma unroll
-            for (int u = 0; u < RU; ++u)
-                if (lane + 32 * u < r) out[(int64_t)pq[u] * ld] = x[u][c];
-        }
-    }
+}
+
+// shared memory of k_wtrsm: gsz factor words, then the segment table of up to nbmax + 1
+// segments
+template <class T>
+__host__ __device__ inline size_t wtrsm_smem(int gsz, int nbmax) {
+    return ((size_t)gsz * sizeof(T) + 15) / 16 * 16 + (size_t)(nbmax + 1) * (sizeof(void*) + 4 * sizeof(int)) +
+           (size_t)(nbmax + 2) * sizeof(int);
 }
 
 // ================================================================== Schur update
@@ -1731,14 +1819,14 @@ k_top_panel(const TopSys* __restrict__ tops, int64_t j0, int nb, DevStatus* st) 
                 if (rv[w] > bb || (rv[w] == bb && ri[w] < bx)) { bb = rv[w]; bx = ri[w]; }
             psel = bx;
             pval = bb;
-            piv[j] = (int)bx;
         }
         __syncthreads();
-        if (!(pval > 0.0) || !isfinite(pval)) {
+        if (!(pval > 0.0) || !isfinite(pval)) {              // piv[j] stays unset (checked by its readers)
             if (tid == 0) dev_fail(st, H2_ERR_SINGULAR, -1, (int)j);
             return;
         }
         const int64_t p = psel;
+        if (tid == 0) piv[j] = (int)p;
         if (p != j)
             for (int c = tid; c < jb; c += blockDim.x) {
                 const double t0 = A[j + (j0 + c) * nt];

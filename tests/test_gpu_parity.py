@@ -125,6 +125,50 @@ def test_fp32_factor_with_refinement(h, name, over, eps, prec):
     assert np.mean(lay["ranks"] == r0) > 0.9
 
 
+W_CASES = [CASES[0], CASES[4], CASES[5], CASES[9]]       # cov2d, sphere, gauss3d (ragged), lru3d (200-point boxes)
+
+
+@pytest.mark.parametrize("prec,flag", [("fp64", "inverse"), ("fp32", "inverse"), ("tf32x3", "triangular")])
+@pytest.mark.parametrize("name,over,eps", W_CASES, ids=[f"{c[0]}-{c[1].get('n', 'full')}" for c in W_CASES])
+def test_w_step_override_matches_oracle(h, name, over, eps, prec, flag):
+    """The non-default application of D_RR^-1 (explicit inverse for FP64 / FP32,
+    triangular solves for TF32X3): same bars as the default paths."""
+    from paper_2509_11152_b300 import binding
+    pb, A, b, Z0, x0 = oracle_solution(name, eps, 2, 1, **over)
+    M = h.h2_matrix_create(pb.A)
+    fl = binding.H2_FLAG_W_INVERSE if flag == "inverse" else binding.H2_FLAG_W_TRIANGULAR
+    p = {"fp64": h.H2_PREC_FP64, "fp32": h.H2_PREC_FP32, "tf32x3": h.H2_PREC_TF32X3}[prec]
+    Z = h.h2_factor_create(M, eps, pb.norm_a, p, flags=fl)
+    if prec == "fp64":
+        x = h.colmajor(torch.from_numpy(b).cuda())
+        h.h2_solve(Z, x)
+        rel = np.linalg.norm(x.cpu().numpy() - x0) / np.linalg.norm(x0)
+        assert rel <= FP64_TOL, rel
+        lay = h.h2_layout_get(Z, 0)
+        assert np.array_equal(lay["ranks"], np.asarray([bx.kt for bx in Z0.levels[0].boxes]))
+        return
+    bt = h.colmajor(torch.from_numpy(b).cuda())
+    xt = h.colmajor(torch.zeros_like(bt))
+    it, berr, ok = h.h2_refine_solve(Z, M, bt, xt, BERR_TOL, 30)
+    x = xt.cpu().numpy()
+    xd = dense_solution(name, 2, 1, **over)
+    e_ref = np.linalg.norm(x - xd) / np.linalg.norm(xd)
+    msg = f"{name} {prec} {flag}: {it} corrections, berr {berr:.2e}, refined vs exact {e_ref:.2e}"
+    print(msg)
+    assert ok and berr <= BERR_TOL, msg
+    nw, _ = dense.backward_error(A, x, b, pb.norm_a)
+    assert nw <= BERR_TOL, (nw, msg)
+
+
+def test_w_step_flags_exclude_each_other(h):
+    from paper_2509_11152_b300 import binding
+    pb = problem("cov2d", n=1024, leaf=32)
+    M = h.h2_matrix_create(pb.A)
+    with pytest.raises(Exception):
+        h.h2_factor_create(M, 1e-8, pb.norm_a, h.H2_PREC_FP32,
+                           flags=binding.H2_FLAG_W_INVERSE | binding.H2_FLAG_W_TRIANGULAR)
+
+
 @pytest.mark.parametrize("name,over", [("cov2d", dict(n=1024, leaf=32)), ("sphere", dict(n=4096, leaf=64)),
                                        ("gauss3d", dict(n=1500, leaf=32))])
 def test_matvec_matches_oracle(h, name, over):

@@ -1,6 +1,7 @@
-"""Sharding of the uneven batch over ranks: LPT partition properties, and a
-world-size-2 gloo run in which each rank takes its share and only the step time is
-reduced (no data-path collective)."""
+"""Sharding of the uneven batch over ranks: LPT partition properties, and world-size-2
+gloo runs in which each rank takes its share and only the step time is reduced (no
+data-path collective); in the second, each rank factorises and solves its share of
+small Gaussian-kernel systems (the oracle stands in for the GPU on the CPU runner)."""
 import os
 import socket
 
@@ -66,3 +67,49 @@ def test_two_gloo_ranks_take_disjoint_shares():
     assert sorted(shares[0] + shares[1]) == list(range(len(sizes)))
     loads = [sum(sizes[i] for i in s) for s in shares]
     assert out[0][2] == out[1][2] == max(loads)
+
+
+def _solve_worker(rank, ws, port, sizes, q):
+    import time
+
+    import numpy as np
+
+    from conftest import problem
+    from h2gen import rhs
+    from oracle import dense, rs
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    mine = lpt_partition(sizes, ws)[rank]
+    t0 = time.perf_counter()
+    errs = []
+    for s in mine:
+        pb = problem("gauss3d", n=sizes[s], leaf=32, seed=s)
+        A = pb.A.numpy()
+        b = rhs(A.n, 2, seed=s)
+        x = rs.solve(rs.factorize(A, 1e-10, pb.norm_a), b)
+        xd = np.linalg.solve(dense.expand(A), b)
+        errs.append(float(np.linalg.norm(x - xd) / np.linalg.norm(xd)))
+    mine_t = time.perf_counter() - t0
+    t = torch.tensor([mine_t], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q.put((rank, mine, mine_t, float(t.item()), errs))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_solve_their_shares():
+    sizes = [700, 300, 900, 500, 400, 600]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_solve_worker, args=(r, 2, port, sizes, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    shares = [o[1] for o in out]
+    assert sorted(shares[0] + shares[1]) == list(range(len(sizes)))
+    assert all(len(o[4]) == len(o[1]) and max(o[4], default=0.0) <= 1e-6 for o in out), out
+    assert out[0][3] == out[1][3] == max(out[0][2], out[1][2])
