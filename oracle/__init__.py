@@ -9,8 +9,9 @@ Parity pins (tests/test_oracle_pins.py): dense Gaussian elimination with zero
 truncation (seven kernel families, including an indefinite oscillatory one), dense LU
 in the no-admissible-block case, slogdet of the factors, backward error against the
 tolerance, symmetry of the working blocks, colouring validity, brute-force layouts,
-the paper's projection identities, linear growth of the factor memory, and the
-augmentation variants and SVD driver fallback.  Unpinned: the individual singular vectors, the
+the paper's projection identities, near-linear growth of the factor memory, the
+operation count and the one-thread time, and the augmentation variants and SVD driver
+fallback.  Unpinned: the individual singular vectors, the
 complement bases and the intermediate blocks at a positive tolerance (they are
 fixed only up to orthogonal changes of basis).
 """
