@@ -66,6 +66,11 @@ def _args():
     p.add_argument("--nsys", type=int, default=64, help="uneven batch: number of systems")
     p.add_argument("--nmin", type=int, default=2048, help="uneven batch: smallest system")
     p.add_argument("--nmax", type=int, default=16384, help="uneven batch: largest system")
+    p.add_argument("--mem-per-point-kb", type=float, default=240.0,
+                   help="uneven batch: estimated device memory per point (H^2 data held twice, "
+                        "factor and working arrays) for the sub-batch split")
+    p.add_argument("--mem-budget-gb", type=float, default=0.0,
+                   help="uneven batch: device memory a sub-batch may use (0 = 85%% of the GPU's)")
     p.add_argument("--matrix-cache", default="", help="load the H^2 matrix from this .npz if it exists, "
                    "else build and save it there (lets a profiler run skip the construction)")
     return p.parse_args()
@@ -366,6 +371,97 @@ def _oracle_err(h, sample, prec, tol):
 
 
 # ------------------------------------------------------------------ our arm
+def _subbatches(args, rank, ws):
+    """The uneven batch's systems of this rank split into sub-batches that fit the GPU
+    (one bin when the whole share fits), with their sizes."""
+    import torch
+    from h2gen import uneven_sizes
+    from paper_2509_11152_b300.shard import lpt_partition, memory_bins
+    sizes = uneven_sizes(args.nsys, args.nmin, args.nmax)
+    mine = lpt_partition(sizes, ws)[rank]
+    budget = args.mem_budget_gb * 1e9 or 0.85 * torch.cuda.get_device_properties(0).total_memory
+    cost = [sizes[s] * args.mem_per_point_kb * 1e3 for s in mine]
+    return sizes, [[mine[k] for k in b] for b in memory_bins(cost, budget)]
+
+
+def run_subbatched(args, dist, rank, ws, sizes, bins):
+    """The uneven batch when one rank's share does not fit the GPU: its sub-batches are
+    built, factorised and refined in turn (construction untimed), each timed with CUDA
+    events over the same warm-up / steps as the whole-batch path; value = the sum of the
+    sub-batches' step times (one pass over every system), max over ranks."""
+    import torch
+    from h2gen import make_problem
+    import paper_2509_11152_b300 as h
+    from paper_2509_11152_b300 import binding
+
+    dev_index = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev_index)
+    if args.precision == "auto":
+        args.precision = "fp32"
+    prec = h.H2_PREC_TF32X3 if args.precision == "tf32x3" else h.H2_PREC_FP32
+    wflag = {"auto": 0, "triangular": binding.H2_FLAG_W_TRIANGULAR, "inverse": binding.H2_FLAG_W_INVERSE}[args.w_step]
+    stream = torch.cuda.current_stream().cuda_stream
+    total, setup_s, launches, refin = 0.0, 0.0, 0, []
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    for b in bins:
+        t0 = time.perf_counter()
+        pbs = [make_problem("gauss3d", device="cuda", n=sizes[s], seed=s) for s in b]
+        setup_s += time.perf_counter() - t0
+        w = pbs[0].workload
+        nrhs = args.nrhs or w.nrhs
+        M = h.h2_matrix_create_batch([pb.A for pb in pbs])
+        norms = [pb.norm_a for pb in pbs]
+        n_tot = sum(pb.A.n for pb in pbs)
+        del pbs
+        torch.cuda.empty_cache()
+        bv = h.colmajor(_rhs(n_tot, nrhs, "cuda"))
+        x = h.colmajor(torch.zeros_like(bv))
+
+        def step():
+            Z = h.h2_factor_create(M, w.tol, norms, prec, stream=stream, flags=wflag)
+            x.zero_()
+            res = h.h2_refine_solve(Z, M, bv, x, BERR_TOL, MAXIT)
+            del Z
+            return res
+
+        for _ in range(max(args.warmup, 0)):
+            step()
+        torch.cuda.synchronize()
+        _barrier(dist)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = binding.lib().h2_kernel_launch_count()
+        e0.record()
+        for _ in range(args.steps):
+            it, berr, ok = step()
+        e1.record()
+        torch.cuda.synchronize()
+        launches += binding.lib().h2_kernel_launch_count() - l0
+        total += e0.elapsed_time(e1) / 1e3 / args.steps
+        refin.append({"systems": len(b), "points": n_tot, "iters": it, "berr": berr, "converged": ok})
+        del M, bv, x
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    value = _max_over_ranks(dist, total)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"uneven batch: {args.nsys} gauss3d systems, N log-uniform in "
+                                       f"[{args.nmin}, {args.nmax}] (total {sum(sizes)}), run as "
+                                       f"{len(bins)} sub-batches on rank 0",
+                           "precision": args.precision, "w_step": args.w_step,
+                           "parallelism": f"systems split over {ws} GPUs (LPT), sub-batches by memory",
+                           "l2": "inputs larger than L2", "setup_s": round(setup_s, 1)},
+                "refinement": {"sub_batches": refin, "converged": all(r["converged"] for r in refin)},
+                "clocks": clk, "gpu_launches": int(launches),
+                "roofline": None, "e2e": None,
+                "note": "sub-batched run: no per-kernel roofline, e2e or CPU baseline (the whole-batch path "
+                        "reports them)"}
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, dist, rank, ws):
     import torch
     from paper_2509_11152_b300 import build
@@ -375,6 +471,10 @@ def run_ours(args, dist, rank, ws):
 
     dev_index = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev_index)
+    if args.workload == "uneven":
+        sizes, bins = _subbatches(args, rank, ws)
+        if len(bins) > 1:
+            return run_subbatched(args, dist, rank, ws, sizes, bins)
     t0 = time.perf_counter()
     pbs, desc = _problems(args, "cuda", rank, ws)
     As = [pb.A for pb in pbs]

@@ -61,3 +61,22 @@ def test_reference_arm_on_a_lattice_family_rounds_the_size():
     assert r.returncode == 0, r.stderr[-2000:]
     line = _json_lines(r.stdout)[-1]
     assert "helmholtz3d N=4913" in line["config"]["workload"] and "N=4913" in line["cpu_baseline"]["sample"]
+
+
+def test_uneven_batch_sub_batches_fit_the_budget():
+    """The sub-batch split of the uneven batch (host logic): the default batch fits one
+    GPU in one piece, the full-size batch splits into pieces within the budget."""
+    import argparse
+    import bench
+    from h2gen import uneven_sizes
+    base = dict(nsys=64, nmin=2048, mem_per_point_kb=240.0, mem_budget_gb=245.0)
+    sizes, bins = bench._subbatches(argparse.Namespace(nmax=16384, **base), 0, 1)
+    assert len(bins) == 1 and sorted(bins[0]) == list(range(64))
+    sizes, bins = bench._subbatches(argparse.Namespace(nmax=131072, **base), 0, 1)
+    assert sizes == uneven_sizes(64, 2048, 131072)
+    assert len(bins) >= 2 and sorted(i for b in bins for i in b) == list(range(64))
+    assert all(sum(sizes[i] for i in b) * 240e3 <= 245e9 for b in bins)
+    # two ranks: each rank's share is split on its own
+    _, b0 = bench._subbatches(argparse.Namespace(nmax=131072, **base), 0, 2)
+    _, b1 = bench._subbatches(argparse.Namespace(nmax=131072, **base), 1, 2)
+    assert sorted(i for b in b0 + b1 for i in b) == list(range(64))

@@ -33,6 +33,26 @@ def test_lpt_small_cases():
         lpt_partition([1], 0)
 
 
+def test_memory_bins_fit_and_cover():
+    from h2gen import uneven_sizes
+    from paper_2509_11152_b300.shard import memory_bins
+    n = uneven_sizes(64, 2048, 131072)
+    for cap in (max(n), 2.5 * max(n), sum(n) / 3, sum(n)):
+        bins = memory_bins(n, cap)
+        flat = sorted(i for b in bins for i in b)
+        assert flat == list(range(len(n)))
+        assert all(sum(n[i] for i in b) <= cap for b in bins)
+        # first fit decreasing never needs more than 11/9 OPT + 1 bins; OPT >= sum / cap
+        assert len(bins) <= 11 / 9 * (sum(n) / cap) + 2
+    assert memory_bins(n, sum(n)) == [list(range(len(n)))]
+    assert memory_bins([5, 4, 3, 3, 3], 9) == [[0, 1], [2, 3, 4]]
+    assert memory_bins([], 1.0) == []
+    with pytest.raises(ValueError):
+        memory_bins([1, 10], 5)
+    with pytest.raises(ValueError):
+        memory_bins([1], 0)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
