@@ -130,10 +130,18 @@ def _augment(V, Frow, eps_fill, method="qr"):
 
     method "qr" (Sec. 2.1, the second approach, the one the paper uses): QR of Y^T,
     SVD of R, keep sigma > eps_fill.
-    method "gram" (Sec. 2.1, the first approach; named again in the conclusions as
+    method "gram" (Sec. 2.1, the first approach; named again in Sec. 3's scaling discussion as
     trading accuracy for speed): the eigendecomposition of the Gram matrix Y Y^T, keep
     lambda > eps_fill^2.  The same subspace as "qr" while the kept sigma are well above
-    sqrt(machine eps) * sigma_max; below that the squared values sink into rounding."""
+    sqrt(machine eps) * sigma_max; below that the squared values sink into rounding.
+    method "cholqr" (Sec. 3's Cholesky QR in place of the Householder QR): the
+    R-factor of Y^T from the Cholesky factor of Y Y^T + s I, then the SVD of R as in
+    "qr".  The shift s = 11 (m n + n (n + 1)) u ||Y||_F^2 (Y^T is m x n; the shifted
+    Cholesky QR of Fukaya, Kannan, Nakatsukasa, Yamamoto and Yanagisawa, 2020, with the
+    Frobenius norm bounding the 2-norm) keeps the factorisation defined for the
+    rank-deficient fill; it lifts
+    every squared singular value by about s, so the kept count compares sigma_R^2 - s
+    with eps_fill^2.  Same accuracy limit as "gram"."""
     n, k = V.shape
     if Frow is None or Frow.shape[1] == 0 or k >= n:
         return V
@@ -143,12 +151,24 @@ def _augment(V, Frow, eps_fill, method="qr"):
         lam, W = lam[::-1], W[:, ::-1]                   # largest first
         keep = min(int(np.count_nonzero(lam > eps_fill * eps_fill)), n - k)
         Vbar = W[:, :keep]
-    else:
+    elif method == "cholqr":
+        m = Y.shape[1]
+        y2 = float(np.sum(Y * Y))
+        if y2 == 0.0:
+            return V
+        shift = 11.0 * (m * n + n * (n + 1)) * np.finfo(float).eps * y2
+        R = np.linalg.cholesky(Y @ Y.T + shift * np.eye(n)).T          # R^T R = Y Y^T + s I
+        _, s, Wt = _svd(R)
+        keep = min(int(np.count_nonzero(s * s - shift > eps_fill * eps_fill)), n - k)
+        Vbar = Wt[:keep].T
+    elif method == "qr":
         R = np.linalg.qr(Y.T, mode="r")                  # QR of Y^T
         _, s, Wt = _svd(R)                               # R = U_R diag(s) W_R^T
         keep = int(np.count_nonzero(s > eps_fill))
         keep = min(keep, n - k)
         Vbar = Wt[:keep].T                               # right sing. vectors of R
+    else:
+        raise ValueError(f"unknown augmentation method {method!r}")
     if keep:
         # they lie in range(Y), orthogonal to V in exact arithmetic; one pass of
         # block Gram-Schmidt + QR restores that in floating point
@@ -255,9 +275,10 @@ def factorize(A, eps_lu: float, norm_a: float, hook=None, augment: str = "qr", l
     """Alg. 1: factorise the H^2 matrix ``A`` (flat numpy storage) with threshold
     ``eps_lu``; ``norm_a`` is ``||A||_2`` (so ``eps_fill = eps_lu * norm_a``).
     ``hook(event, **state)``, if given, observes intermediate states (tests only).
-    ``augment``: "qr" (truncSVD option 2) or "gram" (Gram matrix + eigendecomposition).
+    ``augment``: "qr" (truncSVD option 2), "gram" (Gram matrix + eigendecomposition) or
+    "cholqr" (shifted Cholesky QR of Y^T + SVD of R).
     ``lu``: "lu" (partial pivoting) or "cholesky" (SPD matrices; W_L = W_U^T)."""
-    if augment not in ("qr", "gram") or lu not in ("lu", "cholesky"):
+    if augment not in ("qr", "gram", "cholqr") or lu not in ("lu", "cholesky"):
         raise ValueError((augment, lu))
     eps_fill = eps_lu * norm_a
     d = A.depth

@@ -339,6 +339,65 @@ def test_gram_augmentation_loses_what_squaring_hides():
     assert nq >= 11 and ng < nq, (nq, ng)
 
 
+def test_cholqr_augmentation_spans_the_qr_subspace():
+    """Sec. 3's Cholesky QR in place of the Householder QR (shifted, so that the
+    rank-deficient fill factorises): the shift leaves the eigenvectors of Y Y^T alone,
+    so away from the threshold it keeps the QR variant's subspace."""
+    for seed in range(3):
+        V, F = _augment_case(seed)
+        k = V.shape[1]
+        Vq = rs._augment(V, F, 1e-6, "qr")[:, k:]
+        Vc = rs._augment(V, F, 1e-6, "cholqr")[:, k:]
+        assert Vq.shape[1] == Vc.shape[1] == 10
+        s = np.linalg.svd(Vq.T @ Vc, compute_uv=False)
+        assert np.min(s) >= 1 - 1e-10
+        assert np.linalg.norm(V.T @ Vc) <= 1e-12
+
+
+def test_cholqr_augmentation_handles_rank_deficient_and_zero_fill():
+    """Plain Cholesky of Y Y^T breaks down on a fill of rank below n; the shifted form
+    keeps exactly the fill's rank at a threshold above the method's resolution (about
+    sqrt(u) sigma_max, as for the Gram variant), and a zero fill keeps nothing."""
+    rng = np.random.default_rng(4)
+    n, k = 30, 5
+    V = np.linalg.qr(rng.standard_normal((n, k)))[0]
+    P = np.eye(n) - V @ V.T
+    F = P @ rng.standard_normal((n, 3)) @ rng.standard_normal((3, 70))       # rank 3
+    with pytest.raises(np.linalg.LinAlgError):
+        np.linalg.cholesky((P @ F) @ (P @ F).T)
+    Vt = rs._augment(V, F, 1e-5 * np.linalg.norm(P @ F, 2), "cholqr")
+    assert Vt.shape[1] == k + 3
+    assert np.allclose(Vt.T @ Vt, np.eye(k + 3), atol=1e-12)
+    assert np.linalg.norm(P @ F - Vt @ (Vt.T @ (P @ F))) <= 1e-10 * np.linalg.norm(F)
+    assert rs._augment(V, np.zeros((n, 7)), 1e-8, "cholqr").shape[1] == k
+
+
+def test_cholqr_augmentation_factorises_to_the_same_accuracy():
+    pb = problem("cov2d", n=1024, leaf=32)
+    A = pb.A.numpy()
+    b = rhs(A.n, 2, seed=12)
+    errs = {}
+    for m in ("qr", "cholqr"):
+        Z = rs.factorize(A, 1e-6, pb.norm_a, augment=m)
+        x = rs.solve(Z, b)
+        errs[m] = dense.backward_error(A, x, b, pb.norm_a)[0]
+    assert errs["cholqr"] <= 10 * errs["qr"] + 1e-14 and errs["qr"] <= 1e-5, errs
+
+
+def test_cholqr_augmentation_loses_what_squaring_hides():
+    V, F = _augment_case(0)
+    k = V.shape[1]
+    nq = rs._augment(V, F, 1e-11, "qr").shape[1] - k
+    nc = rs._augment(V, F, 1e-11, "cholqr").shape[1] - k
+    assert nq >= 11 and nc < nq, (nq, nc)
+
+
+def test_unknown_augmentation_method_is_rejected():
+    V, F = _augment_case(0)
+    with pytest.raises(ValueError):
+        rs._augment(V, F, 1e-6, "randomised")
+
+
 @pytest.mark.parametrize("name,over", [("cov2d", dict(n=1024, leaf=32)), ("matern3d", dict(n=1024, leaf=32)),
                                        ("sphere", dict(n=2048, leaf=64))])
 def test_cholesky_variant_equals_lu_on_spd_problems(name, over):
