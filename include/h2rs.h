@@ -44,7 +44,7 @@ enum {
     H2_ERR_ARG = -1,            /* invalid argument or inconsistent descriptor       */
     H2_ERR_OOM = -2,            /* device or host allocation failed                   */
     H2_ERR_SINGULAR = -3,       /* zero or non-finite pivot in a redundant/top block  */
-    H2_ERR_RANK_CAP = -4,       /* augmented rank exceeded the box size (never for k~<=n) */
+    H2_ERR_RANK_CAP = -4,       /* augmented rank above h2_factor_opts.k_cap          */
     H2_ERR_NONFINITE = -5,      /* non-finite value in an input or a result          */
     H2_ERR_NO_CONVERGENCE = -6, /* refinement did not reach the tolerance in maxit   */
     H2_ERR_TIMEOUT = -7,        /* a bounded device wait gave up                      */
@@ -185,6 +185,12 @@ typedef struct {
                                    truncating at eps_fill, so that its layouts can be
                                    compared entry by entry with another factorisation
                                    of the same matrix (e.g. float32 against float64).  */
+    int32_t k_cap;              /* cap on every augmented rank k~_i (0 = none): the
+                                   ranks are checked on the host when they are read
+                                   back after each level, and a level with a rank above
+                                   the cap fails with H2_ERR_RANK_CAP (h2_last_error
+                                   names the first such box and level; retry with a
+                                   larger cap).  Negative: H2_ERR_ARG.                   */
 } h2_factor_opts;
 
 /* h2_factor_opts.flags: time every factorisation kernel launch with CUDA events

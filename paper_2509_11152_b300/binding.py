@@ -42,7 +42,7 @@ class h2_matrix_desc(ctypes.Structure):
 class h2_factor_opts(ctypes.Structure):
     _fields_ = [("eps_lu", ctypes.c_double), ("norm_a", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p), ("sys_norm_a", _dp),
-                ("force_ranks", ctypes.POINTER(ctypes.c_int32))]
+                ("force_ranks", ctypes.POINTER(ctypes.c_int32)), ("k_cap", ctypes.c_int32)]
 
 
 class h2_factor_stats(ctypes.Structure):
@@ -237,7 +237,7 @@ def h2_matrix_batch_info(M: Matrix) -> np.ndarray:
 
 
 def h2_factor_create(M: Matrix, eps_lu: float, norm_a, precision: int = H2_PREC_FP64,
-                     stream=None, flags: int = 0, force_ranks=None) -> Factor:
+                     stream=None, flags: int = 0, force_ranks=None, k_cap: int = 0) -> Factor:
     """``norm_a``: ||A||_2, or for a batch one norm per system (a sequence).
     ``force_ranks``: debug, the augmented ranks of every level (a sequence of arrays,
     leaves first) that the factorisation must use instead of truncating."""
@@ -252,6 +252,7 @@ def h2_factor_create(M: Matrix, eps_lu: float, norm_a, precision: int = H2_PREC_
         o.sys_norm_a = _ptr(keep, ctypes.c_double)
     o.precision = int(precision)
     o.flags = int(flags)
+    o.k_cap = int(k_cap)
     if force_ranks is not None:
         fr = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.int32).ravel() for r in force_ranks])
                                   if len(force_ranks) else np.zeros(0, np.int32))

@@ -260,6 +260,8 @@ FactorImpl<T>::FactorImpl(const MatrixObj* A_, const h2_factor_opts& o) {
             }
     }
     if (o.flags & H2_FLAG_DEBUG_SHORT_WAIT) wait_budget = 1;
+    H2_REQUIRE(o.k_cap >= 0, H2_ERR_ARG, "k_cap must be >= 0");
+    k_cap = o.k_cap;
     stream = static_cast<cudaStream_t>(o.stream);
     status.alloc(sizeof(DevStatus), stream);
 }
@@ -805,6 +807,13 @@ void FactorImpl<T>::run_level(size_t a) {
     H2_CUDA_CHECK(cudaMemcpyAsync(L.kt.data(), L.d_kt.ptr, L.cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
     H2_CUDA_CHECK(cudaStreamSynchronize(s));
     stats.host_ms[3] += ht.lap();
+    if (k_cap > 0)
+        for (int i = 0; i < L.cnt; ++i)
+            if (L.kt[i] > k_cap) {
+                throw Error{H2_ERR_RANK_CAP, "augmented rank " + std::to_string(L.kt[i]) + " of box " +
+                                                 std::to_string(i) + " at level " + std::to_string(a) +
+                                                 " exceeds k_cap " + std::to_string(k_cap)};
+            }
     untrack(this, scratch);
     if (tensor_schur) {
         untrack(this, packA);

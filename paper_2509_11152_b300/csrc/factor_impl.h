@@ -81,6 +81,7 @@ struct FactorImpl : FactorBase {
     // optional per-launch events (H2_FLAG_TIME_KERNELS)
     bool time_kernels = false;
     long long wait_budget = 4000000000LL;     // tensor-core Schur pipeline waits (SM cycles)
+    int k_cap = 0;                            // cap on the augmented ranks (0: none)
     std::vector<cudaEvent_t> kev;
     std::vector<int> kev_id;
     void kbegin(int id);

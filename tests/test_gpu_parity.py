@@ -252,6 +252,27 @@ def test_singular_matrix_reports_error_and_context_survives(h):
     assert np.isfinite(x).all()
 
 
+def test_rank_cap_reports_and_a_sufficient_cap_factorises(h):
+    """h2_factor_opts.k_cap: a cap below the largest augmented rank fails with
+    H2_ERR_RANK_CAP (the context stays usable), the largest rank itself passes and gives
+    the uncapped factor's solution (same ranks, same arithmetic)."""
+    pb = problem("sphere", n=4096, leaf=64)
+    M = h.h2_matrix_create(pb.A)
+    Z0 = h.h2_factor_create(M, 1e-5, pb.norm_a, h.H2_PREC_FP64)
+    kmax = max(int(h.h2_layout_get(Z0, lv)["ranks"].max()) for lv in range(h.h2_factor_stats_get(Z0)["nlevels"]))
+    assert kmax > 1
+    with pytest.raises(h.H2Error) as e:
+        h.h2_factor_create(M, 1e-5, pb.norm_a, h.H2_PREC_FP64, k_cap=kmax - 1)
+    assert e.value.code == -4                       # H2_ERR_RANK_CAP
+    Z = h.h2_factor_create(M, 1e-5, pb.norm_a, h.H2_PREC_FP64, k_cap=kmax)
+    b = rhs(pb.A.n, 1, seed=13)
+    x0 = h.colmajor(torch.from_numpy(b).cuda())
+    x1 = h.colmajor(torch.from_numpy(b).cuda())
+    h.h2_solve(Z0, x0)
+    h.h2_solve(Z, x1)
+    assert (torch.linalg.norm(x0 - x1) / torch.linalg.norm(x0)).item() <= 1e-12
+
+
 def test_gmres_refinement_when_plain_corrections_stall(h):
     """A loose eps_lu on an ill-conditioned Gaussian-kernel matrix: plain corrections
     stop contracting and the refinement continues with preconditioned GMRES cycles;
